@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: P_N solve time to relative residual 1e-6 on GB300, and the
+operator's throughput against HBM.
+
+Workload (one step = one whole solve): P5 (36 real SH coefficients per
+location) on 64^3 cells, seeded 4-octave value-noise fBm extinction in
+[0.5, 40], albedo 0.95, Henyey-Greenstein g = 0.3, point source at a seeded
+voxel, vacuum boundary; FP32 GMRES inner solves with FP64 iterative
+refinement (FP64 residual, inner products, Givens) to ||Q - A u|| / ||Q|| <=
+1e-6, starting from u = 0.  Synthetic data, generated in pn_inputs.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
+replica (seed = rank): the method has no data exchange between independent
+problems, so there is no collective on the data path (weak scaling).
+
+--impl reference times the FP64 CPU oracle (GMRES on its matrix-free
+operator) on the same workload, on the host cores, as a bounded sample per
+step extrapolated to a whole solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "P_N solve time to rel. residual 1e-6 (learned vs plain); apply GDOF/s vs HBM"
+WORKLOAD = "P5 64^3 fBm sigma_t[0.5,40] albedo 0.95 g 0.3 point source, FP32 GMRES + FP64 IR to 1e-6 (plain)"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel class and
+# workload; None until a capture of the current kernel exists.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--no-apply-scan", action="store_true", help="skip the separate operator throughput scan")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+
+def oracle_solve_sample(seed: int, sample_iters: int, m: int):
+    """Time `sample_iters` GMRES(m) iterations of the FP64 oracle (matrix-free
+    operator, numpy) on the full workload.  Returns seconds per iteration and
+    seconds for the initial residual."""
+    import numpy as np
+
+    import pn_inputs
+    from oracle import gmres as ogm
+    from oracle import grid as ogrid
+    from oracle import pn as opn
+    p = pn_inputs.p5_64_fbm(seed)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00, p.sigma_t_min)
+    lay = ogrid.Layout(p.N, p.R)
+    b = opn.rhs(lay, med)
+    mv = lambda v: opn.apply_matrix_free(lay, med, v)  # noqa: E731
+    t0 = time.perf_counter()
+    r0 = b - mv(np.zeros_like(b))
+    t1 = time.perf_counter()
+    _ = r0
+    ogm.gmres(mv, b, tol=1e-30, m=m, max_iter=sample_iters)
+    t2 = time.perf_counter()
+    # gmres() computes one residual before and one after the cycle
+    per_iter = max((t2 - t1) - 2 * (t1 - t0), 0.0) / sample_iters
+    return per_iter, t1 - t0
+
+
+def cpu_cores_used() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        n = 1
+    # the oracle's operator is numpy element-wise work: one thread
+    return 1 if n >= 1 else 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_init(args)
+    if rank != 0:
+        return
+    m = args.restart
+    # the GPU solve of this workload needs about this many inner iterations
+    # and refinement residuals (measured on GB300, stated in the design doc)
+    iters_est = int(os.environ.get("PN_REF_ITERS", "0")) or REF_ITERS_ESTIMATE
+    times = []
+    sample = 3
+    for s in range(args.warmup + args.steps):
+        per_iter, t_res = oracle_solve_sample(0, sample, m)
+        est = per_iter * iters_est + t_res * REF_OUTER_ESTIMATE
+        if s >= args.warmup:
+            times.append(est)
+    sec = statistics.mean(times)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solve/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solver": "oracle GMRES(m) FP64, matrix-free numpy operator",
+                   "restart": m},
+        "cpu_baseline": {"value": value, "unit": "solve/s", "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": f"{sample} GMRES({m}) iterations of the FP64 oracle per step on the full "
+                                   f"P5 64^3 problem, extrapolated to {iters_est} iterations + "
+                                   f"{REF_OUTER_ESTIMATE} residuals (the GPU solve's counts)"},
+        "e2e": {"value": value, "unit": "solve/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+REF_ITERS_ESTIMATE = 300
+REF_OUTER_ESTIMATE = 4
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+
+def apply_scan(torch, System, pn_inputs, hbm_peak):
+    """Separately timed FP32 operator throughput on two workloads."""
+    out = {}
+    for name, maker in (("P7 256^3 cloud (working set >> L2)", lambda: pn_inputs.p7_256_cloud(0)),
+                        ("P5 64^3 fBm (working set ~ L2)", lambda: pn_inputs.p5_64_fbm(0))):
+        p = maker()
+        sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
+        lay = sysm.layout
+        x = torch.rand(lay.n_elems, dtype=torch.float32, device="cuda")
+        ys = [torch.empty_like(x) for _ in range(2)]
+        for i in range(3):
+            sysm.apply(x, ys[i % 2])
+        torch.cuda.synchronize()
+        n = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(n):
+            sysm.apply(x, ys[i % 2])
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        V = p.R ** 3
+        bytes_alg = (2 * lay.n_active + 2 * V) * 4
+        gbs = bytes_alg / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs,
+                     "frac_of_hbm": gbs / hbm_peak, "dof": lay.n_active, "bytes_per_apply": bytes_alg}
+        sysm.close()
+        del x, ys
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    import pn_inputs
+    from paper_1807_00410_gb300 import System
+
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_src = peaks()
+    p = pn_inputs.p5_64_fbm(rank)
+    sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
+    lay = sysm.layout
+    u = sysm.zeros(torch.float64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    opts = dict(solver="ir", tol=1e-6, restart=args.restart, inner_tol=args.inner_tol, max_iter=30000,
+                check_every=5)
+    for _ in range(args.warmup):
+        u.zero_()
+        sysm.solve(u, **opts)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall0 = time.perf_counter()
+    step_ms, stats, prof = [], [], {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between timed solves
+        u.zero_()
+        e0.record()
+        st = sysm.solve(u, profile=True, **opts)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+        for kind, v in sysm.profile().items():
+            agg = prof.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0})
+            for key in agg:
+                agg[key] += v[key]
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel class and its roofline
+    kinds = {k: v for k, v in prof.items() if k != "scalar" and v["launches"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    kernel_names = {"apply": "k_op_naive<float,OP_APPLY>", "residual": "k_op_naive<*,OP_RESIDUAL>",
+                    "mdot": "k_mdot<float,16>", "maxpy": "k_maxpy<float,16>", "dot": "k_dot_f32",
+                    "vector": "vector updates"}
+    traffic = NCU_TRAFFIC.get((dom, "p5_64"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "kernel": kernel_names.get(dom, dom),
+                "kind": dom, "launches_per_step": d["launches"] / args.steps,
+                "avg_launch_us": d["ms"] * 1e3 / d["launches"],
+                "bytes_per_launch": d["bytes"] / d["launches"], "peak_source": f"{peak_src} hbm_gbs",
+                "share_of_step": d["ms"] / sum(step_ms)}
+    breakdown = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                     "gb_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
+                 for k, v in prof.items()}
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+        st_h, q_h = pin(p.sigma_t), pin(p.Q00)
+        out_h = torch.empty(lay.n_elems, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s2 = System(p.N, p.R, st_h, p.albedo, p.g, q_h, sigma_t_min=p.sigma_t_min)
+            u2 = s2.zeros(torch.float64)
+            s2.solve(u2, **opts)
+            out_h.copy_(u2)
+            torch.cuda.synchronize()
+            s2.close()
+        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(t_e2e, world, dev)
+        e2e = {"value": world * args.e2e_steps / t_e2e, "unit": "solve/s",
+               "h2d_bytes_per_step": int(st_h.numel() * 8 + q_h.numel() * 8),
+               "d2h_bytes_per_step": int(out_h.numel() * 8), "steps": args.e2e_steps}
+
+    scan = None
+    if rank == 0 and not args.no_apply_scan:
+        scan = apply_scan(torch, System, pn_inputs, hbm_peak)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        iters = int(round(statistics.mean(s["iterations"] for s in stats)))
+        outers = int(round(statistics.mean(s["outer_iterations"] for s in stats))) + 1
+        sample = 3
+        per_iter, t_res = oracle_solve_sample(0, sample, args.restart)
+        cpu_sec = per_iter * iters + t_res * outers
+        cpu = {"value": 1.0 / cpu_sec, "unit": "solve/s", "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"{sample} GMRES({args.restart}) iterations of the FP64 oracle (matrix-free numpy "
+                         f"operator) on the full P5 64^3 problem, extrapolated to this run's {iters} inner "
+                         f"iterations + {outers} residuals",
+               "seconds_per_solve": cpu_sec}
+
+    sysm.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solve/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart,
+                       "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
+                       "replicas": "one independent problem per GPU (seed = rank)"},
+            "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
+                      "rel_residual": stats[-1]["rel_residual"], "wall_s": wall},
+            "roofline": roofline,
+            "breakdown": breakdown,
+            "apply": scan,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(sum(s["launches"] for s in stats)),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

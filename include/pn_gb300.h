@@ -1,0 +1,224 @@
+/*
+ * pn_gb300.h -- C ABI of the GB300 (sm_103a) staggered-grid P_N library.
+ *
+ * The library applies and solves the discrete real-valued P_N system of
+ * Koerner, Portsmouth and Jakob, "P_N-Method for Multiple Scattering in
+ * Participating Media" (EGSR 2018):
+ *
+ *     A u = Q,   A = T + C - S                  (section "Discretized RTE")
+ *
+ * one equation per real SH coefficient (l, m), l <= N, at its staggered
+ * location (appendix "Final equation"; section "Precomputation",
+ * Fig. staggeredgrid).  Row (l, m) at location p reads
+ *
+ *     sum_d sum_(l',m') A_d[(l,m),(l',m')] (u_(l',m')(p + h/2 e_d)
+ *                                         - u_(l',m')(p - h/2 e_d)) / h
+ *   + (sigma_t(p) - sigma_s(p) g^l) u_(l,m)(p)  =  Q_(l,m)(p)
+ *
+ * with A_d the transport couplings of the printed equations (coefficients
+ * a..f, beta, delta of the appendix, with the denominator of a read as
+ * (2l+3)(2l+1) and the m>0 x-term of L^{l-1,m-1} read with e^{l-1,-m+1}),
+ * the scattering factor lambda_l p^{l,0} = g^l of a normalised
+ * Henyey-Greenstein phase function, a unit-cube grid of R^3 cells (h = 1/R),
+ * and the Dirichlet rule of section "Runtime": a reference to a location
+ * outside the closed domain is dropped.
+ *
+ * Staggering (the paper defers it to StaRMAP): coefficient (l, m) lives on
+ * cell faces along every axis on which its harmonic is odd and on cell
+ * centres along the others:
+ *     p_x = m mod 2 (m >= 0), (|m|+1) mod 2 (m < 0);  p_y = [m < 0];
+ *     p_z = (l + |m|) mod 2.
+ * Along an axis with p = 0 the unknowns are the R cell centres (i+1/2) h;
+ * with p = 1 they are the R+1 faces i h (boundary faces included).
+ *
+ * Parameters are given at voxel centres; sigma_t is clamped below by
+ * sigma_t_min (sections "Runtime" and "Nebulae"), sigma_s = albedo sigma_t,
+ * and both are interpolated to a location as the mean of the adjacent voxel
+ * centres that lie inside the domain.
+ *
+ * ---------------------------------------------------------------------------
+ * Vector layout (every x, y, r, u argument): "padded coefficient-major".
+ * A vector holds K = (N+1)^2 planes; plane p stores coefficient
+ * k = plane_k[p] (k = l*l + l + m) of parity class plane_class[p]
+ * (class = p_x + 2 p_y + 4 p_z); planes are grouped by class.  Element
+ * (z, y, x) of plane p is at
+ *     p * plane_stride + z * pitch_y + y * pitch_x + x
+ * and is an unknown ("active") iff x < R + p_x, y < R + p_y, z < R + p_z.
+ * Every other slot is padding: kernels never read it and write it as 0.
+ * Query the numbers with pn_get_layout().  Element type: float (PN_F32) or
+ * double (PN_F64); base pointers must be 16-byte aligned.
+ *
+ * Ownership: pn_create copies the medium; x/y/r/u buffers belong to the
+ * caller (device memory unless a call says otherwise); scratch and Krylov
+ * work vectors belong to the handle and are freed by pn_destroy.
+ * Streams: every call is ordered on the caller's cudaStream_t (NULL = the
+ * legacy default stream).  Calls that return a host scalar synchronise that
+ * stream.  A handle must not be used from two host threads at once.
+ * Errors: every call returns PN_OK (0) or a negative PN_ERR_* code and never
+ * aborts; pn_last_error() gives a message for the handle's last failure.
+ */
+#ifndef PN_GB300_H
+#define PN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PN_OK                 0
+#define PN_ERR_ARG           -1  /* invalid argument (null, N > 7, R < 2, dtype, ...) */
+#define PN_ERR_ALLOC         -2  /* device or host allocation failed */
+#define PN_ERR_CUDA          -3  /* a CUDA runtime call or kernel launch failed */
+#define PN_ERR_NOT_CONVERGED -4  /* solver hit max_iter; x holds the last iterate */
+#define PN_ERR_BREAKDOWN     -5  /* Krylov breakdown (zero norm denominator) */
+#define PN_ERR_NONFINITE     -6  /* NaN or Inf met in a residual or inner product */
+#define PN_ERR_UNSUPPORTED   -8  /* valid request this build does not implement */
+
+#define PN_F32 0
+#define PN_F64 1
+
+#define PN_BC_VACUUM 0           /* Dirichlet: outside references dropped */
+
+#define PN_Q_CENTRE_00      0    /* Q: R^3 field of Q^{0,0} at voxel centres */
+#define PN_Q_CENTRE_MOMENTS 1    /* Q: K x R^3 centre moments, k-major */
+
+#define PN_MAX_N 7
+#define PN_MAX_K 64
+
+typedef struct pn_handle pn_handle;
+
+/* Voxel-centre medium.  Arrays are indexed [z][y][x] (x fastest), R^3 each. */
+typedef struct {
+    const void* sigma_t;   /* extinction, R^3 (required) */
+    const void* albedo;    /* single-scattering albedo field R^3, or NULL */
+    double albedo_const;   /* used when albedo == NULL */
+    double g;              /* Henyey-Greenstein mean cosine, |g| < 1 */
+    const void* Q;         /* source, layout per q_mode; NULL means Q = 0 */
+    int q_mode;            /* PN_Q_CENTRE_00 or PN_Q_CENTRE_MOMENTS */
+    int dtype;             /* PN_F32 or PN_F64: element type of the arrays */
+    int on_device;         /* 1: device pointers, 0: host pointers */
+    double sigma_t_min;    /* sigma_t := max(sigma_t, sigma_t_min); >= 0 */
+} pn_medium;
+
+typedef struct {
+    int N, K, R;
+    int64_t pitch_x;       /* elements between rows (y) */
+    int64_t pitch_y;       /* elements between slices (z) */
+    int64_t plane_stride;  /* elements between planes */
+    int64_t n_elems;       /* vector length = K * plane_stride */
+    int64_t n_active;      /* number of unknowns (degrees of freedom) */
+    int plane_k[PN_MAX_K];     /* coefficient index stored in plane p */
+    int plane_class[PN_MAX_K]; /* parity class of plane p */
+} pn_layout_info;
+
+/*
+ * Create a handle for the P_N system of order N (1..7) on R^3 cells.
+ * Copies and preprocesses the medium (clamp, sigma_s, Q in padded layout) into
+ * device buffers owned by the handle.  Synchronises `stream` before returning.
+ * boundary must be PN_BC_VACUUM.  On failure *out is NULL and the message is
+ * available from pn_last_error(NULL).
+ */
+int pn_create(pn_handle** out, int N, int R, const pn_medium* medium, int boundary, void* stream);
+
+/* Free every buffer the handle owns.  NULL is accepted. */
+int pn_destroy(pn_handle* h);
+
+/* Fill *out with the vector layout (host struct). */
+int pn_get_layout(const pn_handle* h, pn_layout_info* out);
+
+/* Message of the last failure on h (h == NULL: last pn_create failure). */
+const char* pn_last_error(const pn_handle* h);
+
+/*
+ * y = A x  (the matrix-free staggered operator; Eq. "(T + C - S) u = A u").
+ * x, y: device vectors of `dtype` in the padded layout; must not alias.
+ * Inactive slots of x are ignored; inactive slots of y are written 0.
+ */
+int pn_apply(pn_handle* h, const void* x, void* y, int dtype, void* stream);
+
+/*
+ * y = A^T x.  The transport part is skew-symmetric under the Dirichlet rule,
+ * so A^T = (C - S) - T; needed by CG on the normal equations (section
+ * "Runtime", the paper's solver).  Same arguments as pn_apply.
+ */
+int pn_apply_t(pn_handle* h, const void* x, void* y, int dtype, void* stream);
+
+/*
+ * r = Q - A x.  If rel_out is not NULL, *rel_out (host) receives
+ * ||r||_2 / ||Q||_2 accumulated in FP64 and the stream is synchronised
+ * (||Q|| = 0 gives ||r||_2).  x and r must not alias.
+ */
+int pn_residual(pn_handle* h, const void* x, void* r, double* rel_out, int dtype, void* stream);
+
+/* *out (host) = sum_i x_i y_i over the whole padded vector, accumulated in
+ * FP64 in a fixed order (deterministic).  Synchronises the stream. */
+int pn_dot(pn_handle* h, const void* x, const void* y, double* out, int dtype, void* stream);
+
+/* y = alpha x + beta y over the whole padded vector (device vectors). */
+int pn_axpby(pn_handle* h, double alpha, const void* x, double beta, void* y, int dtype, void* stream);
+
+#define PN_SOLVER_CGLS     0     /* CG on the normal equations (the paper) */
+#define PN_SOLVER_GMRES    1     /* restarted GMRES(m) on A u = Q */
+#define PN_SOLVER_IR_GMRES 2     /* FP64 iterative refinement, FP32 GMRES inner */
+
+typedef struct {
+    int solver;          /* PN_SOLVER_* */
+    int precision;       /* CGLS/GMRES: PN_F32 or PN_F64 vectors; IR: ignored */
+    double tol;          /* target ||Q - A u||_2 / ||Q||_2 (FP64, original system) */
+    int max_iter;        /* cap on inner Krylov iterations (all restarts/outer steps) */
+    int restart;         /* GMRES basis size m (1..200) */
+    double inner_tol;    /* IR: relative reduction asked of each inner solve */
+    int max_outer;       /* IR: cap on refinement steps */
+    int check_every;     /* iterations between host convergence checks */
+    int profile;         /* 1: time every kernel launch of the solve with CUDA
+                            events on the solve's stream (see pn_profile_get) */
+} pn_solve_opts;
+
+typedef struct {
+    int status;          /* return code of the solve */
+    int iterations;      /* inner Krylov iterations (all restarts/outer steps) */
+    int outer_iterations;/* IR refinement steps (0 otherwise) */
+    double rel_residual; /* final ||Q - A u|| / ||Q|| in FP64 */
+    double seconds;      /* host wall time of the call */
+    int64_t launches;    /* CUDA kernels the solve launched */
+} pn_solve_stats;
+
+/* Fill *opts with defaults (CGLS, FP64, tol 1e-6, max_iter 100000, m 60,
+ * inner_tol 1e-2, max_outer 50, check_every 10, profile 0). */
+void pn_default_solve_opts(pn_solve_opts* opts);
+
+/*
+ * Solve A u = Q.  u: device vector in the padded layout, read as the initial
+ * guess and overwritten by the solution.  Its element type is PN_F64 for
+ * PN_SOLVER_IR_GMRES and opts->precision otherwise.  Reductions accumulate
+ * in FP64.  Returns PN_OK, or PN_ERR_NOT_CONVERGED (u holds the last
+ * iterate), PN_ERR_BREAKDOWN, PN_ERR_NONFINITE; stats may be NULL.
+ * Synchronises the stream.
+ */
+int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_solve_stats* stats, void* stream);
+
+/* Kernel classes reported by pn_profile_get. */
+#define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */
+#define PN_PROF_RESIDUAL 1   /* residual operator launches */
+#define PN_PROF_MDOT     2   /* multi-vector inner products (GMRES) */
+#define PN_PROF_MAXPY    3   /* multi-vector updates (GMRES) */
+#define PN_PROF_DOT      4   /* single inner products and their reductions */
+#define PN_PROF_VECTOR   5   /* axpy-type updates, scaling, conversions */
+#define PN_PROF_SCALAR   6   /* one-thread scalar kernels and final reductions */
+#define PN_PROF_KINDS    7
+
+/*
+ * Per-class totals of the last pn_solve run with opts->profile = 1 (zeros
+ * otherwise): summed event-timed milliseconds, number of launches, and the
+ * algorithmic bytes those launches move (every active unknown read or
+ * written once per vector operand, parameter fields once).  Host pointers;
+ * any may be NULL.  No synchronisation (the solve already synchronised).
+ */
+int pn_profile_get(const pn_handle* h, int kind, double* ms, int64_t* launches, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PN_GB300_H */

@@ -238,3 +238,52 @@ def cgls(A, b: np.ndarray, tol: float = 1e-10, max_iter: int = 100000, x0=None, 
         if history is not None:
             history.append(rel)
     return x, it, rel
+
+
+def apply_rows(layout: Layout, medium: Medium, parts, rows, transpose: bool = False) -> np.ndarray:
+    """(A u)[row] (or (A^T u)[row]) for a list of rows (k, iz, iy, ix), one by
+    one, straight from the row definition in this module's docstring.
+
+    `parts` are the per-coefficient grids of u (any array-like supporting
+    integer indexing, e.g. large numpy arrays).  Used to check full-size
+    applies at sampled outputs.  Vacuum boundary only.
+    """
+    if layout.periodic:
+        raise ValueError("apply_rows supports the vacuum boundary only")
+    A = coupling_matrices(layout.N)
+    R, h = layout.R, layout.h
+    st = np.maximum(np.asarray(medium.sigma_t, dtype=np.float64), medium.sigma_t_min)
+    al = np.asarray(medium.albedo, dtype=np.float64)
+    tsign = -1.0 if transpose else 1.0
+    out = []
+    for (k, iz, iy, ix) in rows:
+        l, m = layout.lm[k]
+        c = layout.classes[k]
+        idx = (ix, iy, iz)
+        # parameter means over adjacent in-domain centres
+        cand = []
+        for d in range(3):
+            i = idx[d]
+            cand.append([i] if c[d] == 0 else [j for j in (i - 1, i) if 0 <= j < R])
+        sts, sss = [], []
+        for cz in cand[2]:
+            for cy in cand[1]:
+                for cx in cand[0]:
+                    t = st[cz, cy, cx]
+                    a = al if al.ndim == 0 else al[cz, cy, cx]
+                    sts.append(t)
+                    sss.append(a * t)
+        diag = np.mean(sts) - scattering_factor_printed(l, medium.g) * np.mean(sss)
+        acc = diag * float(parts[k][iz, iy, ix])
+        for d in range(3):
+            for kp in np.nonzero(A[d, k])[0]:
+                shp = layout.shapes[kp]
+                vals = []
+                for off in (1 - c[d], -c[d]):
+                    j = list(idx)
+                    j[d] += off
+                    inside = all(0 <= j[e] < shp[2 - e] for e in range(3))
+                    vals.append(float(parts[kp][j[2], j[1], j[0]]) if inside else 0.0)
+                acc += tsign * A[d, k, kp] / h * (vals[0] - vals[1])
+        out.append(acc)
+    return np.array(out)

@@ -1,0 +1,481 @@
+// C ABI of the GB300 P_N library: handles, layout, medium upload and the
+// operator / vector entry points.  The solver entry point is in pn_solve.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pn_internal.h"
+
+static std::string g_create_error;
+
+int pn_fail(pn_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int pn_cuda_fail(pn_handle* h, cudaError_t e, const char* where) {
+    return pn_fail(h, PN_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int pn_sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+namespace {
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Copy n elements of a host or device array of PN_F32/PN_F64 into a host
+// double vector.
+int load_field(pn_handle* h, const void* src, int64_t n, int dtype, int on_device, std::vector<double>& out) {
+    out.resize(size_t(n));
+    const size_t esz = dtype == PN_F32 ? 4 : 8;
+    std::vector<unsigned char> tmp;
+    const void* hp = src;
+    if (on_device) {
+        tmp.resize(size_t(n) * esz);
+        cudaError_t e = cudaMemcpy(tmp.data(), src, size_t(n) * esz, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_create: reading medium");
+        hp = tmp.data();
+    }
+    if (dtype == PN_F32) {
+        const float* f = (const float*)hp;
+        for (int64_t i = 0; i < n; ++i) out[size_t(i)] = f[i];
+    } else {
+        std::memcpy(out.data(), hp, size_t(n) * 8);
+    }
+    return PN_OK;
+}
+
+template <typename T>
+int dev_alloc(pn_handle* h, T** p, size_t count, const char* what) {
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return pn_fail(h, PN_ERR_ALLOC, std::string("pn_create: cudaMalloc failed for ") + what);
+    }
+    return PN_OK;
+}
+
+// Writes one padded plane from a voxel-centre field: every active slot gets
+// the mean of its adjacent in-domain centres, every other slot 0.
+__global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int64_t pitch_x,
+                             int64_t pitch_y, int64_t plane_stride, double* out_d, float* out_f) {
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < plane_stride;
+         s += int64_t(gridDim.x) * blockDim.x) {
+        const int x = int(s % pitch_x);
+        const int64_t t = s / pitch_x;
+        const int y = int(t % (R + 1));
+        const int z = int(t / (R + 1));
+        double v = 0.0;
+        if (s < pitch_y * (R + 1) && x < R + px && y < R + py && z < R + pz) {
+            const int x0 = px ? max(x - 1, 0) : x, x1 = px ? min(x, R - 1) : x;
+            const int y0 = py ? max(y - 1, 0) : y, y1 = py ? min(y, R - 1) : y;
+            const int z0 = pz ? max(z - 1, 0) : z, z1 = pz ? min(z, R - 1) : z;
+            const int64_t R2 = int64_t(R) * R;
+            v = 0.125 * (F[z0 * R2 + y0 * R + x0] + F[z0 * R2 + y0 * R + x1] + F[z0 * R2 + y1 * R + x0] +
+                         F[z0 * R2 + y1 * R + x1] + F[z1 * R2 + y0 * R + x0] + F[z1 * R2 + y0 * R + x1] +
+                         F[z1 * R2 + y1 * R + x0] + F[z1 * R2 + y1 * R + x1]);
+        }
+        out_d[s] = v;
+        out_f[s] = float(v);
+    }
+}
+
+void free_all(pn_handle* h) {
+    void* ptrs[] = {h->d_planes, h->d_terms, h->d_st_f, h->d_ss_f, h->d_st_d, h->d_ss_d,
+                    h->d_q_f,    h->d_q_d,   h->d_partials, h->d_scalars, h->d_work};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+    h->prof_ev.clear();
+}
+
+}  // namespace
+
+void pn_prof_reset(pn_handle* h, bool on) {
+    h->prof_on = on;
+    h->prof_pending.clear();
+    for (int k = 0; k < PN_PROF_KINDS; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+        h->prof_bytes[k] = 0.0;
+    }
+}
+
+void pn_prof_begin(pn_handle* h, cudaStream_t s) {
+    if (!h->prof_on) return;
+    const size_t need = 2 * (h->prof_pending.size() + 1);
+    while (h->prof_ev.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            h->prof_on = false;  // out of events: stop profiling, keep solving
+            cudaGetLastError();
+            return;
+        }
+        h->prof_ev.push_back(e);
+    }
+    cudaEventRecord(h->prof_ev[need - 2], s);
+}
+
+void pn_prof_end(pn_handle* h, cudaStream_t s, int kind, double bytes) {
+    if (!h->prof_on) return;
+    const size_t i = 2 * h->prof_pending.size();
+    if (i + 1 >= h->prof_ev.size()) return;
+    cudaEventRecord(h->prof_ev[i + 1], s);
+    h->prof_pending.emplace_back(kind, bytes);
+}
+
+void pn_prof_drain(pn_handle* h) {
+    for (size_t i = 0; i < h->prof_pending.size(); ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const int k = h->prof_pending[i].first;
+        h->prof_ms[k] += ms;
+        h->prof_n[k] += 1;
+        h->prof_bytes[k] += h->prof_pending[i].second;
+    }
+    h->prof_pending.clear();
+}
+
+extern "C" {
+
+int pn_profile_get(const pn_handle* h, int kind, double* ms, int64_t* launches, double* bytes) {
+    if (!h || kind < 0 || kind >= PN_PROF_KINDS) return PN_ERR_ARG;
+    if (ms) *ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_n[kind];
+    if (bytes) *bytes = h->prof_bytes[kind];
+    return PN_OK;
+}
+
+const char* pn_last_error(const pn_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void pn_default_solve_opts(pn_solve_opts* o) {
+    if (!o) return;
+    o->solver = PN_SOLVER_CGLS;
+    o->precision = PN_F64;
+    o->tol = 1e-6;
+    o->max_iter = 100000;
+    o->restart = 60;
+    o->inner_tol = 1e-2;
+    o->max_outer = 50;
+    o->check_every = 10;
+    o->profile = 0;
+}
+
+int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream) {
+    if (!out) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: out is NULL");
+    *out = nullptr;
+    if (N < 0 || N > PN_MAX_N) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: N must be in [0, 7]");
+    if (R < 2 || R > 1024) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: R must be in [2, 1024]");
+    if (!m || !m->sigma_t) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: medium or sigma_t is NULL");
+    if (m->dtype != PN_F32 && m->dtype != PN_F64) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: bad medium dtype");
+    if (boundary != PN_BC_VACUUM) return pn_fail(nullptr, PN_ERR_UNSUPPORTED, "pn_create: only PN_BC_VACUUM is built");
+    if (m->Q && m->q_mode != PN_Q_CENTRE_00 && m->q_mode != PN_Q_CENTRE_MOMENTS)
+        return pn_fail(nullptr, PN_ERR_ARG, "pn_create: bad q_mode");
+    if (!(std::fabs(m->g) < 1.0)) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: |g| must be < 1");
+    if (!(m->sigma_t_min >= 0.0)) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: sigma_t_min must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    pn_handle* h = new (std::nothrow) pn_handle();
+    if (!h) return pn_fail(nullptr, PN_ERR_ALLOC, "pn_create: host allocation failed");
+    cudaGetDevice(&h->device);
+    h->N = N;
+    h->K = (N + 1) * (N + 1);
+    h->R = R;
+    h->h = 1.0 / R;
+    h->pitch_x = round_up(R + 1, 4);
+    h->pitch_y = h->pitch_x * (R + 1);
+    h->plane_stride = round_up(h->pitch_y * (R + 1), 32);
+    h->n_elems = h->plane_stride * h->K;
+
+    // planes grouped by parity class, coefficient order within a class
+    const int K = h->K;
+    std::vector<int> cls_of_k(K);
+    for (int l = 0, k = 0; l <= N; ++l)
+        for (int mm = -l; mm <= l; ++mm, ++k) {
+            int px, py, pz;
+            pn::parity_bits(l, mm, px, py, pz);
+            cls_of_k[k] = px + 2 * py + 4 * pz;
+        }
+    int p = 0;
+    for (int c = 0; c < 8; ++c)
+        for (int k = 0; k < K; ++k)
+            if (cls_of_k[k] == c) {
+                h->plane_k[p] = k;
+                h->plane_class[p] = c;
+                h->plane_of_k[k] = p;
+                ++p;
+            }
+    for (int q = K; q < PN_MAX_K; ++q) h->plane_k[q] = h->plane_class[q] = -1;
+
+    std::vector<double> A;
+    pn::transport_couplings(N, A);
+    h->planes.resize(K);
+    h->n_active = 0;
+    for (int q = 0; q < K; ++q) {
+        const int k = h->plane_k[q];
+        int l = 0;
+        while ((l + 1) * (l + 1) <= k) ++l;
+        pn::Plane P;
+        P.k = k;
+        P.l = l;
+        P.m = k - l * l - l;
+        P.cls = h->plane_class[q];
+        P.px = P.cls & 1;
+        P.py = (P.cls >> 1) & 1;
+        P.pz = (P.cls >> 2) & 1;
+        P.fl_d = l == 0 ? 1.0 : std::pow(m->g, l);
+        P.fl_f = float(P.fl_d);
+        P.t0 = int(h->terms.size());
+        for (int d = 0; d < 3; ++d)
+            for (int kp = 0; kp < K; ++kp) {
+                const double a = A[(size_t(d) * K + k) * K + kp];
+                if (a == 0.0) continue;
+                pn::Term t;
+                t.q = h->plane_of_k[kp];
+                t.axis = d;
+                t.cd = a * R;  // A_d / h
+                t.cf = float(t.cd);
+                h->terms.push_back(t);
+            }
+        P.t1 = int(h->terms.size());
+        h->planes[q] = P;
+        h->n_active += int64_t(R + P.px) * (R + P.py) * (R + P.pz);
+    }
+
+    int rc = PN_OK;
+    const int64_t V = int64_t(R) * R * R;
+    std::vector<double> st, al;
+#define PN_TRY(x)                       \
+    do {                                \
+        rc = (x);                       \
+        if (rc != PN_OK) goto fail;     \
+    } while (0)
+    PN_TRY(load_field(nullptr, m->sigma_t, V, m->dtype, m->on_device, st));
+    if (m->albedo) PN_TRY(load_field(nullptr, m->albedo, V, m->dtype, m->on_device, al));
+    {
+        std::vector<double> ss(static_cast<size_t>(V));
+        std::vector<float> stf(static_cast<size_t>(V)), ssf(static_cast<size_t>(V));
+        for (int64_t i = 0; i < V; ++i) {
+            double t = st[size_t(i)];
+            if (!std::isfinite(t)) {
+                rc = pn_fail(nullptr, PN_ERR_ARG, "pn_create: non-finite sigma_t");
+                goto fail;
+            }
+            t = std::max(t, m->sigma_t_min);
+            const double a = m->albedo ? al[size_t(i)] : m->albedo_const;
+            if (!std::isfinite(a)) {
+                rc = pn_fail(nullptr, PN_ERR_ARG, "pn_create: non-finite albedo");
+                goto fail;
+            }
+            st[size_t(i)] = t;
+            ss[size_t(i)] = a * t;
+            stf[size_t(i)] = float(t);
+            ssf[size_t(i)] = float(a * t);
+        }
+        PN_TRY(dev_alloc(nullptr, &h->d_st_d, size_t(V), "sigma_t"));
+        PN_TRY(dev_alloc(nullptr, &h->d_ss_d, size_t(V), "sigma_s"));
+        PN_TRY(dev_alloc(nullptr, &h->d_st_f, size_t(V), "sigma_t"));
+        PN_TRY(dev_alloc(nullptr, &h->d_ss_f, size_t(V), "sigma_s"));
+        cudaError_t e = cudaMemcpy(h->d_st_d, st.data(), V * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_ss_d, ss.data(), V * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_st_f, stf.data(), V * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_ss_f, ssf.data(), V * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            rc = pn_cuda_fail(nullptr, e, "pn_create: uploading medium");
+            goto fail;
+        }
+    }
+    PN_TRY(dev_alloc(nullptr, &h->d_planes, size_t(K), "planes"));
+    PN_TRY(dev_alloc(nullptr, &h->d_terms, std::max<size_t>(1, h->terms.size()), "terms"));
+    {
+        cudaError_t e = cudaMemcpy(h->d_planes, h->planes.data(), K * sizeof(pn::Plane), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !h->terms.empty())
+            e = cudaMemcpy(h->d_terms, h->terms.data(), h->terms.size() * sizeof(pn::Term), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            rc = pn_cuda_fail(nullptr, e, "pn_create: uploading tables");
+            goto fail;
+        }
+    }
+    // scratch
+    h->red_blocks = pn::reduce_blocks();
+    PN_TRY(dev_alloc(nullptr, &h->d_partials,
+                     size_t(std::max(h->red_blocks * PN_MAX_MDOT, pn::op_partial_count(h))), "partials"));
+    PN_TRY(dev_alloc(nullptr, &h->d_scalars, size_t(PN_NSCALARS), "scalars"));
+    if (cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
+        h->h_pinned = nullptr;
+        rc = pn_fail(nullptr, PN_ERR_ALLOC, "pn_create: pinned host allocation failed");
+        goto fail;
+    }
+    // source
+    h->n_q_planes = !m->Q ? 0 : (m->q_mode == PN_Q_CENTRE_00 ? 1 : K);
+    if (h->n_q_planes > 0) {
+        PN_TRY(dev_alloc(nullptr, &h->d_q_d, size_t(h->n_q_planes) * h->plane_stride, "Q"));
+        PN_TRY(dev_alloc(nullptr, &h->d_q_f, size_t(h->n_q_planes) * h->plane_stride, "Q"));
+        double* tmp = nullptr;
+        PN_TRY(dev_alloc(nullptr, &tmp, size_t(V), "Q staging"));
+        std::vector<double> qk;
+        const unsigned char* base = (const unsigned char*)m->Q;
+        const size_t esz = m->dtype == PN_F32 ? 4 : 8;
+        for (int q = 0; q < h->n_q_planes && rc == PN_OK; ++q) {
+            // q_mode 0: plane 0 is coefficient 0 (class 0 comes first)
+            const int k = h->n_q_planes == 1 ? 0 : h->plane_k[q];
+            rc = load_field(nullptr, base + size_t(k) * V * esz, V, m->dtype, m->on_device, qk);
+            if (rc != PN_OK) break;
+            cudaError_t e = cudaMemcpy(tmp, qk.data(), V * 8, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                rc = pn_cuda_fail(nullptr, e, "pn_create: uploading Q");
+                break;
+            }
+            const pn::Plane& P = h->planes[q];
+            k_fill_plane<<<8 * pn_sm_count(), 256, 0, s>>>(tmp, R, P.px, P.py, P.pz, h->pitch_x, h->pitch_y,
+                                                         h->plane_stride, h->d_q_d + q * h->plane_stride,
+                                                         h->d_q_f + q * h->plane_stride);
+            e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) rc = pn_cuda_fail(nullptr, e, "pn_create: filling Q");
+        }
+        cudaFree(tmp);
+        if (rc != PN_OK) goto fail;
+        cudaError_t e = pn::launch_dot(h, h->d_q_d, h->d_q_d, int64_t(h->n_q_planes) * h->plane_stride, PN_F64,
+                                       h->d_scalars, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pinned, h->d_scalars, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = pn_cuda_fail(nullptr, e, "pn_create: norm of Q");
+            goto fail;
+        }
+        h->q_norm2 = h->h_pinned[0];
+    }
+    {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = pn_cuda_fail(nullptr, e, "pn_create");
+            goto fail;
+        }
+    }
+#undef PN_TRY
+    *out = h;
+    return PN_OK;
+fail:
+    free_all(h);
+    delete h;
+    return rc;
+}
+
+int pn_destroy(pn_handle* h) {
+    if (!h) return PN_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) cudaSetDevice(h->device);
+    free_all(h);
+    if (dev != h->device) cudaSetDevice(dev);
+    delete h;
+    return PN_OK;
+}
+
+int pn_get_layout(const pn_handle* h, pn_layout_info* o) {
+    if (!h || !o) return PN_ERR_ARG;
+    o->N = h->N;
+    o->K = h->K;
+    o->R = h->R;
+    o->pitch_x = h->pitch_x;
+    o->pitch_y = h->pitch_y;
+    o->plane_stride = h->plane_stride;
+    o->n_elems = h->n_elems;
+    o->n_active = h->n_active;
+    for (int p = 0; p < PN_MAX_K; ++p) {
+        o->plane_k[p] = h->plane_k[p];
+        o->plane_class[p] = h->plane_class[p];
+    }
+    return PN_OK;
+}
+
+static int check_vec_args(pn_handle* h, const void* a, const void* b, int dtype, const char* fn) {
+    if (!h) return PN_ERR_ARG;
+    if (!a || !b) return pn_fail(h, PN_ERR_ARG, std::string(fn) + ": NULL vector");
+    if (dtype != PN_F32 && dtype != PN_F64) return pn_fail(h, PN_ERR_ARG, std::string(fn) + ": bad dtype");
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u)
+        return pn_fail(h, PN_ERR_ARG, std::string(fn) + ": vectors must be 16-byte aligned");
+    return PN_OK;
+}
+
+static int run_op(pn_handle* h, int mode, const void* x, void* y, int dtype, void* stream, const char* fn) {
+    int rc = check_vec_args(h, x, y, dtype, fn);
+    if (rc != PN_OK) return rc;
+    if (x == y) return pn_fail(h, PN_ERR_ARG, std::string(fn) + ": x and y must not alias");
+    cudaError_t e = pn::launch_op(h, mode, x, y, dtype, nullptr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return pn_cuda_fail(h, e, fn);
+    return PN_OK;
+}
+
+int pn_apply(pn_handle* h, const void* x, void* y, int dtype, void* stream) {
+    return run_op(h, pn::OP_APPLY, x, y, dtype, stream, "pn_apply");
+}
+
+int pn_apply_t(pn_handle* h, const void* x, void* y, int dtype, void* stream) {
+    return run_op(h, pn::OP_APPLY_T, x, y, dtype, stream, "pn_apply_t");
+}
+
+int pn_residual(pn_handle* h, const void* x, void* r, double* rel_out, int dtype, void* stream) {
+    int rc = check_vec_args(h, x, r, dtype, "pn_residual");
+    if (rc != PN_OK) return rc;
+    if (x == r) return pn_fail(h, PN_ERR_ARG, "pn_residual: x and r must not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = pn::launch_op(h, pn::OP_RESIDUAL, x, r, dtype, rel_out ? h->d_partials : nullptr, s);
+    if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_residual");
+    if (rel_out) {
+        e = pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, h->d_scalars, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pinned, h->d_scalars, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_residual");
+        const double rr = h->h_pinned[0];
+        *rel_out = h->q_norm2 > 0.0 ? std::sqrt(rr / h->q_norm2) : std::sqrt(rr);
+        if (!std::isfinite(*rel_out)) return pn_fail(h, PN_ERR_NONFINITE, "pn_residual: non-finite residual");
+    }
+    return PN_OK;
+}
+
+int pn_dot(pn_handle* h, const void* x, const void* y, double* out, int dtype, void* stream) {
+    int rc = check_vec_args(h, x, y, dtype, "pn_dot");
+    if (rc != PN_OK) return rc;
+    if (!out) return pn_fail(h, PN_ERR_ARG, "pn_dot: out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = pn::launch_dot(h, x, y, h->n_elems, dtype, h->d_scalars, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pinned, h->d_scalars, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_dot");
+    *out = h->h_pinned[0];
+    return PN_OK;
+}
+
+int pn_axpby(pn_handle* h, double alpha, const void* x, double beta, void* y, int dtype, void* stream) {
+    int rc = check_vec_args(h, x, y, dtype, "pn_axpby");
+    if (rc != PN_OK) return rc;
+    cudaError_t e = pn::launch_axpby(h->n_elems, alpha, x, beta, y, dtype, (cudaStream_t)stream);
+    if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_axpby");
+    return PN_OK;
+}
+
+}  // extern "C"

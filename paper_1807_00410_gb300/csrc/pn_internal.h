@@ -1,0 +1,132 @@
+// Internal declarations of the GB300 P_N library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pn_gb300.h"
+
+namespace pn {
+
+// One transport coupling of an output plane:
+//   y_p(s) += c * (x_q(s + (1 - b) e_axis) - x_q(s - b e_axis)),   c = A_d[k_p, k_q] / h
+// where b is plane p's parity bit along `axis` (slot arithmetic of the layout).
+struct Term {
+    int q;       // input plane
+    int axis;    // 0 = x, 1 = y, 2 = z
+    float cf;    // c in FP32
+    double cd;   // c in FP64
+};
+
+// Per-plane description.
+struct Plane {
+    int k, l, m;       // coefficient
+    int cls;           // px + 2 py + 4 pz
+    int px, py, pz;    // parity bits
+    int t0, t1;        // term range [t0, t1) in the term table
+    float fl_f;        // scattering factor g^l
+    double fl_d;
+};
+
+// Angular transport couplings from the closed forms of the appendix's final
+// real P_N equations.  A[d][k][k'] dense, d = x, y, z.  Defined in pn_tables.cpp.
+void transport_couplings(int N, std::vector<double>& A /* 3*K*K */);
+
+// Parity class bits of coefficient (l, m).
+inline void parity_bits(int l, int m, int& px, int& py, int& pz) {
+    int am = m < 0 ? -m : m;
+    px = m >= 0 ? (m & 1) : ((am + 1) & 1);
+    py = m < 0 ? 1 : 0;
+    pz = (l + am) & 1;
+}
+
+}  // namespace pn
+
+// Number of SMs of the current device (cached per process).
+int pn_sm_count();
+
+struct pn_handle {
+    int N = 0, K = 0, R = 0;
+    double h = 0.0;
+    int64_t pitch_x = 0, pitch_y = 0, plane_stride = 0, n_elems = 0, n_active = 0;
+    int plane_k[PN_MAX_K];
+    int plane_class[PN_MAX_K];
+    int plane_of_k[PN_MAX_K];
+    std::vector<pn::Plane> planes;
+    std::vector<pn::Term> terms;
+    int device = 0;
+
+    // device copies of the tables
+    pn::Plane* d_planes = nullptr;
+    pn::Term* d_terms = nullptr;
+    // voxel-centre fields (clamped sigma_t, sigma_s = albedo sigma_t), R^3 each
+    float* d_st_f = nullptr;
+    float* d_ss_f = nullptr;
+    double* d_st_d = nullptr;
+    double* d_ss_d = nullptr;
+    // source in the padded layout: n_q_planes planes (1: only Q^{0,0}, K: all)
+    int n_q_planes = 0;
+    float* d_q_f = nullptr;
+    double* d_q_d = nullptr;
+    double q_norm2 = 0.0;  // ||Q||^2 (FP64)
+
+    // scratch: FP64 reduction partials and device scalars
+    int red_blocks = 0;           // blocks of every reduction kernel
+    double* d_partials = nullptr; // red_blocks * PN_MAX_MDOT doubles
+    double* d_scalars = nullptr;  // PN_NSCALARS doubles
+    double* h_pinned = nullptr;   // pinned host mirror of a few scalars
+
+    // Krylov workspace (lazily grown)
+    void* d_work = nullptr;
+    size_t work_bytes = 0;
+
+    // launch profiler of pn_solve (opts.profile): event pairs pending readout
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<std::pair<int, double>> prof_pending;
+    double prof_ms[PN_PROF_KINDS] = {};
+    int64_t prof_n[PN_PROF_KINDS] = {};
+    double prof_bytes[PN_PROF_KINDS] = {};
+
+    std::string err;
+};
+
+#define PN_MAX_MDOT 16
+#define PN_NSCALARS 1024
+
+// Kernel launchers (pn_kernels.cu).  All return cudaError_t of the launch.
+namespace pn {
+
+enum OpMode { OP_APPLY = 0, OP_APPLY_T = 1, OP_RESIDUAL = 2 };
+
+// y = op(x).  For OP_RESIDUAL y = b - A x with b = Q (bvec == null) or the
+// full vector bvec and, if partials != null, the per-block FP64 sums of y^2
+// go to partials[0..op_partial_count(h)).
+cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
+                      double* partials, cudaStream_t s, const void* bvec = nullptr);
+int op_partial_count(const pn_handle* h);
+
+// partials[b] = per-block sum of a_i * b_i (FP64); then *out = sum of partials.
+cudaError_t launch_dot(const pn_handle* h, const void* a, const void* b, int64_t n, int dtype,
+                       double* out_dev, cudaStream_t s);
+cudaError_t launch_reduce(const double* partials, int nblocks, int nvals, double* out_dev,
+                          cudaStream_t s);
+cudaError_t launch_axpby(int64_t n, double alpha, const void* x, double beta, void* y, int dtype,
+                         cudaStream_t s);
+int reduce_blocks();
+
+}  // namespace pn
+
+// Profiler helpers (pn_api.cu).  prof_begin/prof_end bracket one launch on
+// stream s; prof_drain reads out completed pairs (call after a sync).
+void pn_prof_begin(pn_handle* h, cudaStream_t s);
+void pn_prof_end(pn_handle* h, cudaStream_t s, int kind, double bytes);
+void pn_prof_drain(pn_handle* h);
+void pn_prof_reset(pn_handle* h, bool on);
+
+// Set the handle's error message and return code.
+int pn_fail(pn_handle* h, int code, const std::string& msg);
+int pn_cuda_fail(pn_handle* h, cudaError_t e, const char* where);

@@ -1,0 +1,229 @@
+// Operator and vector kernels of the GB300 P_N library.
+//
+// k_op_naive is the plain, one-thread-per-output form of the staggered P_N
+// operator (appendix "Final equation"; central differences between
+// staggered grids, section "Precomputation"; Dirichlet dropping, section
+// "Runtime").  It serves FP64 and every order N through the per-handle term
+// table, and is the correctness baseline for the tiled FP32 kernel.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pn_internal.h"
+
+namespace pn {
+
+template <typename T>
+struct OpArgs {
+    const T* x;
+    T* y;
+    const T* q;        // source planes (n_q) or null
+    int n_q;
+    const T* bvec;     // residual against this full vector instead of Q (or null)
+    const T* st;       // clamped sigma_t at voxel centres, R^3
+    const T* ss;       // sigma_s at voxel centres, R^3
+    const Plane* planes;
+    const Term* terms;
+    int R;
+    int64_t pitch_x, pitch_y, plane_stride;
+    double* partials;  // residual: per-block sums of r^2
+};
+
+template <typename T> __device__ __forceinline__ T term_coef(const Term& t);
+template <> __device__ __forceinline__ float term_coef<float>(const Term& t) { return t.cf; }
+template <> __device__ __forceinline__ double term_coef<double>(const Term& t) { return t.cd; }
+template <typename T> __device__ __forceinline__ T plane_fl(const Plane& p);
+template <> __device__ __forceinline__ float plane_fl<float>(const Plane& p) { return p.fl_f; }
+template <> __device__ __forceinline__ double plane_fl<double>(const Plane& p) { return p.fl_d; }
+
+// Mean of a centre field over the in-domain voxel centres adjacent to slot
+// (x, y, z) of a grid with parity bits (px, py, pz).  Along an odd axis the
+// candidates are slots i-1 and i; clamping both into [0, R) repeats the single
+// in-domain centre at a boundary face, which leaves the mean unchanged.
+template <typename T>
+__device__ __forceinline__ T centre_mean(const T* F, int R, int x, int y, int z, int px, int py, int pz) {
+    const int x0 = px ? max(x - 1, 0) : x, x1 = px ? min(x, R - 1) : x;
+    const int y0 = py ? max(y - 1, 0) : y, y1 = py ? min(y, R - 1) : y;
+    const int z0 = pz ? max(z - 1, 0) : z, z1 = pz ? min(z, R - 1) : z;
+    const int64_t R2 = int64_t(R) * R;
+    T s = F[z0 * R2 + y0 * R + x0] + F[z0 * R2 + y0 * R + x1] + F[z0 * R2 + y1 * R + x0] +
+          F[z0 * R2 + y1 * R + x1] + F[z1 * R2 + y0 * R + x0] + F[z1 * R2 + y0 * R + x1] +
+          F[z1 * R2 + y1 * R + x0] + F[z1 * R2 + y1 * R + x1];
+    return s * T(0.125);
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = 0.0;
+    if (wid == 0) {
+        for (int i = lane; i < nw; i += 32) v += red[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;  // valid in thread 0
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_op_naive(OpArgs<T> a) {
+    const int p = blockIdx.y;
+    const Plane P = a.planes[p];
+    const int R = a.R;
+    const int ny = R + 1;
+    const int64_t box = a.pitch_y * int64_t(R + 1);
+    const int64_t pbase = int64_t(p) * a.plane_stride;
+    const T fl = plane_fl<T>(P);
+    double racc = 0.0;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < a.plane_stride;
+         s += int64_t(gridDim.x) * blockDim.x) {
+        const int x = int(s % a.pitch_x);
+        const int64_t t = s / a.pitch_x;
+        const int y = int(t % ny);
+        const int z = int(t / ny);
+        const bool active = s < box && x < R + P.px && y < R + P.py && z < R + P.pz;
+        T out = T(0);
+        if (active) {
+            const T diag = centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
+                           fl * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
+            T acc = diag * a.x[pbase + s];
+            T tr = T(0);
+            for (int ti = P.t0; ti < P.t1; ++ti) {
+                const Term tm = a.terms[ti];
+                int i, b;
+                int64_t stride;
+                if (tm.axis == 0) { i = x; b = P.px; stride = 1; }
+                else if (tm.axis == 1) { i = y; b = P.py; stride = a.pitch_x; }
+                else { i = z; b = P.pz; stride = a.pitch_y; }
+                const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
+                // plus neighbour at slot i + 1 - b (exists iff < R + 1 - b),
+                // minus neighbour at slot i - b (exists iff >= 0)
+                const T vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
+                const T vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
+                tr += term_coef<T>(tm) * (vp - vm);
+            }
+            acc = (MODE == OP_APPLY_T) ? acc - tr : acc + tr;
+            if (MODE == OP_RESIDUAL) {
+                const T bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : T(0));
+                out = bq - acc;
+                racc += double(out) * double(out);
+            } else {
+                out = acc;
+            }
+        }
+        a.y[pbase + s] = out;
+    }
+    if (MODE == OP_RESIDUAL && a.partials != nullptr) {
+        const double bs = block_sum(racc);
+        if (threadIdx.x == 0) a.partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = bs;
+    }
+}
+
+static int naive_grid_x(const pn_handle* h) {
+    int64_t want = (h->plane_stride + 1023) / 1024;
+    if (want > 4096) want = 4096;
+    if (want < 1) want = 1;
+    return int(want);
+}
+
+int op_partial_count(const pn_handle* h) { return naive_grid_x(h) * h->K; }
+
+template <typename T>
+static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T* st, const T* ss,
+                        const T* q, const T* bvec, double* partials, cudaStream_t s) {
+    OpArgs<T> a;
+    a.x = x; a.y = y; a.q = q; a.n_q = h->n_q_planes; a.bvec = bvec;
+    a.st = st; a.ss = ss;
+    a.planes = h->d_planes; a.terms = h->d_terms;
+    a.R = h->R; a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
+    a.partials = partials;
+    dim3 grid(naive_grid_x(h), h->K);
+    if (mode == OP_APPLY) k_op_naive<T, OP_APPLY><<<grid, 256, 0, s>>>(a);
+    else if (mode == OP_APPLY_T) k_op_naive<T, OP_APPLY_T><<<grid, 256, 0, s>>>(a);
+    else k_op_naive<T, OP_RESIDUAL><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
+                      double* partials, cudaStream_t s, const void* bvec) {
+    if (dtype == PN_F32)
+        return op_t<float>(h, mode, (const float*)x, (float*)y, h->d_st_f, h->d_ss_f, h->d_q_f,
+                           (const float*)bvec, partials, s);
+    return op_t<double>(h, mode, (const double*)x, (double*)y, h->d_st_d, h->d_ss_d, h->d_q_d,
+                        (const double*)bvec, partials, s);
+}
+
+// ---- reductions -------------------------------------------------------------
+
+static int g_reduce_blocks = 0;
+int reduce_blocks() {
+    if (g_reduce_blocks == 0) g_reduce_blocks = 4 * pn_sm_count();
+    return g_reduce_blocks;
+}
+
+// FP64 dot.  FP32 inputs: products of four consecutive elements are summed in
+// FP32 (one float4), each 4-term partial is accumulated in FP64.
+__global__ void __launch_bounds__(256) k_dot_f32(const float4* a, const float4* b, int64_t n4, double* partials) {
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 u = a[i], v = b[i];
+        acc += double(fmaf(u.w, v.w, fmaf(u.z, v.z, fmaf(u.y, v.y, u.x * v.x))));
+    }
+    const double bs = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
+__global__ void __launch_bounds__(256) k_dot_f64(const double* a, const double* b, int64_t n, double* partials) {
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        acc = fma(a[i], b[i], acc);
+    const double bs = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
+// out[v] = sum_b partials[v * nblocks + b], fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_reduce(const double* partials, int nblocks, double* out) {
+    const double* p = partials + int64_t(blockIdx.x) * nblocks;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += p[i];
+    const double bs = block_sum(acc);
+    if (threadIdx.x == 0) out[blockIdx.x] = bs;
+}
+
+cudaError_t launch_reduce(const double* partials, int nblocks, int nvals, double* out_dev, cudaStream_t s) {
+    k_reduce<<<nvals, 256, 0, s>>>(partials, nblocks, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const pn_handle* h, const void* a, const void* b, int64_t n, int dtype,
+                       double* out_dev, cudaStream_t s) {
+    const int nb = reduce_blocks();
+    if (dtype == PN_F32) {
+        k_dot_f32<<<nb, 256, 0, s>>>((const float4*)a, (const float4*)b, n / 4, h->d_partials);
+    } else {
+        k_dot_f64<<<nb, 256, 0, s>>>((const double*)a, (const double*)b, n, h->d_partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce(h->d_partials, nb, 1, out_dev, s);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpby(int64_t n, T alpha, const T* x, T beta, T* y) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = alpha * x[i] + beta * y[i];
+}
+
+cudaError_t launch_axpby(int64_t n, double alpha, const void* x, double beta, void* y, int dtype, cudaStream_t s) {
+    const int nb = 8 * pn_sm_count();
+    if (dtype == PN_F32)
+        k_axpby<float><<<nb, 256, 0, s>>>(n, float(alpha), (const float*)x, float(beta), (float*)y);
+    else
+        k_axpby<double><<<nb, 256, 0, s>>>(n, alpha, (const double*)x, beta, (double*)y);
+    return cudaGetLastError();
+}
+
+}  // namespace pn

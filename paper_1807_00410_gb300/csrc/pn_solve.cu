@@ -1,0 +1,567 @@
+// Krylov solvers of the GB300 P_N library (pn_solve).
+//
+//  * CGLS: CG on the normal equations A^T A u = A^T Q without forming A^T A,
+//    the paper's solver (sections "Runtime" and "Results").  Scalars stay on
+//    the device; the host reads ||r||^2 every `check_every` iterations.
+//  * GMRES(m): restarted GMRES on A u = Q (A is nonsingular with a positive
+//    definite symmetric part, so the normal equations are not needed).
+//    Classical Gram-Schmidt applied twice, FP64 inner products, Hessenberg
+//    matrix, Givens rotations and the triangular solve in FP64 on the device.
+//  * IR: iterative refinement; the residual and the iterate are FP64, each
+//    correction comes from an FP32 GMRES solve of A d = r / ||r||.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <string>
+
+#include "pn_internal.h"
+
+namespace {
+
+// scalar slots in h->d_scalars
+enum { S_RR = 0, S_QQ = 1, S_G0 = 2, S_G1 = 3, S_BETA2 = 4, S_RES = 5, S_SCALE = 6, S_NRM2 = 7, S_MAXPY = 64 };
+
+int nb_vec() { return 8 * pn_sm_count(); }
+
+__device__ __forceinline__ double warp_block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    v = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = lane; i < nw; i += 32) v += red[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// x += alpha p ; r -= alpha q ; partial sums of r^2.   alpha = S[g] / S[qq].
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgls_xr(int64_t n, T* x, T* r, const T* p, const T* q,
+                                                 const double* S, int g, double* partials) {
+    const double qq = S[S_QQ];
+    const T alpha = qq > 0.0 ? T(S[g] / qq) : T(0);
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        x[i] += alpha * p[i];
+        const T ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        acc += double(ri) * double(ri);
+    }
+    const double bs = warp_block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
+// p = s + beta p,  beta = S[gnew] / S[gold]
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgls_p(int64_t n, T* p, const T* s, const double* S, int gold, int gnew) {
+    const double go = S[gold];
+    const T beta = go > 0.0 ? T(S[gnew] / go) : T(0);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        p[i] = s[i] + beta * p[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy(int64_t n, T* dst, const T* src) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = src[i];
+}
+
+// v *= 1 / sqrt(S[idx])  (or v = 0 if S[idx] == 0)
+template <typename T>
+__global__ void __launch_bounds__(256) k_scale_invnorm(int64_t n, T* v, const double* S, int idx) {
+    const double nn = S[idx];
+    const T sc = nn > 0.0 ? T(1.0 / sqrt(nn)) : T(0);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        v[i] *= sc;
+}
+
+// Multi-dot: partials[j * gridDim.x + b] = block b's share of V_j . w, j < nv.
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_mdot(int64_t n, const T* V, int64_t vstride, int nv, const T* w,
+                                              double* partials) {
+    double acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const T wi = w[i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (j < nv) acc[j] += double(V[j * vstride + i] * wi);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        if (j < nv) {
+            const double bs = warp_block_sum(acc[j]);
+            if (threadIdx.x == 0) partials[int64_t(j) * gridDim.x + blockIdx.x] = bs;
+        }
+    }
+}
+
+// w += sign * sum_j c[j] V_j   (c in FP64 on the device, applied in T)
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_maxpy(int64_t n, T* w, const T* V, int64_t vstride, int nv,
+                                               const double* c, double sign) {
+    T cj[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) cj[j] = j < nv ? T(sign * c[j]) : T(0);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        T acc = w[i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (j < nv) acc += cj[j] * V[j * vstride + i];
+        w[i] = acc;
+    }
+}
+
+// Arnoldi step bookkeeping, one thread, FP64.
+//   col: H column j (rows 0..j from pass 1), add: pass-2 corrections (rows 0..j),
+//   S[S_NRM2] = ||w||^2 after orthogonalisation.
+// Applies the previous rotations, forms rotation j, updates g and writes
+// |g[j+1]| to S[S_RES] and 1/||w|| to S[S_SCALE].
+__global__ void k_givens(double* H, int ldh, const double* add, double* cs, double* sn, double* g, int j,
+                         double* S) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double* col = H + int64_t(j) * ldh;
+    for (int i = 0; i <= j; ++i) col[i] += add[i];
+    const double hn = sqrt(fmax(S[S_NRM2], 0.0));
+    col[j + 1] = hn;
+    S[S_SCALE] = hn > 0.0 ? 1.0 / hn : 0.0;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = hypot(a, b);
+    const double c = den > 0.0 ? a / den : 1.0;
+    const double s = den > 0.0 ? b / den : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    S[S_RES] = fabs(g[j + 1]);
+}
+
+__global__ void k_gm_init(double* g, int m, double* S) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double beta = sqrt(fmax(S[S_BETA2], 0.0));
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    S[S_RES] = beta;
+}
+
+// Solve the k x k upper-triangular system H y = g (FP64, one thread).
+__global__ void k_gm_backsolve(const double* H, int ldh, const double* g, double* y, int k) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int c = i + 1; c < k; ++c) t -= H[int64_t(c) * ldh + i] * y[c];
+        const double d = H[int64_t(i) * ldh + i];
+        y[i] = d != 0.0 ? t / d : 0.0;
+    }
+}
+
+// v *= S[S_SCALE]
+template <typename T>
+__global__ void __launch_bounds__(256) k_scale_by(int64_t n, T* v, const double* S, int idx) {
+    const T sc = T(S[idx]);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        v[i] *= sc;
+}
+
+// r32 = r64 / sqrt(S[idx])
+__global__ void __launch_bounds__(256) k_to_f32_scaled(int64_t n, float* dst, const double* src, const double* S, int idx) {
+    const double nn = S[idx];
+    const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = float(src[i] * sc);
+}
+
+// x64 += sqrt(S[idx]) * d32
+__global__ void __launch_bounds__(256) k_add_f32_scaled(int64_t n, double* x, const float* d, const double* S, int idx) {
+    const double sc = sqrt(fmax(S[idx], 0.0));
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        x[i] += sc * double(d[i]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zero(int64_t n, T* v) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        v[i] = T(0);
+}
+
+struct Ctx {
+    pn_handle* h;
+    cudaStream_t s;
+    int rc = PN_OK;
+    void pb() { pn_prof_begin(h, s); }
+    void pe(int kind, double bytes) { pn_prof_end(h, s, kind, bytes); }
+    // algorithmic bytes of `nvec` unknown-sized vector passes of element size esz
+    double vb(double nvec, double esz) const { return nvec * double(h->n_active) * esz; }
+    // algorithmic bytes of one operator launch (x read, y written, sigma_t and
+    // sigma_s read; residual also reads its right-hand side)
+    double ob(int mode, double esz, bool bvec) const {
+        const double V = double(h->R) * h->R * h->R;
+        double b = (2.0 * h->n_active + 2.0 * V) * esz;
+        if (mode == pn::OP_RESIDUAL) b += (bvec || h->n_q_planes > 1 ? double(h->n_active) : (h->n_q_planes ? V : 0.0)) * esz;
+        return b;
+    }
+    bool ok(cudaError_t e, const char* where) {
+        if (e != cudaSuccess && rc == PN_OK) rc = pn_cuda_fail(h, e, where);
+        return rc == PN_OK;
+    }
+    int64_t launches = 0;  // kernels launched by this solve
+    bool launched(const char* where, int count = 1) {
+        launches += count;
+        return ok(cudaGetLastError(), where);
+    }
+    bool lk(cudaError_t e, const char* where, int count = 1) {
+        launches += count;
+        return ok(e, where);
+    }
+    bool lk2(cudaError_t e, const char* where) { return lk(e, where, 2); }
+    // read n doubles from d_scalars[idx..] (synchronises)
+    bool read(int idx, int n, double* out) {
+        if (!ok(cudaMemcpyAsync(h->h_pinned, h->d_scalars + idx, n * sizeof(double), cudaMemcpyDeviceToHost, s),
+                "pn_solve: read scalar"))
+            return false;
+        if (!ok(cudaStreamSynchronize(s), "pn_solve: sync")) return false;
+        pn_prof_drain(h);
+        for (int i = 0; i < n; ++i) out[i] = h->h_pinned[i];
+        return true;
+    }
+};
+
+int ensure_work(pn_handle* h, size_t bytes) {
+    if (h->work_bytes >= bytes) return PN_OK;
+    if (h->d_work) cudaFree(h->d_work);
+    h->d_work = nullptr;
+    h->work_bytes = 0;
+    if (cudaMalloc(&h->d_work, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return pn_fail(h, PN_ERR_ALLOC, "pn_solve: cannot allocate Krylov workspace");
+    }
+    h->work_bytes = bytes;
+    return PN_OK;
+}
+
+double rel_of(const pn_handle* h, double rr) {
+    return h->q_norm2 > 0.0 ? std::sqrt(rr / h->q_norm2) : std::sqrt(rr);
+}
+
+template <typename T>
+int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
+    pn_handle* h = c.h;
+    const int64_t n = h->n_elems;
+    int rc = ensure_work(h, size_t(4) * n * sizeof(T));
+    if (rc != PN_OK) return rc;
+    T* r = (T*)h->d_work;
+    T* s = r + n;
+    T* p = s + n;
+    T* q = p + n;
+    const int dt = sizeof(T) == 4 ? PN_F32 : PN_F64;
+    const double es = sizeof(T);
+    const int nb = nb_vec();
+    double* S = h->d_scalars;
+    auto residual = [&]() {
+        c.pb();
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r, dt, h->d_partials, c.s), "cgls: residual");
+        c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, es, false));
+        c.pb();
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, S + S_RR, c.s), "cgls: reduce");
+        c.pe(PN_PROF_SCALAR, 0.0);
+    };
+    auto op = [&](int mode, const T* in, T* out) {
+        c.pb();
+        c.lk(pn::launch_op(h, mode, in, out, dt, nullptr, c.s), "cgls: operator");
+        c.pe(PN_PROF_APPLY, c.ob(mode, es, false));
+    };
+    auto dot = [&](const T* a, double* out) {
+        c.pb();
+        c.lk2(pn::launch_dot(h, a, a, n, dt, out, c.s), "cgls: dot");
+        c.pe(PN_PROF_DOT, c.vb(1, es));
+    };
+    // r = Q - A x ; s = A^T r ; p = s ; gamma = ||s||^2
+    residual();
+    op(pn::OP_APPLY_T, r, s);
+    dot(s, S + S_G0);
+    c.pb();
+    k_copy<T><<<nb, 256, 0, c.s>>>(n, p, s);
+    c.launched("cgls: copy");
+    c.pe(PN_PROF_VECTOR, c.vb(2, es));
+    double rr = 0.0;
+    if (!c.read(S_RR, 1, &rr)) return c.rc;
+    double rel = rel_of(h, rr);
+    int it = 0, gcur = S_G0, gnew = S_G1;
+    const int every = o.check_every > 0 ? o.check_every : 10;
+    while (c.rc == PN_OK && std::isfinite(rel) && rel > o.tol && it < o.max_iter) {
+        op(pn::OP_APPLY, p, q);
+        dot(q, S + S_QQ);
+        c.pb();
+        k_cgls_xr<T><<<h->red_blocks, 256, 0, c.s>>>(n, x, r, p, q, S, gcur, h->d_partials);
+        c.launched("cgls: update");
+        c.pe(PN_PROF_VECTOR, c.vb(6, es));
+        c.pb();
+        c.lk(pn::launch_reduce(h->d_partials, h->red_blocks, 1, S + S_RR, c.s), "cgls: reduce");
+        c.pe(PN_PROF_SCALAR, 0.0);
+        op(pn::OP_APPLY_T, r, s);
+        dot(s, S + gnew);
+        c.pb();
+        k_cgls_p<T><<<nb, 256, 0, c.s>>>(n, p, s, S, gcur, gnew);
+        c.launched("cgls: direction");
+        c.pe(PN_PROF_VECTOR, c.vb(3, es));
+        std::swap(gcur, gnew);
+        ++it;
+        if (it % every == 0 || it >= o.max_iter) {
+            double v[2];
+            if (!c.read(S_RR, 2, v)) break;
+            rel = rel_of(h, v[0]);
+            if (v[1] == 0.0 && rel > o.tol) {
+                st.iterations = it;
+                st.rel_residual = rel;
+                return pn_fail(h, PN_ERR_BREAKDOWN, "cgls: ||A p|| = 0");
+            }
+        }
+    }
+    if (c.rc != PN_OK) return c.rc;
+    // final residual in the solve's own precision (FP64 accumulation)
+    residual();
+    if (!c.read(S_RR, 1, &rr)) return c.rc;
+    st.iterations = it;
+    st.rel_residual = rel_of(h, rr);
+    if (!std::isfinite(st.rel_residual)) return pn_fail(h, PN_ERR_NONFINITE, "cgls: non-finite residual");
+    if (st.rel_residual > o.tol) return pn_fail(h, PN_ERR_NOT_CONVERGED, "cgls: max_iter reached");
+    return PN_OK;
+}
+
+// Restarted GMRES(m) for A x = b (b = Q if bvec is null).  tol is relative to
+// ||b|| (bnorm2 = ||b||^2).  Adds the inner iterations to *iters.
+template <typename T>
+int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max_iter, int check_every,
+          int* iters, double* rel_out) {
+    pn_handle* h = c.h;
+    const int64_t n = h->n_elems;
+    const int dt = sizeof(T) == 4 ? PN_F32 : PN_F64;
+    const double es = sizeof(T);
+    const int nb = nb_vec();
+    double* S = h->d_scalars;
+    // workspace: V (m+1 vectors), then FP64 H ((m+1) x m), cs, sn, g, y, add
+    const size_t vbytes = size_t(m + 1) * n * sizeof(T);
+    const int ldh = m + 1;
+    const size_t dcount = size_t(ldh) * m + 4 * size_t(m + 1) + 16 * size_t(m + 1);
+    int rc = ensure_work(h, vbytes + dcount * sizeof(double) + 256);
+    if (rc != PN_OK) return rc;
+    T* V = (T*)h->d_work;
+    double* H = (double*)((char*)h->d_work + ((vbytes + 255) / 256) * 256);
+    double* cs = H + size_t(ldh) * m;
+    double* sn = cs + (m + 1);
+    double* g = sn + (m + 1);
+    double* y = g + (m + 1);
+    double* add = y + (m + 1);
+    const double bnorm = std::sqrt(bnorm2);
+    const double target = tol * (bnorm > 0.0 ? bnorm : 1.0);
+    int total = 0;
+    double res = 0.0;
+    const int every = check_every > 0 ? check_every : 1;
+    for (;;) {
+        // r = b - A x into V_0, beta = ||r||
+        c.pb();
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, V, dt, h->d_partials, c.s, bvec), "gmres: residual");
+        c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, es, bvec != nullptr));
+        c.pb();
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, S + S_BETA2, c.s), "gmres: reduce");
+        c.pe(PN_PROF_SCALAR, 0.0);
+        double b2 = 0.0;
+        if (!c.read(S_BETA2, 1, &b2)) return c.rc;
+        res = std::sqrt(b2);
+        if (!std::isfinite(res)) return pn_fail(h, PN_ERR_NONFINITE, "gmres: non-finite residual");
+        if (res <= target || total >= max_iter) break;
+        c.pb();
+        k_gm_init<<<1, 32, 0, c.s>>>(g, m, S);
+        c.launched("gmres: init");
+        c.pe(PN_PROF_SCALAR, 0.0);
+        c.pb();
+        k_scale_invnorm<T><<<nb, 256, 0, c.s>>>(n, V, S, S_BETA2);
+        c.launched("gmres: init");
+        c.pe(PN_PROF_VECTOR, c.vb(2, es));
+        int j = 0;
+        for (; j < m && total < max_iter; ++j) {
+            T* w = V + int64_t(j + 1) * n;
+            c.pb();
+            c.lk(pn::launch_op(h, pn::OP_APPLY, V + int64_t(j) * n, w, dt, nullptr, c.s), "gmres: A v");
+            c.pe(PN_PROF_APPLY, c.ob(pn::OP_APPLY, es, false));
+            // classical Gram-Schmidt, twice
+            for (int pass = 0; pass < 2; ++pass) {
+                double* hc = pass == 0 ? H + int64_t(j) * ldh : add;
+                for (int i0 = 0; i0 <= j; i0 += PN_MAX_MDOT) {
+                    const int nv = std::min(PN_MAX_MDOT, j + 1 - i0);
+                    c.pb();
+                    k_mdot<T, PN_MAX_MDOT><<<h->red_blocks, 256, 0, c.s>>>(n, V + int64_t(i0) * n, n, nv, w,
+                                                                           h->d_partials);
+                    c.launched("gmres: mdot");
+                    c.pe(PN_PROF_MDOT, c.vb(nv + 1, es));
+                    c.pb();
+                    c.lk(pn::launch_reduce(h->d_partials, h->red_blocks, nv, hc + i0, c.s), "gmres: reduce");
+                    c.pe(PN_PROF_SCALAR, 0.0);
+                    c.pb();
+                    k_maxpy<T, PN_MAX_MDOT><<<nb, 256, 0, c.s>>>(n, w, V + int64_t(i0) * n, n, nv, hc + i0, -1.0);
+                    c.launched("gmres: maxpy");
+                    c.pe(PN_PROF_MAXPY, c.vb(nv + 2, es));
+                }
+            }
+            c.pb();
+            c.lk2(pn::launch_dot(h, w, w, n, dt, S + S_NRM2, c.s), "gmres: norm");
+            c.pe(PN_PROF_DOT, c.vb(1, es));
+            c.pb();
+            k_givens<<<1, 32, 0, c.s>>>(H, ldh, add, cs, sn, g, j, S);
+            c.launched("gmres: givens");
+            c.pe(PN_PROF_SCALAR, 0.0);
+            c.pb();
+            k_scale_by<T><<<nb, 256, 0, c.s>>>(n, w, S, S_SCALE);
+            c.launched("gmres: scale");
+            c.pe(PN_PROF_VECTOR, c.vb(2, es));
+            ++total;
+            if ((j + 1) % every == 0 || j + 1 == m || total >= max_iter) {
+                double r1 = 0.0;
+                if (!c.read(S_RES, 1, &r1)) return c.rc;
+                if (!std::isfinite(r1)) return pn_fail(h, PN_ERR_NONFINITE, "gmres: non-finite Hessenberg");
+                if (r1 <= target) {
+                    ++j;
+                    break;
+                }
+            }
+        }
+        // x += V y
+        c.pb();
+        k_gm_backsolve<<<1, 32, 0, c.s>>>(H, ldh, g, y, j);
+        c.launched("gmres: backsolve");
+        c.pe(PN_PROF_SCALAR, 0.0);
+        for (int i0 = 0; i0 < j; i0 += PN_MAX_MDOT) {
+            const int nv = std::min(PN_MAX_MDOT, j - i0);
+            c.pb();
+            k_maxpy<T, PN_MAX_MDOT><<<nb, 256, 0, c.s>>>(n, x, V + int64_t(i0) * n, n, nv, y + i0, 1.0);
+            c.launched("gmres: update");
+            c.pe(PN_PROF_MAXPY, c.vb(nv + 2, es));
+        }
+        if (c.rc != PN_OK) return c.rc;
+    }
+    *iters += total;
+    *rel_out = bnorm > 0.0 ? res / bnorm : res;
+    return c.rc;
+}
+
+int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st) {
+    pn_handle* h = c.h;
+    const int64_t n = h->n_elems;
+    // r64 and the FP32 rhs / correction live outside the GMRES workspace
+    double* r64 = nullptr;
+    float* r32 = nullptr;
+    float* d32 = nullptr;
+    if (cudaMalloc(&r64, n * sizeof(double)) != cudaSuccess || cudaMalloc(&r32, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&d32, n * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        if (r64) cudaFree(r64);
+        if (r32) cudaFree(r32);
+        return pn_fail(h, PN_ERR_ALLOC, "ir: cannot allocate refinement vectors");
+    }
+    const int nb = nb_vec();
+    double* S = h->d_scalars;
+    int outer = 0, inner = 0;
+    double rel = 0.0;
+    int rc = PN_OK;
+    for (;;) {
+        c.pb();
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r64, PN_F64, h->d_partials, c.s), "ir: residual");
+        c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, 8.0, false));
+        c.pb();
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, S + S_RR, c.s), "ir: reduce");
+        c.pe(PN_PROF_SCALAR, 0.0);
+        double rr = 0.0;
+        if (!c.read(S_RR, 1, &rr)) break;
+        rel = rel_of(h, rr);
+        if (!std::isfinite(rel)) {
+            rc = pn_fail(h, PN_ERR_NONFINITE, "ir: non-finite residual");
+            break;
+        }
+        if (rel <= o.tol || outer >= o.max_outer || inner >= o.max_iter) break;
+        c.pb();
+        k_to_f32_scaled<<<nb, 256, 0, c.s>>>(n, r32, r64, S, S_RR);
+        k_zero<float><<<nb, 256, 0, c.s>>>(n, d32);
+        c.launched("ir: convert", 2);
+        c.pe(PN_PROF_VECTOR, c.vb(8.0 / 4.0 + 1.0 + 1.0, 4.0));
+        // keep ||r|| for the correction: copy S_RR aside (GMRES reuses slots)
+        cudaMemcpyAsync(S + S_MAXPY, S + S_RR, sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+        double inner_rel = 0.0;
+        // inner tolerance: relative reduction, but not beyond what the outer target needs
+        double itol = o.inner_tol;
+        if (rel > 0.0 && o.tol / rel > itol) itol = std::min(0.5, o.tol / rel);
+        rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel);
+        if (rc != PN_OK) break;
+        c.pb();
+        k_add_f32_scaled<<<nb, 256, 0, c.s>>>(n, x, d32, S, S_MAXPY);
+        c.launched("ir: update");
+        c.pe(PN_PROF_VECTOR, c.vb(2.0 * 8.0 + 4.0, 1.0));
+        ++outer;
+    }
+    if (rc == PN_OK) rc = c.rc;
+    cudaFree(r64);
+    cudaFree(r32);
+    cudaFree(d32);
+    st.iterations = inner;
+    st.outer_iterations = outer;
+    st.rel_residual = rel;
+    if (rc == PN_OK && rel > o.tol) rc = pn_fail(h, PN_ERR_NOT_CONVERGED, "ir: iteration cap reached");
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_solve_stats* stats, void* stream) {
+    if (!h) return PN_ERR_ARG;
+    if (!u || !opts) return pn_fail(h, PN_ERR_ARG, "pn_solve: NULL argument");
+    if (reinterpret_cast<uintptr_t>(u) & 15u) return pn_fail(h, PN_ERR_ARG, "pn_solve: u must be 16-byte aligned");
+    const pn_solve_opts& o = *opts;
+    if (!(o.tol > 0.0) || o.max_iter < 0) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad tol or max_iter");
+    if (o.solver != PN_SOLVER_CGLS && o.solver != PN_SOLVER_GMRES && o.solver != PN_SOLVER_IR_GMRES)
+        return pn_fail(h, PN_ERR_ARG, "pn_solve: unknown solver");
+    if (o.solver != PN_SOLVER_IR_GMRES && o.precision != PN_F32 && o.precision != PN_F64)
+        return pn_fail(h, PN_ERR_ARG, "pn_solve: bad precision");
+    if (o.solver != PN_SOLVER_CGLS && (o.restart < 1 || o.restart > 200))
+        return pn_fail(h, PN_ERR_ARG, "pn_solve: restart must be in [1, 200]");
+    pn_solve_stats st{};
+    Ctx c{h, (cudaStream_t)stream};
+    pn_prof_reset(h, o.profile != 0);
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc;
+    if (o.solver == PN_SOLVER_CGLS) {
+        rc = o.precision == PN_F32 ? cgls<float>(c, (float*)u, o, st) : cgls<double>(c, (double*)u, o, st);
+    } else if (o.solver == PN_SOLVER_GMRES) {
+        int it = 0;
+        double rel = 0.0;
+        if (o.precision == PN_F32)
+            rc = gmres<float>(c, (float*)u, nullptr, h->q_norm2, o.tol, o.restart, o.max_iter, o.check_every, &it, &rel);
+        else
+            rc = gmres<double>(c, (double*)u, nullptr, h->q_norm2, o.tol, o.restart, o.max_iter, o.check_every, &it, &rel);
+        st.iterations = it;
+        st.rel_residual = rel;
+        if (rc == PN_OK && rel > o.tol) rc = pn_fail(h, PN_ERR_NOT_CONVERGED, "gmres: max_iter reached");
+    } else {
+        rc = ir_gmres(c, (double*)u, o, st);
+    }
+    if (cudaStreamSynchronize(c.s) == cudaSuccess) pn_prof_drain(h);
+    h->prof_on = false;
+    const auto t1 = std::chrono::steady_clock::now();
+    st.seconds = std::chrono::duration<double>(t1 - t0).count();
+    st.status = rc;
+    st.launches = c.launches;
+    if (stats) *stats = st;
+    return rc;
+}

@@ -1,0 +1,371 @@
+"""Python binding of libpn_gb300.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only
+converts arguments (numpy arrays or torch tensors) to the C ABI declared in
+include/pn_gb300.h, allocates caller-owned vectors with torch, and slices the
+padded vector layout into per-coefficient views.  There is no CPU fallback:
+if the library is missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpn_gb300.so")
+
+PN_OK = 0
+PN_ERR_ARG = -1
+PN_ERR_ALLOC = -2
+PN_ERR_CUDA = -3
+PN_ERR_NOT_CONVERGED = -4
+PN_ERR_BREAKDOWN = -5
+PN_ERR_NONFINITE = -6
+PN_ERR_UNSUPPORTED = -8
+PN_F32, PN_F64 = 0, 1
+PN_BC_VACUUM = 0
+PN_Q_CENTRE_00, PN_Q_CENTRE_MOMENTS = 0, 1
+SOLVERS = {"cgls": 0, "gmres": 1, "ir": 2}
+
+ERROR_NAMES = {
+    PN_ERR_ARG: "PN_ERR_ARG", PN_ERR_ALLOC: "PN_ERR_ALLOC", PN_ERR_CUDA: "PN_ERR_CUDA",
+    PN_ERR_NOT_CONVERGED: "PN_ERR_NOT_CONVERGED", PN_ERR_BREAKDOWN: "PN_ERR_BREAKDOWN",
+    PN_ERR_NONFINITE: "PN_ERR_NONFINITE", PN_ERR_UNSUPPORTED: "PN_ERR_UNSUPPORTED",
+}
+
+# Every symbol the header declares (checked by the CPU test-suite).
+EXPORTS = ["pn_create", "pn_destroy", "pn_get_layout", "pn_last_error", "pn_apply", "pn_apply_t",
+           "pn_residual", "pn_dot", "pn_axpby", "pn_default_solve_opts", "pn_solve", "pn_profile_get"]
+PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar"]
+
+
+class PnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Medium(ctypes.Structure):
+    _fields_ = [("sigma_t", ctypes.c_void_p), ("albedo", ctypes.c_void_p), ("albedo_const", ctypes.c_double),
+                ("g", ctypes.c_double), ("Q", ctypes.c_void_p), ("q_mode", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("on_device", ctypes.c_int), ("sigma_t_min", ctypes.c_double)]
+
+
+class _Layout(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int), ("R", ctypes.c_int), ("pitch_x", ctypes.c_int64),
+                ("pitch_y", ctypes.c_int64), ("plane_stride", ctypes.c_int64), ("n_elems", ctypes.c_int64),
+                ("n_active", ctypes.c_int64), ("plane_k", ctypes.c_int * 64), ("plane_class", ctypes.c_int * 64)]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class _SolveStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1807_00410_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "pn_create": (i, [ctypes.POINTER(vp), i, i, ctypes.POINTER(_Medium), i, vp]),
+        "pn_destroy": (i, [vp]),
+        "pn_get_layout": (i, [vp, ctypes.POINTER(_Layout)]),
+        "pn_last_error": (ctypes.c_char_p, [vp]),
+        "pn_apply": (i, [vp, vp, vp, i, vp]),
+        "pn_apply_t": (i, [vp, vp, vp, i, vp]),
+        "pn_residual": (i, [vp, vp, vp, ctypes.POINTER(d), i, vp]),
+        "pn_dot": (i, [vp, vp, vp, ctypes.POINTER(d), i, vp]),
+        "pn_axpby": (i, [vp, d, vp, d, vp, i, vp]),
+        "pn_default_solve_opts": (None, [ctypes.POINTER(_SolveOpts)]),
+        "pn_solve": (i, [vp, vp, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveStats), vp]),
+        "pn_profile_get": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _ = i64
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Layout:
+    N: int
+    K: int
+    R: int
+    pitch_x: int
+    pitch_y: int
+    plane_stride: int
+    n_elems: int
+    n_active: int
+    plane_k: list
+    plane_class: list
+
+    def plane_of_k(self, k: int) -> int:
+        return self.plane_k.index(k)
+
+    def active_shape(self, p: int):
+        c = self.plane_class[p]
+        R = self.R
+        return (R + ((c >> 2) & 1), R + ((c >> 1) & 1), R + (c & 1))  # (z, y, x)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(a) -> bool:
+    try:
+        import torch
+        return isinstance(a, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return PN_F32
+    if t.dtype == torch.float64:
+        return PN_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class System:
+    """One P_N system (order N, R^3 cells, medium) living on the current GPU.
+
+    sigma_t, albedo (array or scalar) and Q are voxel-centre fields indexed
+    [z][y][x]; Q is either an (R, R, R) field of Q^{0,0} or a (K, R, R, R)
+    array of centre moments.  numpy inputs are passed as host arrays (the
+    library copies them); torch CUDA tensors are passed as device pointers.
+    """
+
+    def __init__(self, N: int, R: int, sigma_t, albedo, g: float, Q=None, sigma_t_min: float = 0.0,
+                 stream=None):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        keep = []
+
+        def arr(a):
+            if a is None:
+                return None, None, 0
+            if _is_torch(a):
+                t = a.detach().contiguous()
+                if t.dtype not in (_torch().float32, _torch().float64):
+                    t = t.double()
+                keep.append(t)
+                return ctypes.c_void_p(t.data_ptr()), _dtype_code(t), 1 if t.is_cuda else 0
+            n = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+            keep.append(n)
+            return ctypes.c_void_p(n.ctypes.data), PN_F64, 0
+
+        st_p, st_dt, st_dev = arr(sigma_t)
+        m = _Medium()
+        m.sigma_t = st_p
+        if np.isscalar(albedo):
+            m.albedo = None
+            m.albedo_const = float(albedo)
+        else:
+            al = albedo
+            if _is_torch(sigma_t) and not _is_torch(al):
+                al = _torch().as_tensor(np.asarray(al), dtype=keep[0].dtype, device=keep[0].device)
+            if not _is_torch(sigma_t) and _is_torch(al):
+                al = al.detach().cpu().double().numpy()
+            if _is_torch(al):
+                al = al.to(keep[0].dtype)
+            al_p, _, _ = arr(al)
+            m.albedo = al_p
+        m.g = float(g)
+        K = (N + 1) ** 2
+        if Q is not None:
+            q = Q
+            if _is_torch(sigma_t) and not _is_torch(q):
+                q = _torch().as_tensor(np.asarray(q), dtype=keep[0].dtype, device=keep[0].device)
+            if not _is_torch(sigma_t) and _is_torch(q):
+                q = q.detach().cpu().double().numpy()
+            if _is_torch(q):
+                q = q.to(keep[0].dtype)
+            shape = tuple(q.shape)
+            if shape == (R, R, R):
+                m.q_mode = PN_Q_CENTRE_00
+            elif shape == (K, R, R, R):
+                m.q_mode = PN_Q_CENTRE_MOMENTS
+            else:
+                raise ValueError(f"Q must have shape {(R, R, R)} or {(K, R, R, R)}, got {shape}")
+            q_p, _, _ = arr(q)
+            m.Q = q_p
+        m.dtype = st_dt
+        m.on_device = st_dev
+        m.sigma_t_min = float(sigma_t_min)
+        rc = self._lib.pn_create(ctypes.byref(self._h), int(N), int(R), ctypes.byref(m), PN_BC_VACUUM,
+                                 _stream_ptr(stream) if (st_dev or stream is not None) else ctypes.c_void_p(0))
+        if rc != PN_OK:
+            raise PnError(rc, self._lib.pn_last_error(None).decode())
+        lay = _Layout()
+        self._check(self._lib.pn_get_layout(self._h, ctypes.byref(lay)))
+        self.layout = Layout(lay.N, lay.K, lay.R, lay.pitch_x, lay.pitch_y, lay.plane_stride, lay.n_elems,
+                             lay.n_active, list(lay.plane_k)[:lay.K], list(lay.plane_class)[:lay.K])
+        self.N, self.R, self.K = N, R, K
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, rc):
+        if rc != PN_OK:
+            raise PnError(rc, self._lib.pn_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.pn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _vec(self, t):
+        if not _is_torch(t) or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("expected a contiguous CUDA tensor")
+        if t.numel() != self.layout.n_elems:
+            raise ValueError(f"vector has {t.numel()} elements, layout needs {self.layout.n_elems}")
+        return ctypes.c_void_p(t.data_ptr()), _dtype_code(t)
+
+    def zeros(self, dtype=None, device="cuda"):
+        torch = _torch()
+        return torch.zeros(self.layout.n_elems, dtype=dtype or torch.float32, device=device)
+
+    # -- operator and vector calls ---------------------------------------------
+    def apply(self, x, y, stream=None):
+        """y = A x."""
+        xp, dt = self._vec(x)
+        yp, dt2 = self._vec(y)
+        if dt != dt2:
+            raise TypeError("x and y must share a dtype")
+        self._check(self._lib.pn_apply(self._h, xp, yp, dt, _stream_ptr(stream)))
+        return y
+
+    def apply_t(self, x, y, stream=None):
+        """y = A^T x."""
+        xp, dt = self._vec(x)
+        yp, dt2 = self._vec(y)
+        if dt != dt2:
+            raise TypeError("x and y must share a dtype")
+        self._check(self._lib.pn_apply_t(self._h, xp, yp, dt, _stream_ptr(stream)))
+        return y
+
+    def residual(self, x, r, stream=None) -> float:
+        """r = Q - A x; returns ||r|| / ||Q|| (FP64 accumulation)."""
+        xp, dt = self._vec(x)
+        rp, dt2 = self._vec(r)
+        if dt != dt2:
+            raise TypeError("x and r must share a dtype")
+        out = ctypes.c_double()
+        self._check(self._lib.pn_residual(self._h, xp, rp, ctypes.byref(out), dt, _stream_ptr(stream)))
+        return out.value
+
+    def dot(self, x, y, stream=None) -> float:
+        xp, dt = self._vec(x)
+        yp, _ = self._vec(y)
+        out = ctypes.c_double()
+        self._check(self._lib.pn_dot(self._h, xp, yp, ctypes.byref(out), dt, _stream_ptr(stream)))
+        return out.value
+
+    def axpby(self, alpha, x, beta, y, stream=None):
+        xp, dt = self._vec(x)
+        yp, _ = self._vec(y)
+        self._check(self._lib.pn_axpby(self._h, float(alpha), xp, float(beta), yp, dt, _stream_ptr(stream)))
+        return y
+
+    def solve(self, u, solver: str = "cgls", tol: float = 1e-6, max_iter: int = 100000, restart: int = 60,
+              inner_tol: float = 1e-2, max_outer: int = 50, check_every: int = 10, stream=None,
+              raise_on_error: bool = True, profile: bool = False) -> dict:
+        """Solve A u = Q in place (u is the initial guess).  Returns the stats."""
+        up, dt = self._vec(u)
+        o = _SolveOpts()
+        self._lib.pn_default_solve_opts(ctypes.byref(o))
+        o.solver = SOLVERS[solver]
+        o.precision = dt
+        if solver == "ir" and dt != PN_F64:
+            raise TypeError("iterative refinement keeps u in FP64")
+        o.tol, o.max_iter, o.restart = float(tol), int(max_iter), int(restart)
+        o.inner_tol, o.max_outer, o.check_every = float(inner_tol), int(max_outer), int(check_every)
+        o.profile = 1 if profile else 0
+        st = _SolveStats()
+        rc = self._lib.pn_solve(self._h, up, ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
+        stats = {"status": rc, "iterations": st.iterations, "outer_iterations": st.outer_iterations,
+                 "rel_residual": st.rel_residual, "seconds": st.seconds, "launches": st.launches}
+        if rc != PN_OK and raise_on_error:
+            raise PnError(rc, self._lib.pn_last_error(self._h).decode() + f" (stats {stats})")
+        return stats
+
+    def profile(self) -> dict:
+        """Per-kernel-class totals of the last profiled solve:
+        {kind: {"ms": ..., "launches": ..., "bytes": ...}}."""
+        out = {}
+        for i, name in enumerate(PROFILE_KINDS):
+            ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+            self._check(self._lib.pn_profile_get(self._h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
+        return out
+
+    # -- layout marshalling -------------------------------------------------
+    def to_planes(self, vec):
+        """Padded vector -> list of K numpy arrays in coefficient order k,
+        each the active (z, y, x) region of its staggered grid."""
+        lay = self.layout
+        v = vec.detach().cpu().numpy() if _is_torch(vec) else np.asarray(vec)
+        R = lay.R
+        out = [None] * lay.K
+        for p in range(lay.K):
+            box = v[p * lay.plane_stride: p * lay.plane_stride + lay.pitch_y * (R + 1)]
+            box = box.reshape(R + 1, R + 1, lay.pitch_x)
+            nz, ny, nx = lay.active_shape(p)
+            out[lay.plane_k[p]] = box[:nz, :ny, :nx].copy()
+        return out
+
+    def from_planes(self, planes, dtype=None, device="cuda"):
+        """List of K per-coefficient arrays (coefficient order) -> padded vector."""
+        torch = _torch()
+        lay = self.layout
+        R = lay.R
+        host = np.zeros(lay.n_elems, dtype=np.float64)
+        for p in range(lay.K):
+            nz, ny, nx = lay.active_shape(p)
+            box = host[p * lay.plane_stride: p * lay.plane_stride + lay.pitch_y * (R + 1)].reshape(
+                R + 1, R + 1, lay.pitch_x)
+            box[:nz, :ny, :nx] = np.asarray(planes[lay.plane_k[p]], dtype=np.float64).reshape(nz, ny, nx)
+        return torch.as_tensor(host, dtype=dtype or torch.float32).to(device)

@@ -1,0 +1,291 @@
+"""GPU parity of the CUDA library against the FP64 CPU oracle.
+
+Every test calls the C ABI (through the ctypes binding) and compares element
+by element with the oracle on the same seeded inputs.  Tolerances:
+
+* FP64 apply / transpose / residual: max |y_gpu - y_ref| <= 1e-12 * max(|A| |x|)
+  and ||y_gpu - y_ref|| / ||y_ref|| <= 1e-12;
+* FP32: the same with 1e-5 (inputs rounded to FP32 first, reference in FP64);
+* solves: the oracle's own FP64 residual ||Q - A u|| / ||Q|| of the GPU
+  solution, and the L2 error of L^{0,0} against the oracle's direct solution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import pn_inputs
+from oracle import pn as opn
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1807_00410_gb300 import build
+    build.build()
+
+
+def _system(N, R, seed, g=0.35, q_moments=False, albedo_field=True, sigma_t_min=0.0, lo=0.5, hi=20.0):
+    from paper_1807_00410_gb300 import System
+    st = lo + (hi - lo) * pn_inputs.value_noise_fbm(R, seed, base=2)
+    al = pn_inputs.random_field((R, R, R), seed + 1, 0.3, 0.97) if albedo_field else 0.9
+    K = (N + 1) ** 2
+    Q = pn_inputs.random_field((K, R, R, R) if q_moments else (R, R, R), seed + 2, -1.0, 1.0)
+    med = opn.Medium(st, al, g, Q, sigma_t_min)
+    gpu = System(N, R, st, al, g, Q, sigma_t_min=sigma_t_min)
+    return med, gpu
+
+
+def _rand_planes(layout_o, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [rng.uniform(-1, 1, s) for s in layout_o.shapes]
+
+
+def _compare(y_gpu, y_ref, scale, tol):
+    err = np.max(np.abs(y_gpu - y_ref))
+    assert err <= tol * scale, f"max err {err:.3e} > {tol:.0e} * {scale:.3e}"
+    rel = np.linalg.norm(y_gpu - y_ref) / max(np.linalg.norm(y_ref), 1e-300)
+    assert rel <= tol, f"relative L2 {rel:.3e}"
+
+
+CASES = [(0, 5), (1, 2), (1, 9), (3, 5), (3, 17), (5, 9), (7, 3), (7, 6)]
+
+
+@pytest.mark.parametrize("N,R", CASES)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_apply_transpose_residual_match_oracle(N, R, dtype):
+    med, gpu = _system(N, R, 10 * N + R, q_moments=(N % 2 == 1))
+    S = opn.assemble(N, R, med)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    planes = _rand_planes(S.layout, 7 * R + N)
+    if dtype == "f32":
+        planes = [p.astype(np.float32).astype(np.float64) for p in planes]
+    u = S.layout.join(planes)
+    x = gpu.from_planes(planes, dtype=tdt)
+    y = gpu.zeros(tdt)
+    absA = abs(S.A)
+    scale = np.max(absA @ np.abs(u))
+    gpu.apply(x, y)
+    _compare(S.layout.join(gpu.to_planes(y)), S.A @ u, scale, tol)
+    gpu.apply_t(x, y)
+    _compare(S.layout.join(gpu.to_planes(y)), S.A.T @ u, scale, tol)
+    rel = gpu.residual(x, y)
+    r_ref = S.b - S.A @ u
+    _compare(S.layout.join(gpu.to_planes(y)), r_ref, scale + np.max(np.abs(S.b)), tol)
+    assert abs(rel - np.linalg.norm(r_ref) / np.linalg.norm(S.b)) <= 10 * tol * rel
+    gpu.close()
+
+
+def test_inactive_slots_ignored_and_zeroed():
+    N, R = 3, 6
+    med, gpu = _system(N, R, 3)
+    S = opn.assemble(N, R, med)
+    planes = _rand_planes(S.layout, 1)
+    x = gpu.from_planes(planes, dtype=torch.float64)
+    y_clean = gpu.zeros(torch.float64)
+    gpu.apply(x, y_clean)
+    # poison every padding slot of x with NaN
+    mask = gpu.from_planes([np.ones(s) for s in S.layout.shapes], dtype=torch.float64) == 0
+    x2 = x.clone()
+    x2[mask] = float("nan")
+    y = torch.full_like(x, 7.0)
+    gpu.apply(x2, y)
+    assert torch.isfinite(y).all()
+    assert torch.equal(y, y_clean)
+    assert (y[mask] == 0).all()
+    gpu.close()
+
+
+def test_fp64_apply_and_dot_are_deterministic():
+    med, gpu = _system(5, 9, 4)
+    S = opn.assemble(5, 9, med)
+    x = gpu.from_planes(_rand_planes(S.layout, 2), dtype=torch.float64)
+    y1, y2 = gpu.zeros(torch.float64), gpu.zeros(torch.float64)
+    gpu.apply(x, y1)
+    gpu.apply(x, y2)
+    assert torch.equal(y1, y2)
+    assert gpu.dot(x, y1) == gpu.dot(x, y1)
+    gpu.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_dot_and_axpby(dtype):
+    med, gpu = _system(3, 7, 5)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    g = torch.Generator(device="cpu").manual_seed(0)
+    a = torch.rand(gpu.layout.n_elems, generator=g, dtype=torch.float64).to(tdt)
+    b = torch.rand(gpu.layout.n_elems, generator=g, dtype=torch.float64).to(tdt)
+    ref = float(np.dot(a.double().numpy(), b.double().numpy()))
+    d = gpu.dot(a.cuda(), b.cuda())
+    assert abs(d - ref) <= (1e-13 if dtype == "f64" else 1e-6) * abs(ref)
+    y = b.cuda().clone()
+    gpu.axpby(2.0, a.cuda(), -0.5, y)
+    np.testing.assert_allclose(y.cpu().double().numpy(), 2.0 * a.double().numpy() - 0.5 * b.double().numpy(),
+                               rtol=1e-6 if dtype == "f32" else 1e-15, atol=1e-7 if dtype == "f32" else 1e-15)
+    gpu.close()
+
+
+# --- solves ---------------------------------------------------------------------
+
+def _p1_centre_problem():
+    p = pn_inputs.p1_16_homogeneous()
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00)
+    return p, med
+
+
+@pytest.mark.parametrize("solver", ["cgls", "gmres"])
+def test_p1_point_source_solves_to_1e10_in_fp64(solver):
+    """P1, 16^3, sigma_t = 10, albedo 0.9, isotropic, Q = 1 at the centre voxel,
+    FP64 on the GPU to rel. residual 1e-10; matches the oracle's direct solve."""
+    from paper_1807_00410_gb300 import System
+    p, med = _p1_centre_problem()
+    S = opn.assemble(p.N, p.R, med)
+    u_ref = opn.solve_direct(S)
+    gpu = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver=solver, tol=1e-10, max_iter=20000, restart=80)
+    assert st["rel_residual"] <= 1e-10
+    uo = S.layout.join(gpu.to_planes(u))
+    assert opn.relative_residual(S.A, S.b, uo) <= 1.5e-10
+    err = np.linalg.norm(uo - u_ref) / np.linalg.norm(u_ref)
+    assert err <= 1e-8, err
+    gpu.close()
+
+
+def test_ir_gmres_fp32_inner_reaches_1e6_and_oracle_l00():
+    """FP32 GMRES inner solves with FP64 iterative refinement: the oracle's FP64
+    residual is <= 1e-6 and L^{0,0} is within 1e-5 (relative L2) of the oracle's
+    direct solution."""
+    N, R = 3, 10
+    p = pn_inputs.fbm_point(N, R, 3, 0.5, 40.0, 0.95, 0.3)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00)
+    S = opn.assemble(N, R, med)
+    u_ref = opn.solve_direct(S)
+    from paper_1807_00410_gb300 import System
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver="ir", tol=1e-6, max_iter=20000, restart=40)
+    assert st["rel_residual"] <= 1e-6 and st["outer_iterations"] >= 1
+    uo = S.layout.join(gpu.to_planes(u))
+    assert opn.relative_residual(S.A, S.b, uo) <= 1.0001e-6
+    L00, L00_ref = gpu.to_planes(u)[0], S.layout.split(u_ref)[0]
+    assert np.linalg.norm(L00 - L00_ref) / np.linalg.norm(L00_ref) <= 1e-5
+    gpu.close()
+
+
+def test_zero_source_solves_immediately():
+    from paper_1807_00410_gb300 import System
+    R = 4
+    gpu = System(1, R, np.full((R, R, R), 2.0), 0.5, 0.0, None)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver="gmres", tol=1e-8)
+    assert st["iterations"] == 0 and float(u.abs().max()) == 0.0
+    gpu.close()
+
+
+def test_cgls_fp32_reaches_moderate_tolerance():
+    N, R = 1, 10
+    med, gpu = _system(N, R, 8, albedo_field=False)
+    u = gpu.zeros(torch.float32)
+    st = gpu.solve(u, solver="cgls", tol=1e-4, max_iter=20000)
+    S = opn.assemble(N, R, med)
+    assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u))) <= 2e-4
+    assert st["iterations"] > 0
+    gpu.close()
+
+
+# --- errors ---------------------------------------------------------------------
+
+def test_argument_and_nonfinite_errors():
+    from paper_1807_00410_gb300 import PnError, System
+    from paper_1807_00410_gb300 import pn as ppn
+    R = 4
+    st = np.full((R, R, R), 2.0)
+    st[1, 1, 1] = np.nan
+    with pytest.raises(PnError) as e:
+        System(1, R, st, 0.5, 0.0, np.ones((R, R, R)))
+    assert e.value.code == ppn.PN_ERR_ARG
+    gpu = System(1, R, np.full((R, R, R), 2.0), 0.5, 0.0, np.ones((R, R, R)))
+    x = gpu.zeros(torch.float64)
+    with pytest.raises(ValueError):
+        gpu.apply(x[:-1], x[:-1].clone())
+    with pytest.raises(PnError) as e:
+        gpu.apply(x, x)
+    assert e.value.code == ppn.PN_ERR_ARG
+    x[0] = float("nan")
+    with pytest.raises(PnError) as e:
+        gpu.residual(x, gpu.zeros(torch.float64))
+    assert e.value.code == ppn.PN_ERR_NONFINITE
+    gpu.close()
+
+
+# --- full-size sampled parity ----------------------------------------------------
+
+def _sampled_rows(layout_o, n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows = []
+    for _ in range(n):
+        k = int(rng.integers(layout_o.K))
+        sh = layout_o.shapes[k]
+        rows.append((k, *[int(rng.integers(s)) for s in sh]))
+    # every boundary face / last centre of some coefficients
+    for k in range(0, layout_o.K, max(1, layout_o.K // 8)):
+        nz, ny, nx = layout_o.shapes[k]
+        rows += [(k, 0, 0, 0), (k, nz - 1, ny - 1, nx - 1), (k, nz // 2, 0, nx - 1), (k, 0, ny - 1, nx // 2)]
+    return rows
+
+
+@pytest.mark.parametrize("which", ["p5_64", "p7_256"])
+def test_full_size_fp32_apply_sampled(which):
+    """Full-size workloads in FP32, in the launch configuration the benchmark
+    times: sampled outputs against the oracle's row-by-row evaluation."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.p5_64_fbm(0) if which == "p5_64" else pn_inputs.p7_256_cloud(0)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00, p.sigma_t_min)
+    lay_o = opn.Layout(p.N, p.R)
+    gpu = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
+    lay = gpu.layout
+    rng = np.random.Generator(np.random.PCG64(11))
+    host = rng.random(lay.n_elems, dtype=np.float32) - np.float32(0.5)
+    x = torch.from_numpy(host).cuda()
+    y = torch.empty_like(x)
+    gpu.apply(x, y)
+    r = torch.empty_like(x)
+    gpu.residual(x, r)
+    torch.cuda.synchronize()
+    yh = y.cpu().numpy()
+    rh = r.cpu().numpy()
+    R = p.R
+    parts_x, parts_y, parts_r = [None] * lay.K, [None] * lay.K, [None] * lay.K
+    for q in range(lay.K):
+        nz, ny, nx = lay.active_shape(q)
+        sl = slice(q * lay.plane_stride, q * lay.plane_stride + lay.pitch_y * (R + 1))
+        k = lay.plane_k[q]
+        parts_x[k] = host[sl].reshape(R + 1, R + 1, lay.pitch_x)[:nz, :ny, :nx]
+        parts_y[k] = yh[sl].reshape(R + 1, R + 1, lay.pitch_x)[:nz, :ny, :nx]
+        parts_r[k] = rh[sl].reshape(R + 1, R + 1, lay.pitch_x)[:nz, :ny, :nx]
+    rows = _sampled_rows(lay_o, 1500, 5)
+    ref = opn.apply_rows(lay_o, med, parts_x, rows)
+    got = np.array([parts_y[k][iz, iy, ix] for (k, iz, iy, ix) in rows], dtype=np.float64)
+    scale = 10.0 * R + 100.0  # bounds sum_j |A_ij| |x_j|: <= 10 terms of |A_d|/h < R, |x| <= 1/2, sigma_t <= 100
+    assert np.max(np.abs(got - ref)) <= 1e-5 * scale
+    b = np.zeros(len(rows))
+    b[[i for i, (k, *_r) in enumerate(rows) if k == 0]] = [
+        p.Q00[iz, iy, ix] for (k, iz, iy, ix) in rows if k == 0]
+    gotr = np.array([parts_r[k][iz, iy, ix] for (k, iz, iy, ix) in rows], dtype=np.float64)
+    assert np.max(np.abs(gotr - (b - ref))) <= 1e-5 * scale
+    # padding written as zero
+    mask = np.ones(lay.n_elems, bool)
+    for q in range(lay.K):
+        nz, ny, nx = lay.active_shape(q)
+        box = mask[q * lay.plane_stride: q * lay.plane_stride + lay.pitch_y * (R + 1)].reshape(R + 1, R + 1, lay.pitch_x)
+        box[:nz, :ny, :nx] = False
+    assert not np.any(yh[mask])
+    gpu.close()
+    del x, y, r
+    torch.cuda.empty_cache()

@@ -362,3 +362,18 @@ def test_input_generators_are_seeded_and_in_range():
     c = pn_inputs.cloud_point(7, 16, 1)
     assert c.sigma_t.min() == 0.0 and c.sigma_t.max() <= 100.0
     assert (c.sigma_t == 0).mean() > 0.2
+
+
+def test_row_by_row_apply_equals_csr():
+    """The sampled-row evaluator used for full-size GPU checks agrees with the
+    assembled matrix on every row of a small grid (and for A^T)."""
+    R, N = 5, 3
+    med = _rand_medium(R, 31, g=0.45)
+    S = pn.assemble(N, R, med)
+    u = np.random.default_rng(4).standard_normal(S.layout.n)
+    parts = S.layout.split(u)
+    rows = [(k, iz, iy, ix) for k in range(S.layout.K)
+            for iz in range(S.layout.shapes[k][0]) for iy in range(S.layout.shapes[k][1])
+            for ix in range(S.layout.shapes[k][2])]
+    np.testing.assert_allclose(pn.apply_rows(S.layout, med, parts, rows), S.A @ u, atol=1e-12)
+    np.testing.assert_allclose(pn.apply_rows(S.layout, med, parts, rows, transpose=True), S.A.T @ u, atol=1e-12)
