@@ -74,6 +74,7 @@ extern "C" {
 #define PN_ERR_BREAKDOWN     -5  /* Krylov breakdown (zero norm denominator) */
 #define PN_ERR_NONFINITE     -6  /* NaN or Inf met in a residual or inner product */
 #define PN_ERR_UNSUPPORTED   -8  /* valid request this build does not implement */
+#define PN_ERR_TOO_LARGE     -9  /* request exceeds a fixed capacity of the library */
 
 #define PN_F32 0
 #define PN_F64 1
@@ -197,6 +198,30 @@ void pn_default_solve_opts(pn_solve_opts* opts);
  * Synchronises the stream.
  */
 int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_solve_stats* stats, void* stream);
+
+/*
+ * *out (host) = sum_i x_i y_i for i < n, without allocating anything.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory where they need a reduction (a host application that
+ * owns the whole device-memory budget, a real-time loop that must not take
+ * allocator locks or risk running out of memory midway, code that holds
+ * device vectors but no pn_handle).  pn_dot needs a handle, whose creation
+ * allocates; this call needs none and calls no allocator.
+ * x, y: device vectors of n elements of `dtype` (PN_F32 or PN_F64), aligned to
+ * their element size; any n in [0, PN_NOALLOC_MAX_ELEMS].  Products and sums
+ * are FP64, in a fixed order (deterministic for a given n).
+ * Scratch: a fixed 2 MiB __device__ array inside the library (one FP64
+ * partial per 8192 elements plus a result slot), held on every device that
+ * loads the library until the process exits.  The first call on a device
+ * looks up the array's device address (with that device current), so make
+ * that first call before any stream capture.  All calls share the array and
+ * each call overwrites what it uses: calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race.  Synchronises `stream`.
+ * Returns PN_OK, PN_ERR_ARG (NULL pointer, bad dtype, misalignment, n < 0),
+ * PN_ERR_TOO_LARGE (n > PN_NOALLOC_MAX_ELEMS) or PN_ERR_CUDA.
+ */
+#define PN_NOALLOC_MAX_ELEMS (1LL << 31)
+int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype, double* out, void* stream);
 
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */

@@ -25,6 +25,8 @@ PN_ERR_NOT_CONVERGED = -4
 PN_ERR_BREAKDOWN = -5
 PN_ERR_NONFINITE = -6
 PN_ERR_UNSUPPORTED = -8
+PN_ERR_TOO_LARGE = -9
+PN_NOALLOC_MAX_ELEMS = 1 << 31
 PN_F32, PN_F64 = 0, 1
 PN_BC_VACUUM = 0
 PN_Q_CENTRE_00, PN_Q_CENTRE_MOMENTS = 0, 1
@@ -34,11 +36,13 @@ ERROR_NAMES = {
     PN_ERR_ARG: "PN_ERR_ARG", PN_ERR_ALLOC: "PN_ERR_ALLOC", PN_ERR_CUDA: "PN_ERR_CUDA",
     PN_ERR_NOT_CONVERGED: "PN_ERR_NOT_CONVERGED", PN_ERR_BREAKDOWN: "PN_ERR_BREAKDOWN",
     PN_ERR_NONFINITE: "PN_ERR_NONFINITE", PN_ERR_UNSUPPORTED: "PN_ERR_UNSUPPORTED",
+    PN_ERR_TOO_LARGE: "PN_ERR_TOO_LARGE",
 }
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["pn_create", "pn_destroy", "pn_get_layout", "pn_last_error", "pn_apply", "pn_apply_t",
-           "pn_residual", "pn_dot", "pn_axpby", "pn_default_solve_opts", "pn_solve", "pn_profile_get"]
+           "pn_residual", "pn_dot", "pn_axpby", "pn_default_solve_opts", "pn_solve", "pn_profile_get",
+           "pn_dot_noalloc"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar"]
 
 
@@ -96,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_default_solve_opts": (None, [ctypes.POINTER(_SolveOpts)]),
         "pn_solve": (i, [vp, vp, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveStats), vp]),
         "pn_profile_get": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d)]),
+        "pn_dot_noalloc": (i, [vp, vp, i64, i, ctypes.POINTER(d), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -157,6 +162,23 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def dot_noalloc(x, y, stream=None) -> float:
+    """sum(x * y) over two CUDA tensors through pn_dot_noalloc, which uses a
+    fixed scratch array inside the library and allocates nothing (for callers
+    that cannot allocate device memory where they need the reduction)."""
+    lib = load_library()
+    if not (_is_torch(x) and _is_torch(y) and x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise TypeError("expected contiguous CUDA tensors")
+    if x.numel() != y.numel() or x.dtype != y.dtype:
+        raise ValueError("x and y must have the same length and dtype")
+    out = ctypes.c_double()
+    rc = lib.pn_dot_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                            _dtype_code(x), ctypes.byref(out), _stream_ptr(stream))
+    if rc != PN_OK:
+        raise PnError(rc, "pn_dot_noalloc failed")
+    return out.value
 
 
 class System:
