@@ -33,7 +33,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "P_N solve time to rel. residual 1e-6 (learned vs plain); apply GDOF/s vs HBM"
-WORKLOAD = "P5 64^3 fBm sigma_t[0.5,40] albedo 0.95 g 0.3 point source, FP32 GMRES + FP64 IR to 1e-6 (plain)"
+WORKLOAD = "P5 64^3 fBm sigma_t[0.5,40] albedo 0.95 g 0.3 point source, FP32 GMRES(20) + FP64 IR to 1e-6 (plain)"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -49,10 +49,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--ortho", choices=["cgs2", "cgs1"], default="cgs1")
     ap.add_argument("--no-apply-scan", action="store_true", help="skip the separate operator throughput scan")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time only the FP32 operator on the P_N cloud medium given by --apply-n / --apply-r")
+    ap.add_argument("--apply-n", type=int, default=7)
+    ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
 
 
@@ -269,7 +275,7 @@ def run_ours(args):
     u = sysm.zeros(torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     opts = dict(solver="ir", tol=1e-6, restart=args.restart, inner_tol=args.inner_tol, max_iter=30000,
-                check_every=5)
+                check_every=5, ortho=args.ortho)
     for _ in range(args.warmup):
         u.zero_()
         sysm.solve(u, **opts)
@@ -308,8 +314,8 @@ def run_ours(args):
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     d = kinds[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-    kernel_names = {"apply": "k_op_naive<float,OP_APPLY>", "residual": "k_op_naive<*,OP_RESIDUAL>",
-                    "mdot": "k_mdot<float,16>", "maxpy": "k_maxpy<float,16>", "dot": "k_dot_f32",
+    kernel_names = {"apply": "k_apply_tiled<5,4,OP_APPLY> + k_op_slab", "residual": "k_apply_tiled<*,OP_RESIDUAL>",
+                    "mdot": "k_mdot_f32<16>", "maxpy": "k_maxpy_f32<16>", "dot": "k_dot_f32",
                     "vector": "vector updates"}
     traffic = NCU_TRAFFIC.get((dom, "p5_64"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -348,7 +354,7 @@ def run_ours(args):
         scan = apply_scan(torch, System, pn_inputs, hbm_peak)
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         iters = int(round(statistics.mean(s["iterations"] for s in stats)))
         outers = int(round(statistics.mean(s["outer_iterations"] for s in stats))) + 1
         sample = 3
@@ -366,7 +372,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "solve/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart,
+            "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart, "ortho": args.ortho,
                        "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
                        "replicas": "one independent problem per GPU (seed = rank)"},
             "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
@@ -385,8 +391,46 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_apply_only(args):
+    """Operator throughput alone: W warm-up and K timed FP32 applies on the
+    thresholded-fBm cloud medium at order --apply-n on --apply-r^3 cells."""
+    import torch
+
+    import pn_inputs
+    from paper_1807_00410_gb300 import System
+    torch.cuda.set_device(0)
+    hbm_peak, peak_src = peaks()
+    p = pn_inputs.cloud_point(args.apply_n, args.apply_r, 0)
+    sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
+    lay = sysm.layout
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(lay.n_elems, dtype=torch.float32, device="cuda", generator=g)
+    ys = [torch.empty_like(x) for _ in range(2)]
+    for i in range(args.warmup):
+        sysm.apply(x, ys[i % 2])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        sysm.apply(x, ys[i % 2])
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    V = p.R ** 3
+    bytes_alg = (2 * lay.n_active + 2 * V) * 4
+    gbs = bytes_alg / (ms * 1e-3) / 1e9
+    print(json.dumps({"mode": "apply-only", "workload": f"P{p.N} {p.R}^3 cloud FP32 apply", "ms": ms,
+                      "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac": gbs / hbm_peak,
+                      "peak": hbm_peak, "peak_source": peak_src, "dof": lay.n_active,
+                      "bytes_per_apply": bytes_alg, "steps": args.steps, "warmup": args.warmup}), flush=True)
+    sysm.close()
+
+
 def main():
     args = parse()
+    if args.apply_only:
+        run_apply_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

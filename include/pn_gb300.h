@@ -174,7 +174,13 @@ typedef struct {
     int check_every;     /* iterations between host convergence checks */
     int profile;         /* 1: time every kernel launch of the solve with CUDA
                             events on the solve's stream (see pn_profile_get) */
+    int ortho;           /* GMRES orthogonalisation: PN_ORTHO_CGS2 (classical
+                            Gram-Schmidt twice) or PN_ORTHO_CGS1 (once, norm of
+                            the new vector by Pythagoras, half the traffic) */
 } pn_solve_opts;
+
+#define PN_ORTHO_CGS2 0
+#define PN_ORTHO_CGS1 1
 
 typedef struct {
     int status;          /* return code of the solve */
@@ -186,7 +192,7 @@ typedef struct {
 } pn_solve_stats;
 
 /* Fill *opts with defaults (CGLS, FP64, tol 1e-6, max_iter 100000, m 60,
- * inner_tol 1e-2, max_outer 50, check_every 10, profile 0). */
+ * inner_tol 1e-2, max_outer 50, check_every 10, profile 0, ortho CGS2). */
 void pn_default_solve_opts(pn_solve_opts* opts);
 
 /*
@@ -198,6 +204,34 @@ void pn_default_solve_opts(pn_solve_opts* opts);
  * Synchronises the stream.
  */
 int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_solve_stats* stats, void* stream);
+
+/*
+ * Single-scatter source of a collimated beam, as K = (N+1)^2 voxel-centre
+ * moments (section "Rendering": the single-scattered light is folded into the
+ * emission term, Q = sigma_s int p(w' -> w) L_u(w') dw', with L_u the
+ * uncollided light):
+ *     Q^{l,m}(x) = sigma_s(x) E(x) g^l Y_{l,m}(w_b),  E = exp(-int sigma_t ds).
+ * The beam has unit irradiance, travels along sign * e_axis (axis 0 = x,
+ * 1 = y, 2 = z; sign = +1 or -1), enters through the face it points away
+ * from, and covers the voxel centres within `radius` of the line through
+ * (c0, c1) in the two transverse coordinates (in increasing axis order).
+ * The optical depth to a centre is the sum of sigma_t h over the cells before
+ * it plus half of its own cell; sigma_t is used as given (no threshold).
+ * sigma_t, albedo (or NULL with albedo_const): device arrays R^3 [z][y][x];
+ * Q: device output, K x R^3, coefficient k = l*l + l + m major -- the
+ * PN_Q_CENTRE_MOMENTS layout of pn_create.  Does not synchronise.
+ */
+int pn_single_scatter_beam(int N, int R, const void* sigma_t, const void* albedo, double albedo_const, double g,
+                           int axis, int sign, double radius, double c0, double c1, void* Q, int dtype, void* stream);
+
+/*
+ * out = x interpolated to voxel centres (section "Rendering": the solution is
+ * unstaggered before rendering; the extra boundary coefficients are dropped):
+ * along each axis on which a coefficient lives on faces, the mean of the two
+ * faces of the cell.  x: device vector in the padded layout; out: device
+ * array K x R^3, coefficient-major in k = l*l + l + m order, [z][y][x].
+ */
+int pn_unstagger(pn_handle* h, const void* x, void* out, int dtype, void* stream);
 
 /*
  * *out (host) = sum_i x_i y_i for i < n, without allocating anything.

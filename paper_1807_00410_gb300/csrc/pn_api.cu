@@ -181,6 +181,7 @@ void pn_default_solve_opts(pn_solve_opts* o) {
     o->max_outer = 50;
     o->check_every = 10;
     o->profile = 0;
+    o->ortho = PN_ORTHO_CGS2;
 }
 
 int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream) {
@@ -204,6 +205,7 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
     h->K = (N + 1) * (N + 1);
     h->R = R;
     h->h = 1.0 / R;
+    h->g = m->g;
     h->pitch_x = round_up(R + 1, 4);
     h->pitch_y = h->pitch_x * (R + 1);
     h->plane_stride = round_up(h->pitch_y * (R + 1), 32);
@@ -321,7 +323,7 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
     // scratch
     h->red_blocks = pn::reduce_blocks();
     PN_TRY(dev_alloc(nullptr, &h->d_partials,
-                     size_t(std::max(h->red_blocks * PN_MAX_MDOT, pn::op_partial_count(h))), "partials"));
+                     size_t(std::max(h->red_blocks * (PN_MAX_MDOT + 1), std::max(pn::op_partial_count(h, PN_F32), pn::op_partial_count(h, PN_F64)))), "partials"));
     PN_TRY(dev_alloc(nullptr, &h->d_scalars, size_t(PN_NSCALARS), "scalars"));
     if (cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
         h->h_pinned = nullptr;
@@ -446,7 +448,7 @@ int pn_residual(pn_handle* h, const void* x, void* r, double* rel_out, int dtype
     cudaError_t e = pn::launch_op(h, pn::OP_RESIDUAL, x, r, dtype, rel_out ? h->d_partials : nullptr, s);
     if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_residual");
     if (rel_out) {
-        e = pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, h->d_scalars, s);
+        e = pn::launch_reduce(h->d_partials, pn::op_partial_count(h, dtype), 1, h->d_scalars, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pinned, h->d_scalars, 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_residual");

@@ -1,0 +1,485 @@
+// Tiled FP32 operator of the staggered P_N system for GB300.
+//
+// The operator (appendix "Final equation"; half-cell central differences
+// between the staggered grids, section "Precomputation"; Dirichlet dropping,
+// section "Runtime") couples each coefficient only to coefficients of the
+// three parity classes that differ from its own in exactly one axis, half a
+// cell away along that axis.  The kernel exploits that structure:
+//
+//  * A CTA owns a TX x TY block of (x, y) slots and marches along z through a
+//    chunk of slices.  Thread group g = (bx, by) owns the two classes
+//    (bx, by, 0) and (bx, by, 1), which differ only in z, so every z-coupling
+//    is between values the thread already holds in registers (the even class
+//    at slots s-1 and s, the odd class at s and s+1).
+//  * Each step writes slice s of every plane (plus a one-sided halo: the left
+//    or right column, the lower or upper row, depending on the plane's class)
+//    into a double-buffered shared-memory slice; x- and y-couplings read it.
+//    One barrier per step.
+//  * Each input value is read from HBM once; halos are re-read from L2.
+//  * Couplings are compile-time constants (constexpr closed forms); the 1/h
+//    factor is applied once per output.  sigma_t and sigma_s are staged per
+//    slice at voxel centres and averaged in registers.
+//  * Global loads for slice s+1 (own values, halo, sigma) are issued before
+//    slice s is computed, so memory latency overlaps the arithmetic.
+//
+// Inactive slots read as zero, which realises the Dirichlet rule without
+// branches in the stencil.  Output slots outside the tiles (x >= tiles' end,
+// plane tails) are written by the generic slab kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "pn_couplings.h"
+#include "pn_internal.h"
+
+namespace pn {
+namespace tiled {
+
+constexpr int TX = 32;
+constexpr int NG = 4;          // thread groups: (bx, by) in {0,1}^2
+constexpr int MAXT = 10;       // max transport terms per row per axis
+constexpr int MAXC = 10;       // max coefficients per class (N <= 7)
+
+struct ClassRow {
+    int k, l;
+    int nt[3];
+    int j[3][MAXT];     // index of the input within the neighbour class along that axis
+    float c[3][MAXT];   // A_d (dimensionless; 1/h applied per output)
+};
+struct ClassTab {
+    int n;
+    int plane0;
+    ClassRow row[MAXC];
+};
+struct Tab {
+    int K;
+    int maxc;
+    ClassTab cls[8];
+};
+
+constexpr Tab make_tab(int N) {
+    Tab t{};
+    t.K = (N + 1) * (N + 1);
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cls_of_k[64] = {};
+    int j_of_k[64] = {};
+    for (int l = 0; l <= N; ++l)
+        for (int m = -l; m <= l; ++m) {
+            const int k = l * l + l + m;
+            const int c = cpl::parity_class(l, m);
+            cls_of_k[k] = c;
+            j_of_k[k] = cnt[c]++;
+        }
+    int base = 0;
+    for (int c = 0; c < 8; ++c) {
+        t.cls[c].n = cnt[c];
+        t.cls[c].plane0 = base;
+        base += cnt[c];
+        if (cnt[c] > t.maxc) t.maxc = cnt[c];
+    }
+    for (int l = 0; l <= N; ++l)
+        for (int m = -l; m <= l; ++m) {
+            const int k = l * l + l + m;
+            ClassRow& r = t.cls[cls_of_k[k]].row[j_of_k[k]];
+            r.k = k;
+            r.l = l;
+            const cpl::RowTerms rt = cpl::row_terms(N, l, m);
+            for (int i = 0; i < rt.n; ++i) {
+                const int a = rt.t[i].axis;
+                const int kp = rt.t[i].lp * rt.t[i].lp + rt.t[i].lp + rt.t[i].mp;
+                r.j[a][r.nt[a]] = j_of_k[kp];
+                r.c[a][r.nt[a]] = float(rt.t[i].coef);
+                r.nt[a]++;
+            }
+        }
+    return t;
+}
+
+template <int N>
+struct TabN {
+    static constexpr Tab value = make_tab(N);
+};
+
+struct Args {
+    const float* x;
+    float* y;
+    const float* q;      // source planes (n_q of them) or null
+    const float* bvec;   // full right-hand side vector or null
+    int n_q;
+    const float* st;     // clamped sigma_t, R^3 voxel centres
+    const float* ss;     // sigma_s, R^3
+    int R;
+    int pitch_x;
+    int64_t pitch_y, plane_stride;
+    int zc;              // slices per CTA (z chunk)
+    float inv_h;         // R
+    float tsign;         // +1: A, -1: A^T
+    float fl[8];         // g^l
+    unsigned char pcls[64];  // parity class of plane p
+    double* partials;    // residual: per-CTA FP64 sums of r^2
+};
+
+// Load n values of class C (planes plane0..plane0+n-1) at slot z of this
+// thread's column; inactive slots read 0.
+template <int NV>
+__device__ __forceinline__ void load_class(const Args& a, int plane0, int n, bool colact, int z, int zext,
+                                           int64_t col, float (&v)[MAXC]) {
+    const bool act = colact && z >= 0 && z < zext;
+    const int64_t off = int64_t(z) * a.pitch_y + col;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = (i < n && act) ? __ldg(a.x + int64_t(plane0 + i) * a.plane_stride + off) : 0.0f;
+}
+
+template <int TY>
+struct Geo {
+    static constexpr int SX = TX + 2;           // shared slice row (one halo column each side)
+    static constexpr int SY = TY + 2;
+    static constexpr int SLICE = SX * SY;
+    static constexpr int GX = TX + 1;           // sigma tile: centres x0-1 .. x0+TX-1
+    static constexpr int GY = TY + 1;
+    static constexpr int GSL = GX * GY;
+    static constexpr int NT = TX * TY * NG;     // threads per CTA
+    static constexpr int HALO = TX + TY;        // halo cells per plane per slice
+};
+
+// Compute and store the outputs of one class (C: bits (bx, by, bz)) at slot s.
+//   own[i]   : this class's values at slot s
+//   zp[j], zm[j]: the z-neighbour class's values at the plus / minus slot
+//   st, ss   : sigma_t, sigma_s interpolated to this class's location
+template <int N, int TY, int C, int MODE>
+__device__ __forceinline__ void compute_class(const Args& a, const float* buf, int tx, int ty, bool store_ok,
+                                              bool active, int64_t outoff, const float (&own)[MAXC],
+                                              const float (&zp)[MAXC], const float (&zm)[MAXC], float st, float ss,
+                                              float& rrun) {
+    constexpr Tab T = TabN<N>::value;
+    constexpr ClassTab CT = T.cls[C];
+    constexpr int bx = C & 1, by = (C >> 1) & 1;
+    constexpr int CXn = C ^ 1, CYn = C ^ 2, CZn = C ^ 4;
+    constexpr int nX = T.cls[CXn].n, nY = T.cls[CYn].n, nZ = T.cls[CZn].n;
+    constexpr int pX = T.cls[CXn].plane0, pY = T.cls[CYn].plane0;
+    using G = Geo<TY>;
+    if (CT.n == 0) return;
+    // differences of the neighbour classes across this location
+    float dx[MAXC], dy[MAXC], dz[MAXC];
+    const int cy = ty + 1, cx = tx + 1;
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j) {
+        if (j < nX) {
+            const float* b = buf + (pX + j) * G::SLICE + cy * G::SX;
+            dx[j] = b[cx + 1 - bx] - b[cx - bx];
+        }
+        if (j < nY) {
+            const float* b = buf + (pY + j) * G::SLICE + cx;
+            dy[j] = b[(cy + 1 - by) * G::SX] - b[(cy - by) * G::SX];
+        }
+        if (j < nZ) dz[j] = zp[j] - zm[j];
+    }
+#pragma unroll
+    for (int i = 0; i < MAXC; ++i) {
+        if (i < CT.n) {
+            float tr = 0.0f;
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t)
+                if (t < CT.row[i].nt[0]) tr = fmaf(CT.row[i].c[0][t], dx[CT.row[i].j[0][t]], tr);
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t)
+                if (t < CT.row[i].nt[1]) tr = fmaf(CT.row[i].c[1][t], dy[CT.row[i].j[1][t]], tr);
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t)
+                if (t < CT.row[i].nt[2]) tr = fmaf(CT.row[i].c[2][t], dz[CT.row[i].j[2][t]], tr);
+            const float d = fmaf(-a.fl[CT.row[i].l], ss, st);
+            float out = fmaf(d, own[i], a.tsign * a.inv_h * tr);
+            if (MODE == OP_RESIDUAL) {
+                // right-hand side, read only at active slots (inside the plane box)
+                float b = 0.0f;
+                if (active) {
+                    if (a.bvec) b = __ldg(a.bvec + int64_t(CT.plane0 + i) * a.plane_stride + outoff);
+                    else if (CT.plane0 + i < a.n_q) b = __ldg(a.q + int64_t(CT.plane0 + i) * a.plane_stride + outoff);
+                }
+                out = b - out;
+            }
+            out = active ? out : 0.0f;
+            if (MODE == OP_RESIDUAL) rrun = fmaf(out, out, rrun);
+            if (store_ok) a.y[int64_t(CT.plane0 + i) * a.plane_stride + outoff] = out;
+        }
+    }
+}
+
+// xy-mean of a staged sigma slice at this thread's location for bits (bx, by).
+template <int TY>
+__device__ __forceinline__ float xy_mean(const float* g, int tx, int ty, int bx, int by) {
+    using G = Geo<TY>;
+    const int gx1 = tx + 1, gy1 = ty + 1;
+    const int gx0 = bx ? tx : gx1, gy0 = by ? ty : gy1;
+    return 0.25f * (g[gy0 * G::GX + gx0] + g[gy0 * G::GX + gx1] + g[gy1 * G::GX + gx0] + g[gy1 * G::GX + gx1]);
+}
+
+template <int N, int TY, int GRP, int MODE>
+__device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, int ty, int x, int y, int za, int zb,
+                                          double& racc) {
+    using G = Geo<TY>;
+    constexpr Tab T = TabN<N>::value;
+    constexpr int K = T.K;
+    constexpr int C0 = GRP, C1 = GRP + 4;
+    constexpr int bx = GRP & 1, by = GRP >> 1;
+    constexpr int n0 = T.cls[C0].n, n1 = T.cls[C1].n;
+    constexpr int p0 = T.cls[C0].plane0, p1 = T.cls[C1].plane0;
+    const int R = a.R;
+    float* buf = smem;                       // [2][K][SLICE]
+    float* sg = smem + 2 * K * G::SLICE;     // [2][2][GSL]  (sigma_t, sigma_s)
+    const int tid = tx + TX * (ty + TY * GRP);
+    const int x0 = x - tx, y0 = y - ty;
+    const bool colact0 = x < R + bx && y < R + by;
+    const bool colact1 = colact0;  // same x/y bits
+    const int64_t col = int64_t(y) * a.pitch_x + x;
+    const bool store_ok = x < a.pitch_x && y <= R;
+
+    // halo cells owned by this thread: plane p, shared index, global column offset
+    constexpr int NH = (K * G::HALO + G::NT - 1) / G::NT;
+    int h_sidx[NH];
+    int64_t h_goff[NH];
+    int h_zext[NH];  // 0: cell inactive in x/y; else the plane's z extent
+#pragma unroll
+    for (int u = 0; u < NH; ++u) {
+        const int h = tid + u * G::NT;
+        h_sidx[u] = -1;
+        h_goff[u] = 0;
+        h_zext[u] = 0;
+        if (h < K * G::HALO) {
+            const int p = h / G::HALO, r = h % G::HALO;
+            const int pc = a.pcls[p];
+            const int pbx = pc & 1, pby = (pc >> 1) & 1, pbz = pc >> 2;
+            int hx, hy, sx, sy;
+            if (r < TX) {
+                hx = x0 + r;
+                hy = pby ? y0 + TY : y0 - 1;
+                sx = r + 1;
+                sy = pby ? TY + 1 : 0;
+            } else {
+                hy = y0 + (r - TX);
+                hx = pbx ? x0 + TX : x0 - 1;
+                sy = r - TX + 1;
+                sx = pbx ? TX + 1 : 0;
+            }
+            h_sidx[u] = p * G::SLICE + sy * G::SX + sx;
+            const bool act = hx >= 0 && hy >= 0 && hx < R + pbx && hy < R + pby;
+            h_zext[u] = act ? R + pbz : 0;
+            h_goff[u] = int64_t(p) * a.plane_stride + int64_t(hy) * a.pitch_x + hx;
+        }
+    }
+    // sigma tile cell owned by this thread (two fields)
+    const bool sg_own = tid < 2 * G::GSL;
+    const int sg_field = tid / G::GSL, sg_cell = tid % G::GSL;
+    int64_t sg_off = 0;
+    {
+        const int gx = sg_cell % G::GX, gy = sg_cell / G::GX;
+        const int cxr = min(max(x0 - 1 + gx, 0), R - 1), cyr = min(max(y0 - 1 + gy, 0), R - 1);
+        sg_off = int64_t(cyr) * R + cxr;
+    }
+    const float* sgsrc = sg_field == 0 ? a.st : a.ss;
+    const int64_t R2 = int64_t(R) * R;
+    auto sg_load = [&](int s) -> float {
+        const int zc = min(max(s, 0), R - 1);
+        return sg_own ? __ldg(sgsrc + zc * R2 + sg_off) : 0.0f;
+    };
+
+    // priming: sigma slice za-1 -> xy-means of the previous slice
+    if (sg_own) sg[((za + 1) & 1) * 2 * G::GSL + tid] = sg_load(za - 1);
+    float v0p[MAXC] = {}, v0c[MAXC] = {}, v0n[MAXC] = {}, v1c[MAXC] = {}, v1n[MAXC] = {};
+    load_class<n0>(a, p0, n0, colact0, za - 1, R, col, v0p);
+    load_class<n0>(a, p0, n0, colact0, za, R, col, v0c);
+    load_class<n1>(a, p1, n1, colact1, za, R + 1, col, v1c);
+    load_class<n1>(a, p1, n1, colact1, za + 1, R + 1, col, v1n);
+    float hreg[NH];
+#pragma unroll
+    for (int u = 0; u < NH; ++u)
+        hreg[u] = (h_sidx[u] >= 0 && za < h_zext[u]) ? __ldg(a.x + h_goff[u] + int64_t(za) * a.pitch_y) : 0.0f;
+    float sreg = sg_load(za);
+    __syncthreads();
+    float mt_prev, ms_prev;
+    {
+        const float* g = sg + ((za + 1) & 1) * 2 * G::GSL;
+        mt_prev = xy_mean<TY>(g, tx, ty, bx, by);
+        ms_prev = xy_mean<TY>(g + G::GSL, tx, ty, bx, by);
+    }
+    float rrun = 0.0f;
+    int rcnt = 0;
+    for (int s = za; s < zb; ++s) {
+        float* b = buf + (s & 1) * K * G::SLICE;
+        float* g = sg + (s & 1) * 2 * G::GSL;
+        // stage slice s: own values, halo, sigma
+        const int sidx = (ty + 1) * G::SX + (tx + 1);
+#pragma unroll
+        for (int i = 0; i < n0; ++i) b[(p0 + i) * G::SLICE + sidx] = v0c[i];
+#pragma unroll
+        for (int i = 0; i < n1; ++i) b[(p1 + i) * G::SLICE + sidx] = v1c[i];
+#pragma unroll
+        for (int u = 0; u < NH; ++u)
+            if (h_sidx[u] >= 0) b[h_sidx[u]] = hreg[u];
+        if (sg_own) g[tid] = sreg;
+        // prefetch slice s+1 (and s+2 for the odd class)
+        load_class<n0>(a, p0, n0, colact0, s + 1, R, col, v0n);
+        float v1t[MAXC] = {};
+        load_class<n1>(a, p1, n1, colact1, s + 2, R + 1, col, v1t);
+#pragma unroll
+        for (int u = 0; u < NH; ++u)
+            hreg[u] = (h_sidx[u] >= 0 && s + 1 < h_zext[u]) ? __ldg(a.x + h_goff[u] + int64_t(s + 1) * a.pitch_y) : 0.0f;
+        sreg = sg_load(s + 1);
+        __syncthreads();
+        const float mt = xy_mean<TY>(g, tx, ty, bx, by);
+        const float ms = xy_mean<TY>(g + G::GSL, tx, ty, bx, by);
+        const int64_t outoff = int64_t(s) * a.pitch_y + col;
+        // even class (bz = 0): z-neighbours are the odd class at s+1 (plus) and s (minus)
+        compute_class<N, TY, C0, MODE>(a, b, tx, ty, store_ok, colact0 && s < R, outoff, v0c, v1n, v1c, mt, ms,
+                                       rrun);
+        // odd class (bz = 1): z-neighbours are the even class at s (plus) and s-1 (minus)
+        compute_class<N, TY, C1, MODE>(a, b, tx, ty, store_ok, colact1, outoff, v1c, v0c, v0p,
+                                       0.5f * (mt + mt_prev), 0.5f * (ms + ms_prev), rrun);
+        if (MODE == OP_RESIDUAL && ++rcnt == 4) {
+            racc += double(rrun);
+            rrun = 0.0f;
+            rcnt = 0;
+        }
+        mt_prev = mt;
+        ms_prev = ms;
+#pragma unroll
+        for (int i = 0; i < n0; ++i) {
+            v0p[i] = v0c[i];
+            v0c[i] = v0n[i];
+        }
+#pragma unroll
+        for (int i = 0; i < n1; ++i) {
+            v1c[i] = v1n[i];
+            v1n[i] = v1t[i];
+        }
+    }
+    racc += double(rrun);
+}
+
+template <int N, int TY, int MODE>
+__global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
+    extern __shared__ float smem[];
+    const int tx = threadIdx.x, ty = threadIdx.y, grp = threadIdx.z;
+    const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+    const int za = blockIdx.z * a.zc;
+    const int zb = min(za + a.zc, a.R + 1);
+    double racc = 0.0;
+    switch (grp) {
+        case 0: run_group<N, TY, 0, MODE>(a, smem, tx, ty, x, y, za, zb, racc); break;
+        case 1: run_group<N, TY, 1, MODE>(a, smem, tx, ty, x, y, za, zb, racc); break;
+        case 2: run_group<N, TY, 2, MODE>(a, smem, tx, ty, x, y, za, zb, racc); break;
+        default: run_group<N, TY, 3, MODE>(a, smem, tx, ty, x, y, za, zb, racc); break;
+    }
+    if (MODE == OP_RESIDUAL && a.partials != nullptr) {
+        __shared__ double red[TX * TY * NG / 32];
+        for (int o = 16; o > 0; o >>= 1) racc += __shfl_down_sync(0xffffffffu, racc, o);
+        const int tid = tx + TX * (ty + TY * grp);
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = racc;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int i = 0; i < TX * TY * NG / 32; ++i) t += red[i];
+            a.partials[(int64_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+        }
+    }
+}
+
+}  // namespace tiled
+
+namespace {
+
+struct TiledPlan {
+    dim3 grid, block;
+    int zc;
+    size_t smem;
+    int x_end;  // tiles cover x < x_end
+};
+
+template <int TY>
+TiledPlan plan_for(const pn_handle* h) {
+    using G = tiled::Geo<TY>;
+    TiledPlan p;
+    const int R = h->R;
+    const int nxt = (R + tiled::TX - 1) / tiled::TX;
+    const int nyt = (R + 1 + TY - 1) / TY;
+    const int sms = pn_sm_count();
+    // z chunks: enough CTAs for about 4 per SM, chunks of at least 16 slices
+    int nzc = std::max(1, (4 * sms + nxt * nyt - 1) / (nxt * nyt));
+    nzc = std::min(nzc, std::max(1, (R + 1) / 16));
+    const int zc = (R + 1 + nzc - 1) / nzc;
+    nzc = (R + 1 + zc - 1) / zc;
+    p.grid = dim3(nxt, nyt, nzc);
+    p.block = dim3(tiled::TX, TY, tiled::NG);
+    p.zc = zc;
+    p.smem = (size_t(2) * h->K * G::SLICE + 4 * G::GSL) * sizeof(float);
+    p.x_end = std::min<int>(int(h->pitch_x), nxt * tiled::TX);
+    return p;
+}
+
+constexpr int kTY = 4;
+
+template <int N, int MODE>
+cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& p, cudaStream_t s) {
+    auto kern = tiled::k_apply_tiled<N, kTY, MODE>;
+    static bool configured[8] = {false};
+    if (!configured[N]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        configured[N] = true;
+    }
+    kern<<<p.grid, p.block, p.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(const pn_handle* h, const tiled::Args& a, const TiledPlan& p, cudaStream_t s) {
+    switch (h->N) {
+        case 0: return launch_n<0, MODE>(h, a, p, s);
+        case 1: return launch_n<1, MODE>(h, a, p, s);
+        case 2: return launch_n<2, MODE>(h, a, p, s);
+        case 3: return launch_n<3, MODE>(h, a, p, s);
+        case 4: return launch_n<4, MODE>(h, a, p, s);
+        case 5: return launch_n<5, MODE>(h, a, p, s);
+        case 6: return launch_n<6, MODE>(h, a, p, s);
+        default: return launch_n<7, MODE>(h, a, p, s);
+    }
+}
+
+}  // namespace
+
+int tiled_partial_count(const pn_handle* h) {
+    const TiledPlan p = plan_for<kTY>(h);
+    return int(p.grid.x * p.grid.y * p.grid.z);
+}
+
+int tiled_x_end(const pn_handle* h) { return plan_for<kTY>(h).x_end; }
+
+cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,
+                         double* partials, cudaStream_t s) {
+    const TiledPlan p = plan_for<kTY>(h);
+    tiled::Args a{};
+    a.x = x;
+    a.y = y;
+    a.q = h->d_q_f;
+    a.bvec = bvec;
+    a.n_q = h->n_q_planes;
+    a.st = h->d_st_f;
+    a.ss = h->d_ss_f;
+    a.R = h->R;
+    a.pitch_x = int(h->pitch_x);
+    a.pitch_y = h->pitch_y;
+    a.plane_stride = h->plane_stride;
+    a.zc = p.zc;
+    a.inv_h = float(h->R);
+    a.tsign = mode == OP_APPLY_T ? -1.0f : 1.0f;
+    for (int l = 0; l < 8; ++l) a.fl[l] = l == 0 ? 1.0f : float(std::pow(h->g, l));
+    for (int q = 0; q < 64; ++q) a.pcls[q] = q < h->K ? (unsigned char)h->plane_class[q] : 0;
+    a.partials = partials;
+    if (mode == OP_RESIDUAL) return launch_mode<OP_RESIDUAL>(h, a, p, s);
+    return launch_mode<OP_APPLY>(h, a, p, s);
+}
+
+}  // namespace pn

@@ -51,6 +51,7 @@ int pn_sm_count();
 struct pn_handle {
     int N = 0, K = 0, R = 0;
     double h = 0.0;
+    double g = 0.0;  // Henyey-Greenstein mean cosine
     int64_t pitch_x = 0, pitch_y = 0, plane_stride = 0, n_elems = 0, n_active = 0;
     int plane_k[PN_MAX_K];
     int plane_class[PN_MAX_K];
@@ -75,7 +76,7 @@ struct pn_handle {
 
     // scratch: FP64 reduction partials and device scalars
     int red_blocks = 0;           // blocks of every reduction kernel
-    double* d_partials = nullptr; // red_blocks * PN_MAX_MDOT doubles
+    double* d_partials = nullptr; // >= red_blocks * (PN_MAX_MDOT + 1) doubles
     double* d_scalars = nullptr;  // PN_NSCALARS doubles
     double* h_pinned = nullptr;   // pinned host mirror of a few scalars
 
@@ -107,7 +108,14 @@ enum OpMode { OP_APPLY = 0, OP_APPLY_T = 1, OP_RESIDUAL = 2 };
 // go to partials[0..op_partial_count(h)).
 cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
                       double* partials, cudaStream_t s, const void* bvec = nullptr);
-int op_partial_count(const pn_handle* h);
+int op_partial_count(const pn_handle* h, int dtype);
+
+// Tiled FP32 operator (pn_apply_tiled.cu): covers x < tiled_x_end(h) of every
+// plane box; one FP64 residual partial per CTA.
+cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,
+                         double* partials, cudaStream_t s);
+int tiled_partial_count(const pn_handle* h);
+int tiled_x_end(const pn_handle* h);
 
 // partials[b] = per-block sum of a_i * b_i (FP64); then *out = sum of partials.
 cudaError_t launch_dot(const pn_handle* h, const void* a, const void* b, int64_t n, int dtype,

@@ -68,6 +68,37 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;  // valid in thread 0
 }
 
+// One output of the operator at slot (x, y, z) of plane p (active slot).
+template <typename T, int MODE>
+__device__ __forceinline__ T op_point(const OpArgs<T>& a, int p, const Plane& P, int x, int y, int z, int64_t s) {
+    const int R = a.R;
+    const int64_t pbase = int64_t(p) * a.plane_stride;
+    const T diag = centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
+                   plane_fl<T>(P) * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
+    T acc = diag * a.x[pbase + s];
+    T tr = T(0);
+    for (int ti = P.t0; ti < P.t1; ++ti) {
+        const Term tm = a.terms[ti];
+        int i, b;
+        int64_t stride;
+        if (tm.axis == 0) { i = x; b = P.px; stride = 1; }
+        else if (tm.axis == 1) { i = y; b = P.py; stride = a.pitch_x; }
+        else { i = z; b = P.pz; stride = a.pitch_y; }
+        const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
+        // plus neighbour at slot i + 1 - b (exists iff < R + 1 - b),
+        // minus neighbour at slot i - b (exists iff >= 0)
+        const T vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
+        const T vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
+        tr += term_coef<T>(tm) * (vp - vm);
+    }
+    acc = (MODE == OP_APPLY_T) ? acc - tr : acc + tr;
+    if (MODE == OP_RESIDUAL) {
+        const T bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : T(0));
+        return bq - acc;
+    }
+    return acc;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_op_naive(OpArgs<T> a) {
     const int p = blockIdx.y;
@@ -76,8 +107,9 @@ __global__ void __launch_bounds__(256) k_op_naive(OpArgs<T> a) {
     const int ny = R + 1;
     const int64_t box = a.pitch_y * int64_t(R + 1);
     const int64_t pbase = int64_t(p) * a.plane_stride;
-    const T fl = plane_fl<T>(P);
     double racc = 0.0;
+    T rrun = T(0);  // residual squares summed in T per thread, flushed to FP64 every 16
+    int rcnt = 0;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < a.plane_stride;
          s += int64_t(gridDim.x) * blockDim.x) {
         const int x = int(s % a.pitch_x);
@@ -87,32 +119,53 @@ __global__ void __launch_bounds__(256) k_op_naive(OpArgs<T> a) {
         const bool active = s < box && x < R + P.px && y < R + P.py && z < R + P.pz;
         T out = T(0);
         if (active) {
-            const T diag = centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
-                           fl * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
-            T acc = diag * a.x[pbase + s];
-            T tr = T(0);
-            for (int ti = P.t0; ti < P.t1; ++ti) {
-                const Term tm = a.terms[ti];
-                int i, b;
-                int64_t stride;
-                if (tm.axis == 0) { i = x; b = P.px; stride = 1; }
-                else if (tm.axis == 1) { i = y; b = P.py; stride = a.pitch_x; }
-                else { i = z; b = P.pz; stride = a.pitch_y; }
-                const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
-                // plus neighbour at slot i + 1 - b (exists iff < R + 1 - b),
-                // minus neighbour at slot i - b (exists iff >= 0)
-                const T vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
-                const T vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
-                tr += term_coef<T>(tm) * (vp - vm);
-            }
-            acc = (MODE == OP_APPLY_T) ? acc - tr : acc + tr;
+            out = op_point<T, MODE>(a, p, P, x, y, z, s);
             if (MODE == OP_RESIDUAL) {
-                const T bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : T(0));
-                out = bq - acc;
-                racc += double(out) * double(out);
-            } else {
-                out = acc;
+                rrun += out * out;
+                if (++rcnt == 16) {
+                    racc += double(rrun);
+                    rrun = T(0);
+                    rcnt = 0;
+                }
             }
+        }
+        a.y[pbase + s] = out;
+    }
+    if (MODE == OP_RESIDUAL && a.partials != nullptr) {
+        const double bs = block_sum(racc + double(rrun));
+        if (threadIdx.x == 0) a.partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = bs;
+    }
+}
+
+// The slots a tiled launch does not cover: columns x >= x_lo of every plane
+// box, and each plane's tail beyond its box.  Thread t of plane p handles
+// slot t of the list [(z, y, x) for x in [x_lo, pitch_x)] + tail.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_op_slab(OpArgs<T> a, int x_lo) {
+    const int p = blockIdx.y;
+    const Plane P = a.planes[p];
+    const int R = a.R;
+    const int w = int(a.pitch_x) - x_lo;
+    const int64_t box = a.pitch_y * int64_t(R + 1);
+    const int64_t ncol = int64_t(w) * (R + 1) * (R + 1);
+    const int64_t ntail = a.plane_stride - box;
+    const int64_t pbase = int64_t(p) * a.plane_stride;
+    double racc = 0.0;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < ncol + ntail;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        if (t >= ncol) {
+            a.y[pbase + box + (t - ncol)] = T(0);
+            continue;
+        }
+        const int x = x_lo + int(t % w);
+        const int64_t u = t / w;
+        const int y = int(u % (R + 1));
+        const int z = int(u / (R + 1));
+        const int64_t s = int64_t(z) * a.pitch_y + int64_t(y) * a.pitch_x + x;
+        T out = T(0);
+        if (x < R + P.px && y < R + P.py && z < R + P.pz) {
+            out = op_point<T, MODE>(a, p, P, x, y, z, s);
+            if (MODE == OP_RESIDUAL) racc += double(out) * double(out);
         }
         a.y[pbase + s] = out;
     }
@@ -129,7 +182,18 @@ static int naive_grid_x(const pn_handle* h) {
     return int(want);
 }
 
-int op_partial_count(const pn_handle* h) { return naive_grid_x(h) * h->K; }
+static int slab_grid_x(const pn_handle* h) {
+    const int64_t w = h->pitch_x - tiled_x_end(h);
+    const int64_t n = w * (h->R + 1) * (h->R + 1) + (h->plane_stride - h->pitch_y * (h->R + 1));
+    int64_t g = (n + 255) / 256;
+    if (g > 1024) g = 1024;
+    return int(g < 1 ? 1 : g);
+}
+
+int op_partial_count(const pn_handle* h, int dtype) {
+    if (dtype == PN_F32) return tiled_partial_count(h) + slab_grid_x(h) * h->K;
+    return naive_grid_x(h) * h->K;
+}
 
 template <typename T>
 static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T* st, const T* ss,
@@ -149,9 +213,23 @@ static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T*
 
 cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
                       double* partials, cudaStream_t s, const void* bvec) {
-    if (dtype == PN_F32)
-        return op_t<float>(h, mode, (const float*)x, (float*)y, h->d_st_f, h->d_ss_f, h->d_q_f,
-                           (const float*)bvec, partials, s);
+    if (dtype == PN_F32) {
+        // tiled kernel for x < x_end, generic slab kernel for the rest
+        cudaError_t e = launch_tiled(h, mode, (const float*)x, (float*)y, (const float*)bvec, partials, s);
+        if (e != cudaSuccess) return e;
+        OpArgs<float> a;
+        a.x = (const float*)x; a.y = (float*)y; a.q = h->d_q_f; a.n_q = h->n_q_planes; a.bvec = (const float*)bvec;
+        a.st = h->d_st_f; a.ss = h->d_ss_f;
+        a.planes = h->d_planes; a.terms = h->d_terms;
+        a.R = h->R; a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
+        a.partials = partials ? partials + tiled_partial_count(h) : nullptr;
+        dim3 grid(slab_grid_x(h), h->K);
+        const int x_lo = tiled_x_end(h);
+        if (mode == OP_APPLY) k_op_slab<float, OP_APPLY><<<grid, 256, 0, s>>>(a, x_lo);
+        else if (mode == OP_APPLY_T) k_op_slab<float, OP_APPLY_T><<<grid, 256, 0, s>>>(a, x_lo);
+        else k_op_slab<float, OP_RESIDUAL><<<grid, 256, 0, s>>>(a, x_lo);
+        return cudaGetLastError();
+    }
     return op_t<double>(h, mode, (const double*)x, (double*)y, h->d_st_d, h->d_ss_d, h->d_q_d,
                         (const double*)bvec, partials, s);
 }
@@ -164,13 +242,19 @@ int reduce_blocks() {
     return g_reduce_blocks;
 }
 
-// FP64 dot.  FP32 inputs: products of four consecutive elements are summed in
-// FP32 (one float4), each 4-term partial is accumulated in FP64.
+// FP64 dot.  FP32 inputs: each thread sums runs of up to 32 products in FP32
+// and accumulates each run's sum in FP64.
 __global__ void __launch_bounds__(256) k_dot_f32(const float4* a, const float4* b, int64_t n4, double* partials) {
     double acc = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
-        const float4 u = a[i], v = b[i];
-        acc += double(fmaf(u.w, v.w, fmaf(u.z, v.z, fmaf(u.y, v.y, u.x * v.x))));
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    while (i < n4) {
+        float run = 0.0f;  // up to 8 float4 products in FP32, then into FP64
+        for (int r = 0; r < 8 && i < n4; ++r, i += stride) {
+            const float4 u = a[i], v = b[i];
+            run = fmaf(u.w, v.w, fmaf(u.z, v.z, fmaf(u.y, v.y, fmaf(u.x, v.x, run))));
+        }
+        acc += double(run);
     }
     const double bs = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = bs;

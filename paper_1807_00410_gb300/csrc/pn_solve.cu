@@ -47,12 +47,20 @@ __global__ void __launch_bounds__(256) k_cgls_xr(int64_t n, T* x, T* r, const T*
     const double qq = S[S_QQ];
     const T alpha = qq > 0.0 ? T(S[g] / qq) : T(0);
     double acc = 0.0;
+    T run = T(0);
+    int cnt = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * q[i];
         r[i] = ri;
-        acc += double(ri) * double(ri);
+        run += ri * ri;  // short runs in T, each run's sum added in FP64
+        if (++cnt == 16) {
+            acc += double(run);
+            run = T(0);
+            cnt = 0;
+        }
     }
+    acc += double(run);
     const double bs = warp_block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = bs;
 }
@@ -82,17 +90,22 @@ __global__ void __launch_bounds__(256) k_scale_invnorm(int64_t n, T* v, const do
 }
 
 // Multi-dot: partials[j * gridDim.x + b] = block b's share of V_j . w, j < nv.
+// FP32 vectors: float4 loads; each thread sums kRun float4 products in FP32,
+// then adds the run's sum to its FP64 accumulator (FP64 work is 1/(4 kRun)
+// of the elements; GB300's FP64 rate is far below its FP32 rate).
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_mdot(int64_t n, const T* V, int64_t vstride, int nv, const T* w,
-                                              double* partials) {
-    double acc[NV];
+                                              double* partials, int self_dot) {
+    double acc[NV + 1];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    for (int j = 0; j <= NV; ++j) acc[j] = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
         const T wi = w[i];
 #pragma unroll
         for (int j = 0; j < NV; ++j)
-            if (j < nv) acc[j] += double(V[j * vstride + i] * wi);
+            if (j < nv) acc[j] = fma(double(V[j * vstride + i]), double(wi), acc[j]);
+        if (self_dot) acc[NV] = fma(double(wi), double(wi), acc[NV]);
     }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
@@ -101,22 +114,127 @@ __global__ void __launch_bounds__(256) k_mdot(int64_t n, const T* V, int64_t vst
             if (threadIdx.x == 0) partials[int64_t(j) * gridDim.x + blockIdx.x] = bs;
         }
     }
+    if (self_dot) {
+        const double bs = warp_block_sum(acc[NV]);
+        if (threadIdx.x == 0) partials[int64_t(nv) * gridDim.x + blockIdx.x] = bs;
+    }
+}
+
+constexpr int kRun = 8;
+
+// With self_dot, slot nv also receives w . w (one extra accumulator).
+template <int NV>
+__global__ void __launch_bounds__(256) k_mdot_f32(int64_t n4, const float4* V, int64_t vstride4, int nv,
+                                                  const float4* w, double* partials, int self_dot) {
+    double acc[NV + 1];
+#pragma unroll
+    for (int j = 0; j <= NV; ++j) acc[j] = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    while (i < n4) {
+        float part[NV + 1];
+#pragma unroll
+        for (int j = 0; j <= NV; ++j) part[j] = 0.0f;
+        for (int r = 0; r < kRun && i < n4; ++r, i += stride) {
+            const float4 wi = w[i];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                if (j < nv) {
+                    const float4 v = V[j * vstride4 + i];
+                    part[j] = fmaf(v.w, wi.w, fmaf(v.z, wi.z, fmaf(v.y, wi.y, fmaf(v.x, wi.x, part[j]))));
+                }
+            }
+            if (self_dot) part[NV] = fmaf(wi.w, wi.w, fmaf(wi.z, wi.z, fmaf(wi.y, wi.y, fmaf(wi.x, wi.x, part[NV]))));
+        }
+#pragma unroll
+        for (int j = 0; j <= NV; ++j) acc[j] += double(part[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        if (j < nv) {
+            const double bs = warp_block_sum(acc[j]);
+            if (threadIdx.x == 0) partials[int64_t(j) * gridDim.x + blockIdx.x] = bs;
+        }
+    }
+    if (self_dot) {
+        const double bs = warp_block_sum(acc[NV]);
+        if (threadIdx.x == 0) partials[int64_t(nv) * gridDim.x + blockIdx.x] = bs;
+    }
 }
 
 // w += sign * sum_j c[j] V_j   (c in FP64 on the device, applied in T)
+// w = (w + sign * sum_j c[j] V_j) * scale, scale = *scale_p (1 if null)
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_maxpy(int64_t n, T* w, const T* V, int64_t vstride, int nv,
-                                               const double* c, double sign) {
+                                               const double* c, double sign, const double* scale_p) {
     T cj[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) cj[j] = j < nv ? T(sign * c[j]) : T(0);
+    const T sc = scale_p ? T(*scale_p) : T(1);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         T acc = w[i];
 #pragma unroll
         for (int j = 0; j < NV; ++j)
             if (j < nv) acc += cj[j] * V[j * vstride + i];
+        w[i] = acc * sc;
+    }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(256) k_maxpy_f32(int64_t n4, float4* w, const float4* V, int64_t vstride4, int nv,
+                                                   const double* c, double sign, const double* scale_p) {
+    float cj[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) cj[j] = j < nv ? float(sign * c[j]) : 0.0f;
+    const float sc = scale_p ? float(*scale_p) : 1.0f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+        float4 acc = w[i];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            if (j < nv) {
+                const float4 v = V[j * vstride4 + i];
+                acc.x = fmaf(cj[j], v.x, acc.x);
+                acc.y = fmaf(cj[j], v.y, acc.y);
+                acc.z = fmaf(cj[j], v.z, acc.z);
+                acc.w = fmaf(cj[j], v.w, acc.w);
+            }
+        }
+        acc.x *= sc;
+        acc.y *= sc;
+        acc.z *= sc;
+        acc.w *= sc;
         w[i] = acc;
     }
+}
+
+// Typed launchers: FP32 vectors take the float4 kernels (n is a multiple of 32).
+template <typename T>
+void launch_mdot(int nb, cudaStream_t s, int64_t n, const T* V, int64_t vstride, int nv, const T* w, double* part,
+                 int self_dot = 0);
+template <>
+void launch_mdot<float>(int nb, cudaStream_t s, int64_t n, const float* V, int64_t vstride, int nv, const float* w,
+                        double* part, int self_dot) {
+    k_mdot_f32<PN_MAX_MDOT><<<nb, 256, 0, s>>>(n / 4, (const float4*)V, vstride / 4, nv, (const float4*)w, part,
+                                               self_dot);
+}
+template <>
+void launch_mdot<double>(int nb, cudaStream_t s, int64_t n, const double* V, int64_t vstride, int nv,
+                         const double* w, double* part, int self_dot) {
+    k_mdot<double, PN_MAX_MDOT><<<nb, 256, 0, s>>>(n, V, vstride, nv, w, part, self_dot);
+}
+template <typename T>
+void launch_maxpy(int nb, cudaStream_t s, int64_t n, T* w, const T* V, int64_t vstride, int nv, const double* c,
+                  double sign, const double* scale_p = nullptr);
+template <>
+void launch_maxpy<float>(int nb, cudaStream_t s, int64_t n, float* w, const float* V, int64_t vstride, int nv,
+                         const double* c, double sign, const double* scale_p) {
+    k_maxpy_f32<PN_MAX_MDOT><<<nb, 256, 0, s>>>(n / 4, (float4*)w, (const float4*)V, vstride / 4, nv, c, sign,
+                                                scale_p);
+}
+template <>
+void launch_maxpy<double>(int nb, cudaStream_t s, int64_t n, double* w, const double* V, int64_t vstride, int nv,
+                          const double* c, double sign, const double* scale_p) {
+    k_maxpy<double, PN_MAX_MDOT><<<nb, 256, 0, s>>>(n, w, V, vstride, nv, c, sign, scale_p);
 }
 
 // Arnoldi step bookkeeping, one thread, FP64.
@@ -125,11 +243,20 @@ __global__ void __launch_bounds__(256) k_maxpy(int64_t n, T* w, const T* V, int6
 // Applies the previous rotations, forms rotation j, updates g and writes
 // |g[j+1]| to S[S_RES] and 1/||w|| to S[S_SCALE].
 __global__ void k_givens(double* H, int ldh, const double* add, double* cs, double* sn, double* g, int j,
-                         double* S) {
+                         double* S, int pythagoras) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double* col = H + int64_t(j) * ldh;
-    for (int i = 0; i <= j; ++i) col[i] += add[i];
-    const double hn = sqrt(fmax(S[S_NRM2], 0.0));
+    double nrm2 = S[S_NRM2];
+    if (pythagoras) {
+        // single Gram-Schmidt pass: ||w - V h||^2 = ||w||^2 - ||h||^2 for orthonormal V
+        double hh = 0.0;
+        for (int i = 0; i <= j; ++i) hh += col[i] * col[i];
+        nrm2 = nrm2 - hh;
+        if (!(nrm2 > 1e-14 * S[S_NRM2])) nrm2 = 1e-14 * S[S_NRM2];
+    } else {
+        for (int i = 0; i <= j; ++i) col[i] += add[i];
+    }
+    const double hn = sqrt(fmax(nrm2, 0.0));
     col[j + 1] = hn;
     S[S_SCALE] = hn > 0.0 ? 1.0 / hn : 0.0;
     for (int i = 0; i < j; ++i) {
@@ -148,6 +275,17 @@ __global__ void k_givens(double* H, int ldh, const double* add, double* cs, doub
     g[j + 1] = -s * g[j];
     g[j] = c * g[j];
     S[S_RES] = fabs(g[j + 1]);
+}
+
+// CGS1 bookkeeping: the first chunk's reduction wrote nv0 projections and
+// ||w||^2 into tmp0, later chunks wrote their projections into proj directly.
+// Completes proj[0..j], copies it into the H column (which the Givens kernel
+// then rotates) and puts ||w||^2 into S[S_NRM2].
+__global__ void k_cgs1_gather(double* col, double* proj, const double* tmp0, int nv0, int j, double* S) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < nv0; ++i) proj[i] = tmp0[i];
+    for (int i = 0; i <= j; ++i) col[i] = proj[i];
+    S[S_NRM2] = tmp0[nv0];
 }
 
 __global__ void k_gm_init(double* g, int m, double* S) {
@@ -276,7 +414,7 @@ int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
         c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r, dt, h->d_partials, c.s), "cgls: residual");
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, es, false));
         c.pb();
-        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, S + S_RR, c.s), "cgls: reduce");
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, dt), 1, S + S_RR, c.s), "cgls: reduce");
         c.pe(PN_PROF_SCALAR, 0.0);
     };
     auto op = [&](int mode, const T* in, T* out) {
@@ -346,7 +484,7 @@ int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
 // ||b|| (bnorm2 = ||b||^2).  Adds the inner iterations to *iters.
 template <typename T>
 int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max_iter, int check_every,
-          int* iters, double* rel_out) {
+          int* iters, double* rel_out, int ortho = PN_ORTHO_CGS2) {
     pn_handle* h = c.h;
     const int64_t n = h->n_elems;
     const int dt = sizeof(T) == 4 ? PN_F32 : PN_F64;
@@ -377,7 +515,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
         c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, V, dt, h->d_partials, c.s, bvec), "gmres: residual");
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, es, bvec != nullptr));
         c.pb();
-        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, S + S_BETA2, c.s), "gmres: reduce");
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, dt), 1, S + S_BETA2, c.s), "gmres: reduce");
         c.pe(PN_PROF_SCALAR, 0.0);
         double b2 = 0.0;
         if (!c.read(S_BETA2, 1, &b2)) return c.rc;
@@ -398,36 +536,70 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
             c.pb();
             c.lk(pn::launch_op(h, pn::OP_APPLY, V + int64_t(j) * n, w, dt, nullptr, c.s), "gmres: A v");
             c.pe(PN_PROF_APPLY, c.ob(pn::OP_APPLY, es, false));
-            // classical Gram-Schmidt, twice
-            for (int pass = 0; pass < 2; ++pass) {
-                double* hc = pass == 0 ? H + int64_t(j) * ldh : add;
+            if (ortho == PN_ORTHO_CGS1) {
+                // classical Gram-Schmidt once: all projections and ||w||^2 in one
+                // pass over the basis; the new vector is normalised by the last
+                // update.  The projections stay unrotated in `add` (the Givens
+                // kernel rotates the H column in place before the updates run).
+                double* tmp0 = add + (m + 1);  // chunk 0: nv projections + ||w||^2
+                const int nv0 = std::min(PN_MAX_MDOT, j + 1);
                 for (int i0 = 0; i0 <= j; i0 += PN_MAX_MDOT) {
                     const int nv = std::min(PN_MAX_MDOT, j + 1 - i0);
                     c.pb();
-                    k_mdot<T, PN_MAX_MDOT><<<h->red_blocks, 256, 0, c.s>>>(n, V + int64_t(i0) * n, n, nv, w,
-                                                                           h->d_partials);
+                    launch_mdot<T>(h->red_blocks, c.s, n, V + int64_t(i0) * n, n, nv, w, h->d_partials, i0 == 0);
                     c.launched("gmres: mdot");
                     c.pe(PN_PROF_MDOT, c.vb(nv + 1, es));
                     c.pb();
-                    c.lk(pn::launch_reduce(h->d_partials, h->red_blocks, nv, hc + i0, c.s), "gmres: reduce");
+                    c.lk(pn::launch_reduce(h->d_partials, h->red_blocks, i0 == 0 ? nv + 1 : nv,
+                                           i0 == 0 ? tmp0 : add + i0, c.s),
+                         "gmres: reduce");
                     c.pe(PN_PROF_SCALAR, 0.0);
+                }
+                c.pb();
+                k_cgs1_gather<<<1, 32, 0, c.s>>>(H + int64_t(j) * ldh, add, tmp0, nv0, j, S);
+                k_givens<<<1, 32, 0, c.s>>>(H, ldh, add, cs, sn, g, j, S, 1);
+                c.launched("gmres: givens", 2);
+                c.pe(PN_PROF_SCALAR, 0.0);
+                for (int i0 = 0; i0 <= j; i0 += PN_MAX_MDOT) {
+                    const int nv = std::min(PN_MAX_MDOT, j + 1 - i0);
+                    const bool last = i0 + PN_MAX_MDOT > j;
                     c.pb();
-                    k_maxpy<T, PN_MAX_MDOT><<<nb, 256, 0, c.s>>>(n, w, V + int64_t(i0) * n, n, nv, hc + i0, -1.0);
+                    launch_maxpy<T>(nb, c.s, n, w, V + int64_t(i0) * n, n, nv, add + i0, -1.0,
+                                    last ? S + S_SCALE : nullptr);
                     c.launched("gmres: maxpy");
                     c.pe(PN_PROF_MAXPY, c.vb(nv + 2, es));
                 }
+            } else {
+                // classical Gram-Schmidt, twice
+                for (int pass = 0; pass < 2; ++pass) {
+                    double* hc = pass == 0 ? H + int64_t(j) * ldh : add;
+                    for (int i0 = 0; i0 <= j; i0 += PN_MAX_MDOT) {
+                        const int nv = std::min(PN_MAX_MDOT, j + 1 - i0);
+                        c.pb();
+                        launch_mdot<T>(h->red_blocks, c.s, n, V + int64_t(i0) * n, n, nv, w, h->d_partials);
+                        c.launched("gmres: mdot");
+                        c.pe(PN_PROF_MDOT, c.vb(nv + 1, es));
+                        c.pb();
+                        c.lk(pn::launch_reduce(h->d_partials, h->red_blocks, nv, hc + i0, c.s), "gmres: reduce");
+                        c.pe(PN_PROF_SCALAR, 0.0);
+                        c.pb();
+                        launch_maxpy<T>(nb, c.s, n, w, V + int64_t(i0) * n, n, nv, hc + i0, -1.0);
+                        c.launched("gmres: maxpy");
+                        c.pe(PN_PROF_MAXPY, c.vb(nv + 2, es));
+                    }
+                }
+                c.pb();
+                c.lk2(pn::launch_dot(h, w, w, n, dt, S + S_NRM2, c.s), "gmres: norm");
+                c.pe(PN_PROF_DOT, c.vb(1, es));
+                c.pb();
+                k_givens<<<1, 32, 0, c.s>>>(H, ldh, add, cs, sn, g, j, S, 0);
+                c.launched("gmres: givens");
+                c.pe(PN_PROF_SCALAR, 0.0);
+                c.pb();
+                k_scale_by<T><<<nb, 256, 0, c.s>>>(n, w, S, S_SCALE);
+                c.launched("gmres: scale");
+                c.pe(PN_PROF_VECTOR, c.vb(2, es));
             }
-            c.pb();
-            c.lk2(pn::launch_dot(h, w, w, n, dt, S + S_NRM2, c.s), "gmres: norm");
-            c.pe(PN_PROF_DOT, c.vb(1, es));
-            c.pb();
-            k_givens<<<1, 32, 0, c.s>>>(H, ldh, add, cs, sn, g, j, S);
-            c.launched("gmres: givens");
-            c.pe(PN_PROF_SCALAR, 0.0);
-            c.pb();
-            k_scale_by<T><<<nb, 256, 0, c.s>>>(n, w, S, S_SCALE);
-            c.launched("gmres: scale");
-            c.pe(PN_PROF_VECTOR, c.vb(2, es));
             ++total;
             if ((j + 1) % every == 0 || j + 1 == m || total >= max_iter) {
                 double r1 = 0.0;
@@ -447,7 +619,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
         for (int i0 = 0; i0 < j; i0 += PN_MAX_MDOT) {
             const int nv = std::min(PN_MAX_MDOT, j - i0);
             c.pb();
-            k_maxpy<T, PN_MAX_MDOT><<<nb, 256, 0, c.s>>>(n, x, V + int64_t(i0) * n, n, nv, y + i0, 1.0);
+            launch_maxpy<T>(nb, c.s, n, x, V + int64_t(i0) * n, n, nv, y + i0, 1.0);
             c.launched("gmres: update");
             c.pe(PN_PROF_MAXPY, c.vb(nv + 2, es));
         }
@@ -482,7 +654,7 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st) {
         c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r64, PN_F64, h->d_partials, c.s), "ir: residual");
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, 8.0, false));
         c.pb();
-        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h), 1, S + S_RR, c.s), "ir: reduce");
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, PN_F64), 1, S + S_RR, c.s), "ir: reduce");
         c.pe(PN_PROF_SCALAR, 0.0);
         double rr = 0.0;
         if (!c.read(S_RR, 1, &rr)) break;
@@ -503,7 +675,8 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st) {
         // inner tolerance: relative reduction, but not beyond what the outer target needs
         double itol = o.inner_tol;
         if (rel > 0.0 && o.tol / rel > itol) itol = std::min(0.5, o.tol / rel);
-        rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel);
+        rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel,
+                          o.ortho);
         if (rc != PN_OK) break;
         c.pb();
         k_add_f32_scaled<<<nb, 256, 0, c.s>>>(n, x, d32, S, S_MAXPY);
@@ -536,6 +709,7 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
         return pn_fail(h, PN_ERR_ARG, "pn_solve: bad precision");
     if (o.solver != PN_SOLVER_CGLS && (o.restart < 1 || o.restart > 200))
         return pn_fail(h, PN_ERR_ARG, "pn_solve: restart must be in [1, 200]");
+    if (o.ortho != PN_ORTHO_CGS2 && o.ortho != PN_ORTHO_CGS1) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad ortho");
     pn_solve_stats st{};
     Ctx c{h, (cudaStream_t)stream};
     pn_prof_reset(h, o.profile != 0);
@@ -547,9 +721,11 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
         int it = 0;
         double rel = 0.0;
         if (o.precision == PN_F32)
-            rc = gmres<float>(c, (float*)u, nullptr, h->q_norm2, o.tol, o.restart, o.max_iter, o.check_every, &it, &rel);
+            rc = gmres<float>(c, (float*)u, nullptr, h->q_norm2, o.tol, o.restart, o.max_iter, o.check_every, &it, &rel,
+                              o.ortho);
         else
-            rc = gmres<double>(c, (double*)u, nullptr, h->q_norm2, o.tol, o.restart, o.max_iter, o.check_every, &it, &rel);
+            rc = gmres<double>(c, (double*)u, nullptr, h->q_norm2, o.tol, o.restart, o.max_iter, o.check_every, &it,
+                               &rel, o.ortho);
         st.iterations = it;
         st.rel_residual = rel;
         if (rc == PN_OK && rel > o.tol) rc = pn_fail(h, PN_ERR_NOT_CONVERGED, "gmres: max_iter reached");

@@ -42,7 +42,7 @@ ERROR_NAMES = {
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["pn_create", "pn_destroy", "pn_get_layout", "pn_last_error", "pn_apply", "pn_apply_t",
            "pn_residual", "pn_dot", "pn_axpby", "pn_default_solve_opts", "pn_solve", "pn_profile_get",
-           "pn_dot_noalloc"]
+           "pn_dot_noalloc", "pn_single_scatter_beam", "pn_unstagger"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar"]
 
 
@@ -67,7 +67,8 @@ class _Layout(ctypes.Structure):
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
+                ("ortho", ctypes.c_int)]
 
 
 class _SolveStats(ctypes.Structure):
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_solve": (i, [vp, vp, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveStats), vp]),
         "pn_profile_get": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d)]),
         "pn_dot_noalloc": (i, [vp, vp, i64, i, ctypes.POINTER(d), vp]),
+        "pn_single_scatter_beam": (i, [i, i, vp, vp, d, d, i, i, d, d, d, vp, i, vp]),
+        "pn_unstagger": (i, [vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +165,33 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def single_scatter_beam(N: int, sigma_t, albedo, g: float, axis: int, sign: int, radius: float,
+                        centre=(0.5, 0.5), stream=None):
+    """Voxel-centre moments (K, R, R, R) of the single-scattered light of a
+    collimated beam (pn_single_scatter_beam).  sigma_t (and albedo, unless a
+    scalar) are CUDA tensors of shape (R, R, R); the result has their dtype."""
+    torch = _torch()
+    lib = load_library()
+    st = sigma_t.contiguous()
+    if not (st.is_cuda and st.dim() == 3 and st.shape[0] == st.shape[1] == st.shape[2]):
+        raise TypeError("sigma_t must be a cubic CUDA tensor")
+    R = st.shape[0]
+    K = (N + 1) ** 2
+    al_p, al_c = None, 0.0
+    if np.isscalar(albedo):
+        al_c = float(albedo)
+    else:
+        al = albedo.to(st.dtype).contiguous()
+        al_p = ctypes.c_void_p(al.data_ptr())
+    out = torch.empty((K, R, R, R), dtype=st.dtype, device=st.device)
+    rc = lib.pn_single_scatter_beam(int(N), int(R), ctypes.c_void_p(st.data_ptr()), al_p, al_c, float(g), int(axis),
+                                    int(sign), float(radius), float(centre[0]), float(centre[1]),
+                                    ctypes.c_void_p(out.data_ptr()), _dtype_code(st), _stream_ptr(stream))
+    if rc != PN_OK:
+        raise PnError(rc, "pn_single_scatter_beam failed")
+    return out
 
 
 def dot_noalloc(x, y, stream=None) -> float:
@@ -334,7 +364,7 @@ class System:
 
     def solve(self, u, solver: str = "cgls", tol: float = 1e-6, max_iter: int = 100000, restart: int = 60,
               inner_tol: float = 1e-2, max_outer: int = 50, check_every: int = 10, stream=None,
-              raise_on_error: bool = True, profile: bool = False) -> dict:
+              raise_on_error: bool = True, profile: bool = False, ortho: str = "cgs2") -> dict:
         """Solve A u = Q in place (u is the initial guess).  Returns the stats."""
         up, dt = self._vec(u)
         o = _SolveOpts()
@@ -346,6 +376,7 @@ class System:
         o.tol, o.max_iter, o.restart = float(tol), int(max_iter), int(restart)
         o.inner_tol, o.max_outer, o.check_every = float(inner_tol), int(max_outer), int(check_every)
         o.profile = 1 if profile else 0
+        o.ortho = {"cgs2": 0, "cgs1": 1}[ortho]
         st = _SolveStats()
         rc = self._lib.pn_solve(self._h, up, ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
         stats = {"status": rc, "iterations": st.iterations, "outer_iterations": st.outer_iterations,
@@ -362,6 +393,15 @@ class System:
             ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
             self._check(self._lib.pn_profile_get(self._h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
             out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
+        return out
+
+    def unstagger(self, x, stream=None):
+        """Padded vector -> (K, R, R, R) tensor of voxel-centre values."""
+        torch = _torch()
+        xp, dt = self._vec(x)
+        R = self.layout.R
+        out = torch.empty((self.layout.K, R, R, R), dtype=x.dtype, device=x.device)
+        self._check(self._lib.pn_unstagger(self._h, xp, ctypes.c_void_p(out.data_ptr()), dt, _stream_ptr(stream)))
         return out
 
     # -- layout marshalling -------------------------------------------------

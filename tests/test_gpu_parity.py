@@ -52,7 +52,9 @@ def _compare(y_gpu, y_ref, scale, tol):
     assert rel <= tol, f"relative L2 {rel:.3e}"
 
 
-CASES = [(0, 5), (1, 2), (1, 9), (3, 5), (3, 17), (5, 9), (7, 3), (7, 6)]
+# sizes span one and several x-tiles (32 wide), the columns right of the
+# tiles (R a multiple of 32), several z-chunks, and ragged y-tiles
+CASES = [(0, 5), (1, 2), (1, 9), (3, 5), (3, 17), (5, 9), (7, 3), (7, 6), (3, 32), (1, 33), (2, 40), (5, 20)]
 
 
 @pytest.mark.parametrize("N,R", CASES)
@@ -289,3 +291,78 @@ def test_full_size_fp32_apply_sampled(which):
     gpu.close()
     del x, y, r
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("ortho", ["cgs2", "cgs1"])
+def test_ir_with_each_orthogonalisation_meets_oracle_residual(ortho):
+    """Both Gram-Schmidt variants of the FP32 inner GMRES give an FP64-refined
+    solution whose oracle residual is <= 1e-6."""
+    from paper_1807_00410_gb300 import System
+    N, R = 5, 12
+    p = pn_inputs.fbm_point(N, R, 7, 0.5, 40.0, 0.95, 0.3)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00)
+    S = opn.assemble(N, R, med)
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver="ir", tol=1e-6, restart=20, ortho=ortho, profile=True)
+    assert st["rel_residual"] <= 1e-6
+    assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u))) <= 1.0001e-6
+    prof = gpu.profile()
+    assert prof["apply"]["launches"] >= st["iterations"]
+    assert prof["mdot"]["launches"] > 0 and prof["apply"]["ms"] > 0
+    assert st["launches"] > prof["apply"]["launches"]
+    gpu.close()
+
+
+# --- source building and unstaggering ---------------------------------------------
+
+@pytest.mark.parametrize("dtype,axis,sign", [("f64", 0, 1), ("f64", 2, -1), ("f32", 1, 1)])
+def test_single_scatter_beam_matches_oracle(dtype, axis, sign):
+    from oracle import source as osrc
+    from paper_1807_00410_gb300 import pn as ppn
+    N, R = 5, 13
+    st = 40.0 * pn_inputs.value_noise_fbm(R, 2)
+    al = pn_inputs.random_field((R, R, R), 3, 0.5, 0.99)
+    ref = osrc.single_scatter_beam(st, al, 0.6, N, axis, sign, 0.3, (0.45, 0.55))
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    got = ppn.single_scatter_beam(N, torch.tensor(st, dtype=tdt).cuda(), torch.tensor(al, dtype=tdt).cuda(), 0.6,
+                                  axis, sign, 0.3, (0.45, 0.55)).cpu().double().numpy()
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    assert (ref != 0).sum() > 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_unstagger_matches_oracle(dtype):
+    from oracle import source as osrc
+    N, R = 3, 9
+    med, gpu = _system(N, R, 12)
+    lay_o = opn.Layout(N, R)
+    planes = _rand_planes(lay_o, 5)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    out = gpu.unstagger(gpu.from_planes(planes, dtype=tdt)).cpu().double().numpy()
+    if dtype == "f32":
+        planes = [p.astype(np.float32).astype(np.float64) for p in planes]
+    ref = osrc.unstagger(lay_o, planes)
+    np.testing.assert_allclose(out, ref, atol=1e-12 if dtype == "f64" else 1e-6)
+    gpu.close()
+
+
+def test_beam_source_solve_end_to_end():
+    """Beam single-scatter moments built on the GPU feed pn_create as centre
+    moments; the FP64-refined solve meets the oracle's residual on the same Q."""
+    from oracle import source as osrc
+    from paper_1807_00410_gb300 import System
+    from paper_1807_00410_gb300 import pn as ppn
+    N, R = 3, 12
+    p = pn_inputs.cloud_point(N, R, 4, sig_max=30.0, albedo=0.9, g=0.5, sigma_t_min=0.5)
+    st_d = torch.tensor(p.sigma_t, dtype=torch.float64).cuda()
+    Q = ppn.single_scatter_beam(N, st_d, p.albedo, p.g, 0, 1, 0.25)
+    gpu = System(N, R, st_d, p.albedo, p.g, Q, sigma_t_min=p.sigma_t_min)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver="ir", tol=1e-6, restart=30)
+    Qo = osrc.single_scatter_beam(p.sigma_t, p.albedo, p.g, N, 0, 1, 0.25)
+    S = opn.assemble(N, R, opn.Medium(p.sigma_t, p.albedo, p.g, Qo, p.sigma_t_min))
+    assert st["rel_residual"] <= 1e-6
+    assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u))) <= 1.001e-6
+    gpu.close()
