@@ -33,7 +33,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "P_N solve time to rel. residual 1e-6 (learned vs plain); apply GDOF/s vs HBM"
-WORKLOAD = "P5 64^3 fBm sigma_t[0.5,40] albedo 0.95 g 0.3 point source, FP32 GMRES(20) + FP64 IR to 1e-6 (plain)"
+WORKLOAD = "P5 64^3 fBm sigma_t[0.5,40] albedo 0.95 g 0.3 point source, FP32 GMRES(15) + FP64 IR to 1e-6 (plain)"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--restart", type=int, default=15)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
     ap.add_argument("--ortho", choices=["cgs2", "cgs1"], default="cgs1")
     ap.add_argument("--no-apply-scan", action="store_true", help="skip the separate operator throughput scan")

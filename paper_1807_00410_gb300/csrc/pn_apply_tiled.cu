@@ -112,7 +112,7 @@ struct Args {
     const float* ss;     // sigma_s, R^3
     int R;
     int pitch_x;
-    int64_t pitch_y, plane_stride;
+    uint32_t pitch_y, plane_stride;  // element strides (the launcher checks they fit)
     int zc;              // slices per CTA (z chunk)
     float inv_h;         // R
     float tsign;         // +1: A, -1: A^T
@@ -121,15 +121,17 @@ struct Args {
     double* partials;    // residual: per-CTA FP64 sums of r^2
 };
 
-// Load n values of class C (planes plane0..plane0+n-1) at slot z of this
-// thread's column; inactive slots read 0.
+// Load n values of one class at slot z of this thread's column; inactive
+// slots read 0.  `base` points at the class's first plane, z = 0, this column;
+// planes are ps elements apart, slices py elements apart (both < 2^32 / 4 /
+// MAXC bytes, checked by the launcher).
 template <int NV>
-__device__ __forceinline__ void load_class(const Args& a, int plane0, int n, bool colact, int z, int zext,
-                                           int64_t col, float (&v)[MAXC]) {
+__device__ __forceinline__ void load_class(const float* base, uint32_t ps, uint32_t py, bool colact, int z, int zext,
+                                           float (&v)[MAXC]) {
     const bool act = colact && z >= 0 && z < zext;
-    const int64_t off = int64_t(z) * a.pitch_y + col;
+    const float* q = base + size_t(uint32_t(z) * py);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = (i < n && act) ? __ldg(a.x + int64_t(plane0 + i) * a.plane_stride + off) : 0.0f;
+    for (int i = 0; i < NV; ++i) v[i] = act ? __ldg(q + uint32_t(i) * ps) : 0.0f;
 }
 
 template <int TY>
@@ -150,7 +152,7 @@ struct Geo {
 //   st, ss   : sigma_t, sigma_s interpolated to this class's location
 template <int N, int TY, int C, int MODE>
 __device__ __forceinline__ void compute_class(const Args& a, const float* buf, int tx, int ty, bool store_ok,
-                                              bool active, int64_t outoff, const float (&own)[MAXC],
+                                              bool active, size_t outoff, const float (&own)[MAXC],
                                               const float (&zp)[MAXC], const float (&zm)[MAXC], float st, float ss,
                                               float& rrun) {
     constexpr Tab T = TabN<N>::value;
@@ -161,6 +163,9 @@ __device__ __forceinline__ void compute_class(const Args& a, const float* buf, i
     constexpr int pX = T.cls[CXn].plane0, pY = T.cls[CYn].plane0;
     using G = Geo<TY>;
     if (CT.n == 0) return;
+    const uint32_t ps = a.plane_stride;
+    float* yb = a.y + size_t(CT.plane0) * ps + outoff;
+    const float tscale = a.tsign * a.inv_h;
     // differences of the neighbour classes across this location
     float dx[MAXC], dy[MAXC], dz[MAXC];
     const int cy = ty + 1, cx = tx + 1;
@@ -190,19 +195,19 @@ __device__ __forceinline__ void compute_class(const Args& a, const float* buf, i
             for (int t = 0; t < MAXT; ++t)
                 if (t < CT.row[i].nt[2]) tr = fmaf(CT.row[i].c[2][t], dz[CT.row[i].j[2][t]], tr);
             const float d = fmaf(-a.fl[CT.row[i].l], ss, st);
-            float out = fmaf(d, own[i], a.tsign * a.inv_h * tr);
+            float out = fmaf(d, own[i], tscale * tr);
             if (MODE == OP_RESIDUAL) {
                 // right-hand side, read only at active slots (inside the plane box)
                 float b = 0.0f;
                 if (active) {
-                    if (a.bvec) b = __ldg(a.bvec + int64_t(CT.plane0 + i) * a.plane_stride + outoff);
-                    else if (CT.plane0 + i < a.n_q) b = __ldg(a.q + int64_t(CT.plane0 + i) * a.plane_stride + outoff);
+                    if (a.bvec) b = __ldg(a.bvec + size_t(CT.plane0) * ps + outoff + uint32_t(i) * ps);
+                    else if (CT.plane0 + i < a.n_q) b = __ldg(a.q + size_t(CT.plane0) * ps + outoff + uint32_t(i) * ps);
                 }
                 out = b - out;
             }
             out = active ? out : 0.0f;
             if (MODE == OP_RESIDUAL) rrun = fmaf(out, out, rrun);
-            if (store_ok) a.y[int64_t(CT.plane0 + i) * a.plane_stride + outoff] = out;
+            if (store_ok) yb[uint32_t(i) * ps] = out;
         }
     }
 }
@@ -233,19 +238,22 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
     const int x0 = x - tx, y0 = y - ty;
     const bool colact0 = x < R + bx && y < R + by;
     const bool colact1 = colact0;  // same x/y bits
-    const int64_t col = int64_t(y) * a.pitch_x + x;
+    const uint32_t col = uint32_t(y) * uint32_t(a.pitch_x) + uint32_t(x);
     const bool store_ok = x < a.pitch_x && y <= R;
+    const uint32_t ps = a.plane_stride, py = a.pitch_y;
+    const float* xb0 = a.x + size_t(p0) * ps + col;  // class C0, z = 0, this column
+    const float* xb1 = a.x + size_t(p1) * ps + col;
 
     // halo cells owned by this thread: plane p, shared index, global column offset
     constexpr int NH = (K * G::HALO + G::NT - 1) / G::NT;
     int h_sidx[NH];
-    int64_t h_goff[NH];
+    const float* h_ptr[NH];
     int h_zext[NH];  // 0: cell inactive in x/y; else the plane's z extent
 #pragma unroll
     for (int u = 0; u < NH; ++u) {
         const int h = tid + u * G::NT;
         h_sidx[u] = -1;
-        h_goff[u] = 0;
+        h_ptr[u] = a.x;
         h_zext[u] = 0;
         if (h < K * G::HALO) {
             const int p = h / G::HALO, r = h % G::HALO;
@@ -266,7 +274,7 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
             h_sidx[u] = p * G::SLICE + sy * G::SX + sx;
             const bool act = hx >= 0 && hy >= 0 && hx < R + pbx && hy < R + pby;
             h_zext[u] = act ? R + pbz : 0;
-            h_goff[u] = int64_t(p) * a.plane_stride + int64_t(hy) * a.pitch_x + hx;
+            if (act) h_ptr[u] = a.x + size_t(p) * ps + uint32_t(hy) * uint32_t(a.pitch_x) + uint32_t(hx);
         }
     }
     // sigma tile cell owned by this thread (two fields)
@@ -288,14 +296,14 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
     // priming: sigma slice za-1 -> xy-means of the previous slice
     if (sg_own) sg[((za + 1) & 1) * 2 * G::GSL + tid] = sg_load(za - 1);
     float v0p[MAXC] = {}, v0c[MAXC] = {}, v0n[MAXC] = {}, v1c[MAXC] = {}, v1n[MAXC] = {};
-    load_class<n0>(a, p0, n0, colact0, za - 1, R, col, v0p);
-    load_class<n0>(a, p0, n0, colact0, za, R, col, v0c);
-    load_class<n1>(a, p1, n1, colact1, za, R + 1, col, v1c);
-    load_class<n1>(a, p1, n1, colact1, za + 1, R + 1, col, v1n);
+    load_class<n0>(xb0, ps, py, colact0, za - 1, R, v0p);
+    load_class<n0>(xb0, ps, py, colact0, za, R, v0c);
+    load_class<n1>(xb1, ps, py, colact1, za, R + 1, v1c);
+    load_class<n1>(xb1, ps, py, colact1, za + 1, R + 1, v1n);
     float hreg[NH];
 #pragma unroll
     for (int u = 0; u < NH; ++u)
-        hreg[u] = (h_sidx[u] >= 0 && za < h_zext[u]) ? __ldg(a.x + h_goff[u] + int64_t(za) * a.pitch_y) : 0.0f;
+        hreg[u] = (za < h_zext[u]) ? __ldg(h_ptr[u] + size_t(uint32_t(za) * py)) : 0.0f;
     float sreg = sg_load(za);
     __syncthreads();
     float mt_prev, ms_prev;
@@ -320,17 +328,17 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
             if (h_sidx[u] >= 0) b[h_sidx[u]] = hreg[u];
         if (sg_own) g[tid] = sreg;
         // prefetch slice s+1 (and s+2 for the odd class)
-        load_class<n0>(a, p0, n0, colact0, s + 1, R, col, v0n);
+        load_class<n0>(xb0, ps, py, colact0, s + 1, R, v0n);
         float v1t[MAXC] = {};
-        load_class<n1>(a, p1, n1, colact1, s + 2, R + 1, col, v1t);
+        load_class<n1>(xb1, ps, py, colact1, s + 2, R + 1, v1t);
 #pragma unroll
         for (int u = 0; u < NH; ++u)
-            hreg[u] = (h_sidx[u] >= 0 && s + 1 < h_zext[u]) ? __ldg(a.x + h_goff[u] + int64_t(s + 1) * a.pitch_y) : 0.0f;
+            hreg[u] = (s + 1 < h_zext[u]) ? __ldg(h_ptr[u] + size_t(uint32_t(s + 1) * py)) : 0.0f;
         sreg = sg_load(s + 1);
         __syncthreads();
         const float mt = xy_mean<TY>(g, tx, ty, bx, by);
         const float ms = xy_mean<TY>(g + G::GSL, tx, ty, bx, by);
-        const int64_t outoff = int64_t(s) * a.pitch_y + col;
+        const size_t outoff = size_t(uint32_t(s) * py) + col;
         // even class (bz = 0): z-neighbours are the odd class at s+1 (plus) and s (minus)
         compute_class<N, TY, C0, MODE>(a, b, tx, ty, store_ok, colact0 && s < R, outoff, v0c, v1n, v1c, mt, ms,
                                        rrun);
@@ -406,9 +414,9 @@ TiledPlan plan_for(const pn_handle* h) {
     const int nxt = (R + tiled::TX - 1) / tiled::TX;
     const int nyt = (R + 1 + TY - 1) / TY;
     const int sms = pn_sm_count();
-    // z chunks: enough CTAs for about 4 per SM, chunks of at least 16 slices
+    // z chunks: enough CTAs for about 4 per SM, chunks of at least 4 slices
     int nzc = std::max(1, (4 * sms + nxt * nyt - 1) / (nxt * nyt));
-    nzc = std::min(nzc, std::max(1, (R + 1) / 16));
+    nzc = std::min(nzc, std::max(1, (R + 1) / 4));
     const int zc = (R + 1 + nzc - 1) / nzc;
     nzc = (R + 1 + zc - 1) / zc;
     p.grid = dim3(nxt, nyt, nzc);
@@ -470,8 +478,8 @@ cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y,
     a.ss = h->d_ss_f;
     a.R = h->R;
     a.pitch_x = int(h->pitch_x);
-    a.pitch_y = h->pitch_y;
-    a.plane_stride = h->plane_stride;
+    a.pitch_y = uint32_t(h->pitch_y);
+    a.plane_stride = uint32_t(h->plane_stride);
     a.zc = p.zc;
     a.inv_h = float(h->R);
     a.tsign = mode == OP_APPLY_T ? -1.0f : 1.0f;

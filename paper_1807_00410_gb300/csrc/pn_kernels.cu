@@ -191,7 +191,8 @@ static int slab_grid_x(const pn_handle* h) {
 }
 
 int op_partial_count(const pn_handle* h, int dtype) {
-    if (dtype == PN_F32) return tiled_partial_count(h) + slab_grid_x(h) * h->K;
+    if (dtype == PN_F32 && h->plane_stride * 16 < (int64_t(1) << 32))
+        return tiled_partial_count(h) + slab_grid_x(h) * h->K;
     return naive_grid_x(h) * h->K;
 }
 
@@ -213,7 +214,10 @@ static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T*
 
 cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
                       double* partials, cudaStream_t s, const void* bvec) {
-    if (dtype == PN_F32) {
+    // the tiled kernel forms addresses with 32-bit element offsets of up to
+    // MAXC planes: it needs plane_stride * 16 < 2^32 (R <= 1000 or so)
+    const bool tiled_ok = h->plane_stride * 16 < (int64_t(1) << 32);
+    if (dtype == PN_F32 && tiled_ok) {
         // tiled kernel for x < x_end, generic slab kernel for the rest
         cudaError_t e = launch_tiled(h, mode, (const float*)x, (float*)y, (const float*)bvec, partials, s);
         if (e != cudaSuccess) return e;
@@ -238,7 +242,7 @@ cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int 
 
 static int g_reduce_blocks = 0;
 int reduce_blocks() {
-    if (g_reduce_blocks == 0) g_reduce_blocks = 4 * pn_sm_count();
+    if (g_reduce_blocks == 0) g_reduce_blocks = 2 * pn_sm_count();
     return g_reduce_blocks;
 }
 

@@ -22,7 +22,7 @@ namespace {
 // scalar slots in h->d_scalars
 enum { S_RR = 0, S_QQ = 1, S_G0 = 2, S_G1 = 3, S_BETA2 = 4, S_RES = 5, S_SCALE = 6, S_NRM2 = 7, S_MAXPY = 64 };
 
-int nb_vec() { return 8 * pn_sm_count(); }
+int nb_vec() { return 4 * pn_sm_count(); }
 
 __device__ __forceinline__ double warp_block_sum(double v) {
     __shared__ double red[32];
@@ -120,9 +120,31 @@ __global__ void __launch_bounds__(256) k_mdot(int64_t n, const T* V, int64_t vst
     }
 }
 
-constexpr int kRun = 8;
+constexpr int kRun = 16;
 
-// With self_dot, slot nv also receives w . w (one extra accumulator).
+// Sums acc[0..nv) (and acc[NV] if self_dot) over the block: every thread
+// stores its FP64 partials in shared memory, then warp w sums the values of
+// vectors w, w + 8, ... (eight strided FP64 adds per lane, then a shuffle
+// tree), so the FP64 work per block is a few hundred adds per vector.
+template <int NV>
+__device__ __forceinline__ void block_sum_multi(const double (&acc)[NV + 1], int nv, int self_dot, double* out,
+                                                int64_t out_stride) {
+    __shared__ double red[NV + 1][256];
+#pragma unroll
+    for (int j = 0; j <= NV; ++j) red[j][threadIdx.x] = acc[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nvals = nv + (self_dot ? 1 : 0);
+    for (int v = warp; v < nvals; v += 8) {
+        const int j = v < nv ? v : NV;  // the self-dot lives in slot NV
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[j][lane + 32 * q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) out[int64_t(v) * out_stride] = t;
+    }
+}
+
 template <int NV>
 __global__ void __launch_bounds__(256) k_mdot_f32(int64_t n4, const float4* V, int64_t vstride4, int nv,
                                                   const float4* w, double* partials, int self_dot) {
@@ -149,20 +171,10 @@ __global__ void __launch_bounds__(256) k_mdot_f32(int64_t n4, const float4* V, i
 #pragma unroll
         for (int j = 0; j <= NV; ++j) acc[j] += double(part[j]);
     }
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        if (j < nv) {
-            const double bs = warp_block_sum(acc[j]);
-            if (threadIdx.x == 0) partials[int64_t(j) * gridDim.x + blockIdx.x] = bs;
-        }
-    }
-    if (self_dot) {
-        const double bs = warp_block_sum(acc[NV]);
-        if (threadIdx.x == 0) partials[int64_t(nv) * gridDim.x + blockIdx.x] = bs;
-    }
+    // partials[v * gridDim.x + block]; the self-dot goes to slot v = nv
+    block_sum_multi<NV>(acc, nv, self_dot, partials + blockIdx.x, gridDim.x);
 }
 
-// w += sign * sum_j c[j] V_j   (c in FP64 on the device, applied in T)
 // w = (w + sign * sum_j c[j] V_j) * scale, scale = *scale_p (1 if null)
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_maxpy(int64_t n, T* w, const T* V, int64_t vstride, int nv,
