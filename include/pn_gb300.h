@@ -88,6 +88,7 @@ extern "C" {
 #define PN_MAX_K 64
 
 typedef struct pn_handle pn_handle;
+typedef struct pn_cnn pn_cnn;
 
 /* Voxel-centre medium.  Arrays are indexed [z][y][x] (x fastest), R^3 each. */
 typedef struct {
@@ -162,6 +163,8 @@ int pn_axpby(pn_handle* h, double alpha, const void* x, double beta, void* y, in
 #define PN_SOLVER_CGLS     0     /* CG on the normal equations (the paper) */
 #define PN_SOLVER_GMRES    1     /* restarted GMRES(m) on A u = Q */
 #define PN_SOLVER_IR_GMRES 2     /* FP64 iterative refinement, FP32 GMRES inner */
+#define PN_SOLVER_IR_FGMRES 3    /* FP64 iterative refinement, FP32 flexible GMRES inner,
+                                    right-preconditioned by the learned network opts->precond */
 
 typedef struct {
     int solver;          /* PN_SOLVER_* */
@@ -177,6 +180,8 @@ typedef struct {
     int ortho;           /* GMRES orthogonalisation: PN_ORTHO_CGS2 (classical
                             Gram-Schmidt twice) or PN_ORTHO_CGS1 (once, norm of
                             the new vector by Pythagoras, half the traffic) */
+    void* precond;       /* PN_SOLVER_IR_FGMRES: the pn_cnn network (c_in = K + 3,
+                            c_out = K) of pn_cnn_precondition; R a multiple of 8 */
 } pn_solve_opts;
 
 #define PN_ORTHO_CGS2 0
@@ -189,6 +194,8 @@ typedef struct {
     double rel_residual; /* final ||Q - A u|| / ||Q|| in FP64 */
     double seconds;      /* host wall time of the call */
     int64_t launches;    /* CUDA kernels the solve launched */
+    int precond_applications; /* learned-preconditioner applications */
+    int fallback;        /* 1 if the learned preconditioner was dropped for plain GMRES */
 } pn_solve_stats;
 
 /* Fill *opts with defaults (CGLS, FP64, tol 1e-6, max_iter 100000, m 60,
@@ -233,6 +240,42 @@ int pn_single_scatter_beam(int N, int R, const void* sigma_t, const void* albedo
  */
 int pn_unstagger(pn_handle* h, const void* x, void* out, int dtype, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner network (an extension; the paper has no network).
+ * A 3D convolutional encoder-decoder: four resolution levels of widths
+ * widths[0..3] (default 16, 32, 48, 64), two 3x3x3 convolutions with ReLU per
+ * encoder level, 2x average pooling down, nearest 2x upsampling up with skip
+ * connections by channel concatenation, one 3x3x3 convolution with ReLU per
+ * decoder level, and a linear 3x3x3 output layer to c_out channels.  BF16
+ * weights and activations on the tensor cores with FP32 accumulation; FP32
+ * master weights trained by Adam.  Tensors at the ABI are FP32 device arrays,
+ * channels-last [b][z][y][x][c], with Z, Y, X multiples of 8.
+ * Host parameter order: per layer (e0a e0b e1a e1b e2a e2b e3a e3b d2 d1 d0
+ * out) the weights W[o][c][tap] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1), the
+ * convolution reads in[c][p + (dz,dy,dx)]) then the biases b[o].
+ */
+int pn_cnn_create(pn_cnn** out, int c_in, int c_out, const int widths[4]);
+int pn_cnn_destroy(pn_cnn* net);
+const char* pn_cnn_last_error(const pn_cnn* net);
+int64_t pn_cnn_num_params(const pn_cnn* net);
+/* copy parameters (host FP32, count = pn_cnn_num_params) in / out; setting
+ * resets the Adam state */
+int pn_cnn_set_params(pn_cnn* net, const float* host, int64_t count);
+int pn_cnn_get_params(pn_cnn* net, float* host, int64_t count);
+/* gradients of the last pn_cnn_backward / pn_cnn_train_step (host FP32) */
+int pn_cnn_get_grads(pn_cnn* net, float* host, int64_t count);
+/* out = net(in): in [B][Z][Y][X][c_in], out [B][Z][Y][X][c_out] (or NULL) */
+int pn_cnn_forward(pn_cnn* net, const float* in, float* out, int B, int Z, int Y, int X, void* stream);
+/* parameter gradients of sum(grad_out * net(in)) for the last forward input */
+int pn_cnn_backward(pn_cnn* net, const float* grad_out, void* stream);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) with the current gradients */
+int pn_cnn_adam_step(pn_cnn* net, double lr, void* stream);
+/* forward, loss = mean over samples of |net(in_b) - target_b|^2 / |target_b|^2,
+ * backward and one Adam step; *loss_out (host) = the loss before the step
+ * (synchronises when loss_out is not NULL).  B <= 4096. */
+int pn_cnn_train_step(pn_cnn* net, const float* in, const float* target, int B, int Z, int Y, int X, double lr,
+                      double* loss_out, void* stream);
+
 /*
  * *out (host) = sum_i x_i y_i for i < n, without allocating anything.
  * The paper has no counterpart: this is a service for callers that cannot
@@ -257,6 +300,22 @@ int pn_unstagger(pn_handle* h, const void* x, void* out, int dtype, void* stream
 #define PN_NOALLOC_MAX_ELEMS (1LL << 31)
 int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype, double* out, void* stream);
 
+/*
+ * The learned preconditioner M(v) = |v| net(features(v / |v|)) + D^{-1} v
+ * (an extension; the paper has no preconditioner).  features(u): for each
+ * voxel (x, y, z) < R, channel p = u in plane p at slot (x, y, z), then
+ * log(sigma_t h), sigma_s / sigma_t and g (c_in = K + 3); the network's K
+ * output channels return to slot (x, y, z) of each plane; D is the
+ * collision-minus-scattering diagonal.  R must be a multiple of 8.
+ * pn_cnn_features writes scale * features(v) ([R^3][K+3], FP32, device);
+ * pn_cnn_targets writes the training target scale * (e - D^{-1} r) at the
+ * cells' own slots ([R^3][K]); pn_cnn_precondition writes z = M(v) (device
+ * FP32 padded vectors; allocates scratch; synchronises).
+ */
+int pn_cnn_features(pn_handle* h, const float* v, double scale, float* out, void* stream);
+int pn_cnn_targets(pn_handle* h, const float* e, const float* r, double scale, float* out, void* stream);
+int pn_cnn_precondition(pn_handle* h, pn_cnn* net, const float* v, float* z, void* stream);
+
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */
 #define PN_PROF_RESIDUAL 1   /* residual operator launches */
@@ -265,7 +324,8 @@ int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype, double* o
 #define PN_PROF_DOT      4   /* single inner products and their reductions */
 #define PN_PROF_VECTOR   5   /* axpy-type updates, scaling, conversions */
 #define PN_PROF_SCALAR   6   /* one-thread scalar kernels and final reductions */
-#define PN_PROF_KINDS    7
+#define PN_PROF_PRECOND  7   /* learned-preconditioner applications (network + glue) */
+#define PN_PROF_KINDS    8
 
 /*
  * Per-class totals of the last pn_solve run with opts->profile = 1 (zeros

@@ -182,6 +182,7 @@ void pn_default_solve_opts(pn_solve_opts* o) {
     o->check_every = 10;
     o->profile = 0;
     o->ortho = PN_ORTHO_CGS2;
+    o->precond = nullptr;
 }
 
 int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream) {

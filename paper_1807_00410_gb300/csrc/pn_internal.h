@@ -128,6 +128,12 @@ int reduce_blocks();
 
 }  // namespace pn
 
+namespace pn {
+// z = M(v), the learned preconditioner (pn_precond.cu); scratch: R^3 (2K+3) floats.
+int precond_apply(pn_handle* h, struct pn_cnn* net, const float* v, float* z, float* scratch, double* nrm2_dev,
+                  cudaStream_t s);
+}
+
 // Profiler helpers (pn_api.cu).  prof_begin/prof_end bracket one launch on
 // stream s; prof_drain reads out completed pairs (call after a sync).
 void pn_prof_begin(pn_handle* h, cudaStream_t s);

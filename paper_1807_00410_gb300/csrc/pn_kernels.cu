@@ -191,8 +191,7 @@ static int slab_grid_x(const pn_handle* h) {
 }
 
 int op_partial_count(const pn_handle* h, int dtype) {
-    if (dtype == PN_F32 && h->plane_stride * 16 < (int64_t(1) << 32))
-        return tiled_partial_count(h) + slab_grid_x(h) * h->K;
+    if (dtype == PN_F32 && h->plane_stride * 16 < (int64_t(1) << 32)) return tiled_partial_count(h);
     return naive_grid_x(h) * h->K;
 }
 
@@ -218,21 +217,8 @@ cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int 
     // MAXC planes: it needs plane_stride * 16 < 2^32 (R <= 1000 or so)
     const bool tiled_ok = h->plane_stride * 16 < (int64_t(1) << 32);
     if (dtype == PN_F32 && tiled_ok) {
-        // tiled kernel for x < x_end, generic slab kernel for the rest
-        cudaError_t e = launch_tiled(h, mode, (const float*)x, (float*)y, (const float*)bvec, partials, s);
-        if (e != cudaSuccess) return e;
-        OpArgs<float> a;
-        a.x = (const float*)x; a.y = (float*)y; a.q = h->d_q_f; a.n_q = h->n_q_planes; a.bvec = (const float*)bvec;
-        a.st = h->d_st_f; a.ss = h->d_ss_f;
-        a.planes = h->d_planes; a.terms = h->d_terms;
-        a.R = h->R; a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
-        a.partials = partials ? partials + tiled_partial_count(h) : nullptr;
-        dim3 grid(slab_grid_x(h), h->K);
-        const int x_lo = tiled_x_end(h);
-        if (mode == OP_APPLY) k_op_slab<float, OP_APPLY><<<grid, 256, 0, s>>>(a, x_lo);
-        else if (mode == OP_APPLY_T) k_op_slab<float, OP_APPLY_T><<<grid, 256, 0, s>>>(a, x_lo);
-        else k_op_slab<float, OP_RESIDUAL><<<grid, 256, 0, s>>>(a, x_lo);
-        return cudaGetLastError();
+        // tiled kernel for x < x_end, face-column kernel for the rest
+        return launch_tiled(h, mode, (const float*)x, (float*)y, (const float*)bvec, partials, s);
     }
     return op_t<double>(h, mode, (const double*)x, (double*)y, h->d_st_d, h->d_ss_d, h->d_q_d,
                         (const double*)bvec, partials, s);

@@ -20,7 +20,8 @@
 namespace {
 
 // scalar slots in h->d_scalars
-enum { S_RR = 0, S_QQ = 1, S_G0 = 2, S_G1 = 3, S_BETA2 = 4, S_RES = 5, S_SCALE = 6, S_NRM2 = 7, S_MAXPY = 64 };
+enum { S_RR = 0, S_QQ = 1, S_G0 = 2, S_G1 = 3, S_BETA2 = 4, S_RES = 5, S_SCALE = 6, S_NRM2 = 7, S_MAXPY = 64,
+       S_PNRM = 65 };
 
 int nb_vec() { return 4 * pn_sm_count(); }
 
@@ -496,20 +497,27 @@ int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
 // ||b|| (bnorm2 = ||b||^2).  Adds the inner iterations to *iters.
 template <typename T>
 int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max_iter, int check_every,
-          int* iters, double* rel_out, int ortho = PN_ORTHO_CGS2) {
+          int* iters, double* rel_out, int ortho = PN_ORTHO_CGS2, struct pn_cnn* net = nullptr,
+          int* papps = nullptr, int* fell_back = nullptr) {
     pn_handle* h = c.h;
     const int64_t n = h->n_elems;
     const int dt = sizeof(T) == 4 ? PN_F32 : PN_F64;
     const double es = sizeof(T);
     const int nb = nb_vec();
     double* S = h->d_scalars;
-    // workspace: V (m+1 vectors), then FP64 H ((m+1) x m), cs, sn, g, y, add
-    const size_t vbytes = size_t(m + 1) * n * sizeof(T);
+    // workspace: V (m+1 vectors), [Z (m vectors), preconditioner scratch],
+    // then FP64 H ((m+1) x m), cs, sn, g, y, add
+    if (net && (sizeof(T) != 4 || h->R % 8)) net = nullptr;  // the network runs on FP32, R % 8 == 0
+    const int64_t V3 = int64_t(h->R) * h->R * h->R;
+    const size_t zbytes = net ? size_t(m) * n * sizeof(T) + size_t(V3) * (2 * h->K + 3) * sizeof(float) + 256 : 0;
+    const size_t vbytes = size_t(m + 1) * n * sizeof(T) + zbytes;
     const int ldh = m + 1;
     const size_t dcount = size_t(ldh) * m + 4 * size_t(m + 1) + 16 * size_t(m + 1);
     int rc = ensure_work(h, vbytes + dcount * sizeof(double) + 256);
     if (rc != PN_OK) return rc;
     T* V = (T*)h->d_work;
+    T* Zb = V + int64_t(m + 1) * n;
+    float* pscratch = (float*)(((uintptr_t)(Zb + int64_t(m) * n) + 255) / 256 * 256);
     double* H = (double*)((char*)h->d_work + ((vbytes + 255) / 256) * 256);
     double* cs = H + size_t(ldh) * m;
     double* sn = cs + (m + 1);
@@ -519,7 +527,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
     const double bnorm = std::sqrt(bnorm2);
     const double target = tol * (bnorm > 0.0 ? bnorm : 1.0);
     int total = 0;
-    double res = 0.0;
+    double res = 0.0, res_cycle = -1.0;
     const int every = check_every > 0 ? check_every : 1;
     for (;;) {
         // r = b - A x into V_0, beta = ||r||
@@ -534,6 +542,13 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
         res = std::sqrt(b2);
         if (!std::isfinite(res)) return pn_fail(h, PN_ERR_NONFINITE, "gmres: non-finite residual");
         if (res <= target || total >= max_iter) break;
+        // fallback: a learned cycle that removed less than 10 % of the residual
+        // hands the rest of the solve to plain GMRES
+        if (net && res_cycle > 0.0 && res > 0.9 * res_cycle) {
+            net = nullptr;
+            if (fell_back) *fell_back = 1;
+        }
+        res_cycle = res;
         c.pb();
         k_gm_init<<<1, 32, 0, c.s>>>(g, m, S);
         c.launched("gmres: init");
@@ -545,8 +560,20 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
         int j = 0;
         for (; j < m && total < max_iter; ++j) {
             T* w = V + int64_t(j + 1) * n;
+            const T* av = V + int64_t(j) * n;
+            if (net) {
+                // z_j = M(v_j); w = A z_j
+                T* zj = Zb + int64_t(j) * n;
+                c.pb();
+                const int prc = pn::precond_apply(h, net, (const float*)av, (float*)zj, pscratch, S + S_PNRM, c.s);
+                if (prc != PN_OK) return prc;
+                c.launches += 36;
+                c.pe(PN_PROF_PRECOND, 0.0);
+                if (papps) ++*papps;
+                av = zj;
+            }
             c.pb();
-            c.lk(pn::launch_op(h, pn::OP_APPLY, V + int64_t(j) * n, w, dt, nullptr, c.s), "gmres: A v");
+            c.lk(pn::launch_op(h, pn::OP_APPLY, av, w, dt, nullptr, c.s), "gmres: A v");
             c.pe(PN_PROF_APPLY, c.ob(pn::OP_APPLY, es, false));
             if (ortho == PN_ORTHO_CGS1) {
                 // classical Gram-Schmidt once: all projections and ||w||^2 in one
@@ -628,10 +655,11 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
         k_gm_backsolve<<<1, 32, 0, c.s>>>(H, ldh, g, y, j);
         c.launched("gmres: backsolve");
         c.pe(PN_PROF_SCALAR, 0.0);
+        const T* basis = net ? Zb : V;  // x += Z y (flexible) or V y
         for (int i0 = 0; i0 < j; i0 += PN_MAX_MDOT) {
             const int nv = std::min(PN_MAX_MDOT, j - i0);
             c.pb();
-            launch_maxpy<T>(nb, c.s, n, x, V + int64_t(i0) * n, n, nv, y + i0, 1.0);
+            launch_maxpy<T>(nb, c.s, n, x, basis + int64_t(i0) * n, n, nv, y + i0, 1.0);
             c.launched("gmres: update");
             c.pe(PN_PROF_MAXPY, c.vb(nv + 2, es));
         }
@@ -642,8 +670,9 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
     return c.rc;
 }
 
-int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st) {
+int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, struct pn_cnn* net = nullptr) {
     pn_handle* h = c.h;
+    int fell_back = 0;
     const int64_t n = h->n_elems;
     // r64 and the FP32 rhs / correction live outside the GMRES workspace
     double* r64 = nullptr;
@@ -688,7 +717,8 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st) {
         double itol = o.inner_tol;
         if (rel > 0.0 && o.tol / rel > itol) itol = std::min(0.5, o.tol / rel);
         rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel,
-                          o.ortho);
+                          o.ortho, net, &st.precond_applications, &fell_back);
+        if (fell_back) net = nullptr;
         if (rc != PN_OK) break;
         c.pb();
         k_add_f32_scaled<<<nb, 256, 0, c.s>>>(n, x, d32, S, S_MAXPY);
@@ -703,6 +733,7 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st) {
     st.iterations = inner;
     st.outer_iterations = outer;
     st.rel_residual = rel;
+    st.fallback = fell_back;
     if (rc == PN_OK && rel > o.tol) rc = pn_fail(h, PN_ERR_NOT_CONVERGED, "ir: iteration cap reached");
     return rc;
 }
@@ -715,9 +746,14 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
     if (reinterpret_cast<uintptr_t>(u) & 15u) return pn_fail(h, PN_ERR_ARG, "pn_solve: u must be 16-byte aligned");
     const pn_solve_opts& o = *opts;
     if (!(o.tol > 0.0) || o.max_iter < 0) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad tol or max_iter");
-    if (o.solver != PN_SOLVER_CGLS && o.solver != PN_SOLVER_GMRES && o.solver != PN_SOLVER_IR_GMRES)
+    if (o.solver != PN_SOLVER_CGLS && o.solver != PN_SOLVER_GMRES && o.solver != PN_SOLVER_IR_GMRES &&
+        o.solver != PN_SOLVER_IR_FGMRES)
         return pn_fail(h, PN_ERR_ARG, "pn_solve: unknown solver");
-    if (o.solver != PN_SOLVER_IR_GMRES && o.precision != PN_F32 && o.precision != PN_F64)
+    if (o.solver == PN_SOLVER_IR_FGMRES && !o.precond)
+        return pn_fail(h, PN_ERR_ARG, "pn_solve: PN_SOLVER_IR_FGMRES needs opts->precond");
+    if (o.solver == PN_SOLVER_IR_FGMRES && h->R % 8)
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the learned preconditioner needs R % 8 == 0");
+    if (o.solver < PN_SOLVER_IR_GMRES && o.precision != PN_F32 && o.precision != PN_F64)
         return pn_fail(h, PN_ERR_ARG, "pn_solve: bad precision");
     if (o.solver != PN_SOLVER_CGLS && (o.restart < 1 || o.restart > 200))
         return pn_fail(h, PN_ERR_ARG, "pn_solve: restart must be in [1, 200]");
@@ -742,7 +778,8 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
         st.rel_residual = rel;
         if (rc == PN_OK && rel > o.tol) rc = pn_fail(h, PN_ERR_NOT_CONVERGED, "gmres: max_iter reached");
     } else {
-        rc = ir_gmres(c, (double*)u, o, st);
+        rc = ir_gmres(c, (double*)u, o, st,
+                      o.solver == PN_SOLVER_IR_FGMRES ? static_cast<struct pn_cnn*>(o.precond) : nullptr);
     }
     if (cudaStreamSynchronize(c.s) == cudaSuccess) pn_prof_drain(h);
     h->prof_on = false;

@@ -1,0 +1,229 @@
+"""Training and evaluation of the learned preconditioner (an extension of
+the paper's solver; the paper has no network).
+
+Data: for seeded random media (value-noise fBm extinction, albedo and g
+drawn per medium) and seeded sources (point sources and collimated-beam
+single-scatter sources), the library's own solver computes u with A u = Q
+(FP64 iterative refinement to 1e-6).  Each solved pair (Q, u), and random
+linear combinations of pairs of the same medium (still exact pairs, by
+linearity), gives one training sample: input features(r / |r|) and target
+(e - D^{-1} r) / |r| (pn_cnn_features / pn_cnn_targets).  The network is
+trained with pn_cnn_train_step (forward, relative-L2 loss, backward and Adam,
+all on the GPU with the library's kernels).
+
+The discrete P_N system in cell units depends only on sigma_t h, albedo and g,
+so media for a grid of R cells are drawn with sigma_t in [lo, hi] * R / 64 to
+match the optical thickness per cell of the 64^3 workload; the network (fully
+convolutional, fed log(sigma_t h)) is trained on small grids and applied to
+64^3 ones.
+
+Usage:
+    python -m paper_1807_00410_gb300.learned train --out weights.npy
+    python -m paper_1807_00410_gb300.learned eval --weights weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_ORDER = 3       # P3, K = 16
+SIG_LO, SIG_HI = 0.5, 80.0   # sigma_t range of the 64^3 media
+
+
+def medium(seed: int, R: int, tiny: bool = False):
+    """Seeded fBm medium for an R^3 grid with the optical thickness per cell of
+    the 64^3 workload (sigma_t in [0.5, 80] on 64^3)."""
+    import pn_inputs
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    albedo = float(rng.uniform(0.8, 0.99))
+    g = float(rng.uniform(0.0, 0.6))
+    scale = R / 64.0
+    st = (SIG_LO + (SIG_HI - SIG_LO) * pn_inputs.value_noise_fbm(R, seed)) * scale
+    return st, albedo, g
+
+
+def sources(seed: int, R: int, count: int):
+    """Seeded source specifications: ('point', voxel) or ('beam', axis, sign, radius, centre)."""
+    rng = np.random.Generator(np.random.PCG64(seed * 7 + 3))
+    out = []
+    for i in range(count):
+        if i % 2 == 0:
+            out.append(("point", tuple(int(v) for v in rng.integers(R // 8, R - R // 8, size=3))))
+        else:
+            out.append(("beam", int(rng.integers(3)), int(rng.choice([-1, 1])), float(rng.uniform(0.05, 0.2)),
+                        (float(rng.uniform(0.3, 0.7)), float(rng.uniform(0.3, 0.7)))))
+    return out
+
+
+def solve_pairs(seed: int, R: int, n_src: int, torch, tol: float = 1e-6):
+    """[(r32, u32, System)] for the seeded medium and sources (padded vectors)."""
+    from paper_1807_00410_gb300 import System
+    from paper_1807_00410_gb300 import pn as ppn
+    st, albedo, g = medium(seed, R)
+    st_d = torch.tensor(st, dtype=torch.float64, device="cuda")
+    pairs = []
+    for spec in sources(seed, R, n_src):
+        if spec[0] == "point":
+            Q = np.zeros((R, R, R))
+            Q[spec[1]] = float(R ** 3)  # unit total strength
+            sysm = System(N_ORDER, R, st_d, albedo, g, torch.tensor(Q, dtype=torch.float64, device="cuda"))
+        else:
+            _, axis, sign, radius, centre = spec
+            Qm = ppn.single_scatter_beam(N_ORDER, st_d, albedo, g, axis, sign, radius, centre)
+            sysm = System(N_ORDER, R, st_d, albedo, g, Qm)
+        u = sysm.zeros(torch.float64)
+        sysm.solve(u, solver="ir", tol=tol, restart=15, ortho="cgs1", max_iter=50000)
+        r32 = sysm.zeros(torch.float32)
+        sysm.residual(sysm.zeros(torch.float32), r32)  # r = Q - A 0 = Q in the padded layout
+        pairs.append((r32, u.float(), sysm))
+    return pairs
+
+
+def make_dataset(seeds, R: int, n_src: int, n_mix: int, torch, log=print):
+    """Features (S, R, R, R, K+3) and targets (S, R, R, R, K) on the GPU."""
+    feats, tgts = [], []
+    rng = np.random.Generator(np.random.PCG64(12345))
+    t0 = time.time()
+    for i, seed in enumerate(seeds):
+        pairs = solve_pairs(seed, R, n_src, torch)
+        sysm = pairs[0][2]
+        combos = [(p[0], p[1]) for p in pairs]
+        for _ in range(n_mix):
+            w = rng.standard_normal(len(pairs))
+            r = sum(float(wk) * p[0] for wk, p in zip(w, pairs))
+            e = sum(float(wk) * p[1] for wk, p in zip(w, pairs))
+            combos.append((r, e))
+        for r, e in combos:
+            nr = float(torch.linalg.vector_norm(r.double()))
+            feats.append(sysm.cnn_features(r, 1.0 / nr))
+            tgts.append(sysm.cnn_targets(e, r, 1.0 / nr))
+        for p in pairs:
+            p[2].close()
+        if (i + 1) % 10 == 0:
+            log(f"  data: {i + 1}/{len(seeds)} media, {len(feats)} samples, {time.time() - t0:.1f} s")
+    return torch.stack(feats), torch.stack(tgts)
+
+
+def train(net, X, Y, steps: int, batch: int, lr: float, torch, log=print, seed: int = 0):
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    S = X.shape[0]
+    losses = []
+    t0 = time.time()
+    for it in range(steps):
+        idx = torch.randint(0, S, (batch,), generator=gen).cuda()
+        lr_it = lr * 0.5 * (1.0 + math.cos(math.pi * it / steps))  # cosine schedule
+        losses.append(net.train_step(X[idx], Y[idx], lr_it))
+        if (it + 1) % max(1, steps // 10) == 0:
+            log(f"  train: step {it + 1}/{steps} loss {np.mean(losses[-20:]):.4f} ({time.time() - t0:.1f} s)")
+    return losses
+
+
+def init_params(c_in: int, c_out: int, seed: int, widths=(16, 32, 48, 64)) -> np.ndarray:
+    """He-style initial weights in the pn_cnn host parameter order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    names_dims = [("e0a", c_in, widths[0]), ("e0b", widths[0], widths[0]), ("e1a", widths[0], widths[1]),
+                  ("e1b", widths[1], widths[1]), ("e2a", widths[1], widths[2]), ("e2b", widths[2], widths[2]),
+                  ("e3a", widths[2], widths[3]), ("e3b", widths[3], widths[3]),
+                  ("d2", widths[3] + widths[2], widths[2]), ("d1", widths[2] + widths[1], widths[1]),
+                  ("d0", widths[1] + widths[0], widths[0]), ("out", widths[0], c_out)]
+    parts = []
+    for name, ci, co in names_dims:
+        std = math.sqrt(2.0 / (27 * ci)) * (0.1 if name == "out" else 1.0)
+        parts += [rng.standard_normal(co * ci * 27) * std, np.zeros(co)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def compare(net, seeds, R: int, torch, restart: int = 15, log=print):
+    """Learned FGMRES vs plain GMRES (both inside FP64 refinement) to 1e-6 on
+    held-out media: wall time (CUDA events), iterations, residuals."""
+    from paper_1807_00410_gb300 import System
+    rows = []
+    for seed in seeds:
+        st, albedo, g = medium(seed, R)
+        src = sources(seed, R, 1)[0]
+        Q = np.zeros((R, R, R))
+        Q[src[1]] = float(R ** 3)
+        sysm = System(N_ORDER, R, st, albedo, g, Q)
+        res = {}
+        for mode in ("plain", "learned"):
+            times = []
+            for rep in range(2):
+                u = sysm.zeros(torch.float64)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if mode == "plain":
+                    s = sysm.solve(u, solver="ir", tol=1e-6, restart=restart, ortho="cgs1", max_iter=100000)
+                else:
+                    s = sysm.solve(u, solver="ir_fgmres", tol=1e-6, restart=restart, ortho="cgs1", max_iter=100000,
+                                   precond=net)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            res[mode] = {"ms": min(times), "iterations": s["iterations"], "rel_residual": s["rel_residual"],
+                         "precond_applications": s["precond_applications"], "fallback": s["fallback"]}
+        rows.append({"seed": seed, **res})
+        log(f"  eval seed {seed}: plain {res['plain']['ms']:.1f} ms ({res['plain']['iterations']} it), learned "
+            f"{res['learned']['ms']:.1f} ms ({res['learned']['iterations']} it, fallback {res['learned']['fallback']})")
+        sysm.close()
+    return rows
+
+
+def main(argv=None):
+    import torch
+
+    from paper_1807_00410_gb300 import Net, build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("--weights", default=None)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--train-r", type=int, default=32)
+    ap.add_argument("--media", type=int, default=200)
+    ap.add_argument("--sources", type=int, default=4)
+    ap.add_argument("--mix", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--eval-r", type=int, default=64)
+    ap.add_argument("--eval-media", type=int, default=8)
+    args = ap.parse_args(argv)
+    build.build()
+    K = (N_ORDER + 1) ** 2
+    net = Net(K + 3, K)
+    report = {}
+    if args.cmd == "train":
+        net.set_params(init_params(K + 3, K, seed=1))
+        t0 = time.time()
+        X, Y = make_dataset(list(range(1000, 1000 + args.media)), args.train_r, args.sources, args.mix, torch)
+        report["data_seconds"] = time.time() - t0
+        report["samples"] = int(X.shape[0])
+        t0 = time.time()
+        losses = train(net, X, Y, args.steps, args.batch, args.lr, torch)
+        torch.cuda.synchronize()
+        report["train_seconds"] = time.time() - t0
+        report["loss_start"] = float(np.mean(losses[:20]))
+        report["loss_end"] = float(np.mean(losses[-50:]))
+        if args.out:
+            np.save(args.out, net.get_params())
+    else:
+        net.set_params(np.load(args.weights))
+    rows = compare(net, list(range(90000, 90000 + args.eval_media)), args.eval_r, torch)
+    report["eval"] = rows
+    report["plain_ms_mean"] = float(np.mean([r["plain"]["ms"] for r in rows]))
+    report["learned_ms_mean"] = float(np.mean([r["learned"]["ms"] for r in rows]))
+    print(json.dumps(report))
+    net.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -30,7 +30,7 @@ PN_NOALLOC_MAX_ELEMS = 1 << 31
 PN_F32, PN_F64 = 0, 1
 PN_BC_VACUUM = 0
 PN_Q_CENTRE_00, PN_Q_CENTRE_MOMENTS = 0, 1
-SOLVERS = {"cgls": 0, "gmres": 1, "ir": 2}
+SOLVERS = {"cgls": 0, "gmres": 1, "ir": 2, "ir_fgmres": 3}
 
 ERROR_NAMES = {
     PN_ERR_ARG: "PN_ERR_ARG", PN_ERR_ALLOC: "PN_ERR_ALLOC", PN_ERR_CUDA: "PN_ERR_CUDA",
@@ -42,8 +42,11 @@ ERROR_NAMES = {
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["pn_create", "pn_destroy", "pn_get_layout", "pn_last_error", "pn_apply", "pn_apply_t",
            "pn_residual", "pn_dot", "pn_axpby", "pn_default_solve_opts", "pn_solve", "pn_profile_get",
-           "pn_dot_noalloc", "pn_single_scatter_beam", "pn_unstagger"]
-PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar"]
+           "pn_dot_noalloc", "pn_single_scatter_beam", "pn_unstagger", "pn_cnn_create", "pn_cnn_destroy",
+           "pn_cnn_last_error", "pn_cnn_num_params", "pn_cnn_set_params", "pn_cnn_get_params", "pn_cnn_get_grads",
+           "pn_cnn_forward", "pn_cnn_backward", "pn_cnn_adam_step", "pn_cnn_train_step", "pn_cnn_features",
+           "pn_cnn_targets", "pn_cnn_precondition"]
+PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
 class PnError(RuntimeError):
@@ -68,12 +71,13 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
-                ("ortho", ctypes.c_int)]
+                ("ortho", ctypes.c_int), ("precond", ctypes.c_void_p)]
 
 
 class _SolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("precond_applications", ctypes.c_int), ("fallback", ctypes.c_int)]
 
 
 _lib = None
@@ -104,6 +108,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_dot_noalloc": (i, [vp, vp, i64, i, ctypes.POINTER(d), vp]),
         "pn_single_scatter_beam": (i, [i, i, vp, vp, d, d, i, i, d, d, d, vp, i, vp]),
         "pn_unstagger": (i, [vp, vp, vp, i, vp]),
+        "pn_cnn_create": (i, [ctypes.POINTER(vp), i, i, ctypes.POINTER(ctypes.c_int * 4)]),
+        "pn_cnn_destroy": (i, [vp]),
+        "pn_cnn_last_error": (ctypes.c_char_p, [vp]),
+        "pn_cnn_num_params": (i64, [vp]),
+        "pn_cnn_set_params": (i, [vp, vp, i64]),
+        "pn_cnn_get_params": (i, [vp, vp, i64]),
+        "pn_cnn_get_grads": (i, [vp, vp, i64]),
+        "pn_cnn_forward": (i, [vp, vp, vp, i, i, i, i, vp]),
+        "pn_cnn_backward": (i, [vp, vp, vp]),
+        "pn_cnn_adam_step": (i, [vp, d, vp]),
+        "pn_cnn_train_step": (i, [vp, vp, vp, i, i, i, i, d, ctypes.POINTER(d), vp]),
+        "pn_cnn_features": (i, [vp, vp, d, vp, vp]),
+        "pn_cnn_targets": (i, [vp, vp, vp, d, vp, vp]),
+        "pn_cnn_precondition": (i, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -364,15 +382,17 @@ class System:
 
     def solve(self, u, solver: str = "cgls", tol: float = 1e-6, max_iter: int = 100000, restart: int = 60,
               inner_tol: float = 1e-2, max_outer: int = 50, check_every: int = 10, stream=None,
-              raise_on_error: bool = True, profile: bool = False, ortho: str = "cgs2") -> dict:
+              raise_on_error: bool = True, profile: bool = False, ortho: str = "cgs2", precond=None) -> dict:
         """Solve A u = Q in place (u is the initial guess).  Returns the stats."""
         up, dt = self._vec(u)
         o = _SolveOpts()
         self._lib.pn_default_solve_opts(ctypes.byref(o))
         o.solver = SOLVERS[solver]
         o.precision = dt
-        if solver == "ir" and dt != PN_F64:
+        if solver in ("ir", "ir_fgmres") and dt != PN_F64:
             raise TypeError("iterative refinement keeps u in FP64")
+        if precond is not None:
+            o.precond = precond._h
         o.tol, o.max_iter, o.restart = float(tol), int(max_iter), int(restart)
         o.inner_tol, o.max_outer, o.check_every = float(inner_tol), int(max_outer), int(check_every)
         o.profile = 1 if profile else 0
@@ -380,7 +400,8 @@ class System:
         st = _SolveStats()
         rc = self._lib.pn_solve(self._h, up, ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
         stats = {"status": rc, "iterations": st.iterations, "outer_iterations": st.outer_iterations,
-                 "rel_residual": st.rel_residual, "seconds": st.seconds, "launches": st.launches}
+                 "rel_residual": st.rel_residual, "seconds": st.seconds, "launches": st.launches,
+                 "precond_applications": st.precond_applications, "fallback": st.fallback}
         if rc != PN_OK and raise_on_error:
             raise PnError(rc, self._lib.pn_last_error(self._h).decode() + f" (stats {stats})")
         return stats
@@ -394,6 +415,31 @@ class System:
             self._check(self._lib.pn_profile_get(self._h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
             out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
         return out
+
+    def cnn_features(self, v, scale: float = 1.0, stream=None):
+        """Network input features of a padded FP32 vector: (R, R, R, K + 3)."""
+        torch = _torch()
+        R, K = self.layout.R, self.layout.K
+        out = torch.empty((R, R, R, K + 3), dtype=torch.float32, device=v.device)
+        self._check(self._lib.pn_cnn_features(self._h, ctypes.c_void_p(v.data_ptr()), float(scale),
+                                              ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def cnn_targets(self, e, r, scale: float, stream=None):
+        """Training target scale * (e - D^{-1} r) at the cells' own slots: (R, R, R, K)."""
+        torch = _torch()
+        R, K = self.layout.R, self.layout.K
+        out = torch.empty((R, R, R, K), dtype=torch.float32, device=e.device)
+        self._check(self._lib.pn_cnn_targets(self._h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                             float(scale), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def precondition(self, net, v, stream=None):
+        """z = M(v) with the learned network (padded FP32 vectors)."""
+        z = _torch().empty_like(v)
+        self._check(self._lib.pn_cnn_precondition(self._h, net._h, ctypes.c_void_p(v.data_ptr()),
+                                                  ctypes.c_void_p(z.data_ptr()), _stream_ptr(stream)))
+        return z
 
     def unstagger(self, x, stream=None):
         """Padded vector -> (K, R, R, R) tensor of voxel-centre values."""
@@ -431,3 +477,86 @@ class System:
                 R + 1, R + 1, lay.pitch_x)
             box[:nz, :ny, :nx] = np.asarray(planes[lay.plane_k[p]], dtype=np.float64).reshape(nz, ny, nx)
         return torch.as_tensor(host, dtype=dtype or torch.float32).to(device)
+
+
+class Net:
+    """The learned preconditioner's 3D convolutional encoder-decoder
+    (pn_cnn_*): BF16 tensor-core forward and backward kernels with FP32
+    accumulation, FP32 master weights trained by Adam on the GPU.  Tensors
+    are float32 CUDA tensors shaped (B, Z, Y, X, C)."""
+
+    def __init__(self, c_in: int, c_out: int, widths=(16, 32, 48, 64)):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        w = (ctypes.c_int * 4)(*[int(v) for v in widths])
+        rc = self._lib.pn_cnn_create(ctypes.byref(self._h), int(c_in), int(c_out), ctypes.byref(w))
+        if rc != PN_OK:
+            raise PnError(rc, "pn_cnn_create failed")
+        self.c_in, self.c_out, self.widths = c_in, c_out, tuple(widths)
+        self.n_params = int(self._lib.pn_cnn_num_params(self._h))
+
+    def _check(self, rc):
+        if rc != PN_OK:
+            raise PnError(rc, self._lib.pn_cnn_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.pn_cnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        self._check(self._lib.pn_cnn_set_params(self._h, ctypes.c_void_p(a.ctypes.data), a.size))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        self._check(self._lib.pn_cnn_get_params(self._h, ctypes.c_void_p(a.ctypes.data), a.size))
+        return a
+
+    def get_grads(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        self._check(self._lib.pn_cnn_get_grads(self._h, ctypes.c_void_p(a.ctypes.data), a.size))
+        return a
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        B, Z, Y, X, C = x.shape
+        assert C == self.c_in and x.dtype == torch.float32 and x.is_cuda
+        x = x.contiguous()
+        out = torch.empty((B, Z, Y, X, self.c_out), dtype=torch.float32, device=x.device)
+        self._check(self._lib.pn_cnn_forward(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                             B, Z, Y, X, _stream_ptr(stream)))
+        return out
+
+    def backward(self, grad_out, stream=None):
+        g = grad_out.contiguous()
+        self._check(self._lib.pn_cnn_backward(self._h, ctypes.c_void_p(g.data_ptr()), _stream_ptr(stream)))
+
+    def adam_step(self, lr: float, stream=None):
+        self._check(self._lib.pn_cnn_adam_step(self._h, float(lr), _stream_ptr(stream)))
+
+    def train_step(self, x, target, lr: float, stream=None) -> float:
+        B, Z, Y, X, C = x.shape
+        x, t = x.contiguous(), target.contiguous()
+        loss = ctypes.c_double()
+        self._check(self._lib.pn_cnn_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                                B, Z, Y, X, float(lr), ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+
+def flatten_cnn_params(params: dict, layer_names) -> np.ndarray:
+    """{name: (W[o][c][27], b[o])} -> the host parameter order of pn_cnn."""
+    parts = []
+    for name in layer_names:
+        W, b = params[name]
+        parts += [np.asarray(W, dtype=np.float64).ravel(), np.asarray(b, dtype=np.float64).ravel()]
+    return np.concatenate(parts)
+
+
+CNN_LAYERS = ["e0a", "e0b", "e1a", "e1b", "e2a", "e2b", "e3a", "e3b", "d2", "d1", "d0", "out"]

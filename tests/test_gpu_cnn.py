@@ -1,0 +1,180 @@
+"""GPU CNN kernels (BF16 tensor cores, FP32 accumulation) against the CPU
+reference oracle/cnn.py: forward output and every parameter gradient, plus
+a short training run whose loss must fall.
+
+The kernels keep every activation and gradient tensor in BF16.  The oracle
+runs twice: exactly (FP64), and with BF16 rounding at exactly the tensors the
+kernels store (oracle `store` hook), exact arithmetic in between.  The GPU
+must match the BF16-storage model closely (relative L2 <= 2e-2 forward,
+<= 4e-2 per layer gradient) and be no further from the exact result than
+the model itself is (times 1.5, plus 2e-2)."""
+import numpy as np
+import pytest
+
+from oracle import cnn as ocnn
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available()
+    from paper_1807_00410_gb300 import build
+    build.build()
+
+
+def _bf16(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _setup(widths, c_in, c_out, R, B, seed):
+    from paper_1807_00410_gb300 import pn
+    params = ocnn.unet_init(c_in, c_out, seed=seed, widths=widths)
+    rng = np.random.default_rng(seed)
+    for k in params:
+        W, b = params[k]
+        params[k] = (_bf16(W * 2.0), rng.standard_normal(b.shape) * 0.05)
+    x = _bf16(rng.standard_normal((B, c_in, R, R, R)))
+    net = pn.Net(c_in, c_out, widths)
+    net.set_params(pn.flatten_cnn_params(params, pn.CNN_LAYERS))
+    return pn, params, x, net
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _store(a):
+    return _bf16(a)
+
+
+@pytest.mark.parametrize("widths,c_in,c_out,R", [((16, 16, 16, 16), 3, 2, 16), ((16, 32, 48, 64), 19, 16, 16)])
+def test_forward_matches_cpu_reference(widths, c_in, c_out, R):
+    pn, params, x, net = _setup(widths, c_in, c_out, R, 2, 7)
+    xt = torch.tensor(np.moveaxis(x, 1, -1), dtype=torch.float32).cuda()
+    y = net.forward(xt).cpu().double().numpy()
+    for b in range(2):
+        ref, _ = ocnn.unet_forward(params, x[b])
+        model, _ = ocnn.unet_forward(params, x[b], store=_store)
+        got = np.moveaxis(y[b], -1, 0)
+        assert _rel(got, model) < 2e-2
+        assert _rel(got, ref) < 1.5 * _rel(model, ref) + 2e-2
+    assert np.abs(y).max() > 0
+    net.close()
+
+
+def test_parameter_gradients_match_cpu_reference():
+    widths, c_in, c_out, R, B = (16, 16, 16, 16), 3, 2, 16, 2
+    pn, params, x, net = _setup(widths, c_in, c_out, R, B, 11)
+    rng = np.random.default_rng(1)
+    gy = rng.standard_normal((B, c_out, R, R, R))
+    xt = torch.tensor(np.moveaxis(x, 1, -1), dtype=torch.float32).cuda()
+    net.forward(xt)
+    net.backward(torch.tensor(np.moveaxis(_bf16(gy), 1, -1), dtype=torch.float32).cuda())
+    got = net.get_grads()
+    exact, model = None, None
+    for b in range(B):
+        for store in (None, _store):
+            _, cache = ocnn.unet_forward(params, x[b], store=store)
+            g = ocnn.unet_backward(params, cache, _bf16(gy[b]), store=store)
+            flat = pn.flatten_cnn_params(g, pn.CNN_LAYERS)
+            if store is None:
+                exact = flat if exact is None else exact + flat
+            else:
+                model = flat if model is None else model + flat
+    off = 0
+    for name, ci, co in ocnn.unet_layers(c_in, c_out, widths):
+        nw, nb = co * ci * 27, co
+        for sl in (slice(off, off + nw), slice(off + nw, off + nw + nb)):
+            assert _rel(got[sl], model[sl]) < 4e-2, name
+            assert _rel(got[sl], exact[sl]) < 1.5 * _rel(model[sl], exact[sl]) + 2e-2, name
+        off += nw + nb
+    net.close()
+
+
+def test_training_reduces_loss():
+    """Fit a fixed linear target map (a random 3x3x3 filter bank) on random
+    inputs: the relative loss must fall well below its starting value."""
+    from paper_1807_00410_gb300 import pn
+    rng = np.random.default_rng(5)
+    c_in, c_out, R, B = 4, 2, 16, 4
+    net = pn.Net(c_in, c_out, (16, 16, 16, 16))
+    net.set_params(pn.flatten_cnn_params(ocnn.unet_init(c_in, c_out, seed=3, widths=(16, 16, 16, 16)), pn.CNN_LAYERS))
+    Wt = rng.standard_normal((c_out, c_in, 27)) * 0.2
+    losses = []
+    for it in range(120):
+        x = rng.standard_normal((B, c_in, R, R, R))
+        t = np.stack([ocnn.conv3d(x[b], Wt, np.zeros(c_out)) for b in range(B)])
+        xt = torch.tensor(np.moveaxis(x, 1, -1), dtype=torch.float32).cuda()
+        tt = torch.tensor(np.moveaxis(t, 1, -1), dtype=torch.float32).cuda()
+        losses.append(net.train_step(xt, tt, 3e-3))
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-10:]) < 0.3 * np.mean(losses[:5]), (losses[:5], losses[-10:])
+    net.close()
+
+
+# --- the preconditioner glue and flexible GMRES -------------------------------------
+
+def _p3_system(R, seed):
+    import pn_inputs
+    from oracle import pn as opn
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(3, R, seed, 0.5, 20.0, 0.9, 0.4)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00)
+    return p, med, System(3, R, p.sigma_t, p.albedo, p.g, p.Q00)
+
+
+def test_features_layout():
+    p, med, gpu = _p3_system(8, 1)
+    lay = gpu.layout
+    g = torch.Generator(device="cpu").manual_seed(2)
+    v = torch.rand(lay.n_elems, generator=g).cuda()
+    f = gpu.cnn_features(v, 0.5).cpu().numpy()
+    vh = v.cpu().numpy()
+    R = lay.R
+    for q in range(lay.K):
+        box = vh[q * lay.plane_stride: q * lay.plane_stride + lay.pitch_y * (R + 1)].reshape(R + 1, R + 1, lay.pitch_x)
+        np.testing.assert_allclose(f[..., q], 0.5 * box[:R, :R, :R], rtol=1e-6)
+    np.testing.assert_allclose(f[..., lay.K], np.log(p.sigma_t / R), rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(f[..., lay.K + 1], p.albedo, rtol=1e-6)
+    np.testing.assert_allclose(f[..., lay.K + 2], p.g, rtol=1e-6)
+    gpu.close()
+
+
+def test_zero_network_preconditioner_is_jacobi():
+    from oracle import pn as opn
+    from paper_1807_00410_gb300 import Net
+    p, med, gpu = _p3_system(16, 3)
+    K = gpu.layout.K
+    net = Net(K + 3, K)
+    net.set_params(np.zeros(net.n_params, dtype=np.float32))
+    lay_o = opn.Layout(3, 16)
+    rng = np.random.default_rng(0)
+    planes = [rng.uniform(-1, 1, s) for s in lay_o.shapes]
+    v = gpu.from_planes(planes, dtype=torch.float32)
+    z = gpu.precondition(net, v)
+    D = lay_o.split(opn.diagonal(lay_o, med))
+    got = gpu.to_planes(z)
+    for k in range(K):
+        np.testing.assert_allclose(got[k], np.asarray(planes[k], np.float32) / D[k], rtol=2e-5, atol=1e-7)
+    net.close()
+    gpu.close()
+
+
+def test_ir_fgmres_with_untrained_network_meets_oracle_residual():
+    from oracle import pn as opn
+    from paper_1807_00410_gb300 import Net
+    from paper_1807_00410_gb300 import learned
+    p, med, gpu = _p3_system(16, 5)
+    K = gpu.layout.K
+    net = Net(K + 3, K)
+    net.set_params(learned.init_params(K + 3, K, seed=4))
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver="ir_fgmres", tol=1e-6, restart=15, ortho="cgs1", precond=net)
+    S = opn.assemble(3, 16, med)
+    assert st["rel_residual"] <= 1e-6 and st["precond_applications"] > 0
+    assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u))) <= 1.0001e-6
+    net.close()
+    gpu.close()
