@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU oracle timing")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the FP32 operator on the P_N cloud medium given by --apply-n / --apply-r")
+    ap.add_argument("--threshold-sweep", action="store_true",
+                    help="iterations / time to 1e-6 vs the sigma_t threshold on the 64^3 cloud medium")
     ap.add_argument("--apply-n", type=int, default=7)
     ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
@@ -426,8 +428,36 @@ def run_apply_only(args):
     sysm.close()
 
 
+def run_threshold_sweep(args):
+    """Convergence against the extinction threshold (the paper clamps sigma_t
+    from below because vacuum makes A singular, section "Nebulae"): IR solves
+    of the thresholded-fBm cloud (54 % empty voxels) at each threshold."""
+    import torch
+
+    import pn_inputs
+    from paper_1807_00410_gb300 import System
+    torch.cuda.set_device(0)
+    rows = []
+    for N in (1, 5):
+        for smin in (1.0, 0.3, 0.1, 0.03):
+            p = pn_inputs.cloud_point(N, 64, 0, sigma_t_min=smin)
+            sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=smin)
+            u = sysm.zeros(torch.float64)
+            st = sysm.solve(u, solver="ir", tol=1e-6, restart=args.restart, ortho=args.ortho, max_iter=200000,
+                            raise_on_error=False)
+            rows.append({"N": N, "sigma_t_min": smin, "iterations": st["iterations"],
+                         "outer": st["outer_iterations"], "seconds": st["seconds"],
+                         "rel_residual": st["rel_residual"], "status": st["status"]})
+            sysm.close()
+    print(json.dumps({"mode": "threshold-sweep", "workload": "64^3 thresholded-fBm cloud, albedo 0.99, g 0.6, "
+                      "point source, FP32 GMRES + FP64 IR to 1e-6", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.threshold_sweep:
+        run_threshold_sweep(args)
+        return
     if args.apply_only:
         run_apply_only(args)
         return

@@ -301,8 +301,9 @@ int pn_cnn_train_step(pn_cnn* net, const float* in, const float* target, int B, 
 int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype, double* out, void* stream);
 
 /*
- * The learned preconditioner M(v) = |v| net(features(v / |v|)) + D^{-1} v
- * (an extension; the paper has no preconditioner).  features(u): for each
+ * The learned preconditioner M(v) = s net(features(v / s)) + D^{-1} v with
+ * s = |v| / sqrt(n), n the number of unknowns (an extension; the paper has
+ * no preconditioner).  features(u): for each
  * voxel (x, y, z) < R, channel p = u in plane p at slot (x, y, z), then
  * log(sigma_t h), sigma_s / sigma_t and g (c_in = K + 3); the network's K
  * output channels return to slot (x, y, z) of each plane; D is the

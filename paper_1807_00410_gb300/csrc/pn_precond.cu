@@ -1,7 +1,8 @@
 // Learned preconditioner glue: P_N vectors <-> network tensors, and the
 // preconditioner application used inside flexible GMRES.
 //
-//   M(v) = |v| net(features(v / |v|)) + D^{-1} v
+//   M(v) = s net(features(v / s)) + D^{-1} v,   s = |v| / sqrt(n) (RMS of v over
+//   the n unknowns, so the network sees values of order one)
 //
 // features(u) at voxel (x, y, z) < R: channel p = u of plane p at slot
 // (x, y, z) (the cell's own slot on every staggered grid), then
@@ -10,7 +11,7 @@
 // collision-minus-scattering diagonal) covers every unknown, including the
 // x = R, y = R, z = R face slots the network does not see, so M is never
 // rank-deficient.  The network is trained on pairs (r, e) with A e = r:
-// input features(r / |r|), target (e - D^{-1} r) / |r|.
+// input features(r / s), target (e - D^{-1} r) / s, s = RMS of r.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,7 +35,7 @@ __device__ __forceinline__ float centre_mean_f(const float* F, int R, int x, int
 
 struct FeatArgs {
     const float* u;       // padded vector
-    const double* nrm2;   // device |u|^2 (scale = 1/|u|) or null
+    const double* nrm2;   // device |u|^2 (scale = sqrt(n_unknowns)/|u|) or null
     double scale;         // used when nrm2 is null
     const float* st;
     const float* ss;
@@ -50,7 +51,7 @@ __global__ void k_features(FeatArgs a) {
     float sc = float(a.scale);
     if (a.nrm2) {
         const double n2 = *a.nrm2;
-        sc = n2 > 0.0 ? float(1.0 / sqrt(n2)) : 0.0f;
+        sc = n2 > 0.0 ? float(a.scale / sqrt(n2)) : 0.0f;
     }
     const float h = 1.0f / a.R;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V * C; i += int64_t(gridDim.x) * blockDim.x) {
@@ -75,7 +76,7 @@ __global__ void k_features(FeatArgs a) {
 // target mode (e != null): out[v][c] = scale * (e - D^{-1} r) at slots < R.
 struct ScatterArgs {
     const float* net_out;  // [R^3][K] or null
-    const double* nrm2;    // device |v|^2: scale = |v| (or null: scale field)
+    const double* nrm2;    // device |v|^2: scale = |v| * scale field (or null: scale field)
     double scale;
     const float* v;        // vector for the Jacobi term (or null)
     float* z;              // padded output
@@ -90,7 +91,7 @@ __global__ void k_scatter(ScatterArgs a) {
     const int64_t n = a.plane_stride * a.K;
     const int R = a.R;
     float sc = float(a.scale);
-    if (a.nrm2) sc = float(sqrt(fmax(*a.nrm2, 0.0)));
+    if (a.nrm2) sc = float(a.scale * sqrt(fmax(*a.nrm2, 0.0)));
     const int64_t box = a.pitch_y * (R + 1);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         const int p = int(i / a.plane_stride);
@@ -147,13 +148,15 @@ int precond_apply(pn_handle* h, struct pn_cnn* net, const float* v, float* z, fl
     if (e != cudaSuccess) return pn_cuda_fail(h, e, "precond: norm");
     float* feat = scratch;
     float* out = scratch + V * (K + 3);
-    FeatArgs fa{v, nrm2_dev, 1.0, h->d_st_f, h->d_ss_f, float(h->g), R, K, h->pitch_x, h->pitch_y, h->plane_stride, feat};
+    const double rms_n = std::sqrt(double(h->n_active));
+    FeatArgs fa{v, nrm2_dev, rms_n, h->d_st_f, h->d_ss_f, float(h->g), R, K, h->pitch_x, h->pitch_y, h->plane_stride,
+                feat};
     k_features<<<grid_for(V * (K + 3)), 256, 0, s>>>(fa);
     e = cudaGetLastError();
     if (e != cudaSuccess) return pn_cuda_fail(h, e, "precond: features");
     const int rc = pn_cnn_forward(net, feat, out, 1, R, R, R, s);
     if (rc != PN_OK) return pn_fail(h, rc, "precond: network forward failed");
-    ScatterArgs sa{out, nrm2_dev, 1.0, v, z, h->d_planes, h->d_st_f, h->d_ss_f, R, K, h->pitch_x, h->pitch_y,
+    ScatterArgs sa{out, nrm2_dev, 1.0 / rms_n, v, z, h->d_planes, h->d_st_f, h->d_ss_f, R, K, h->pitch_x, h->pitch_y,
                    h->plane_stride};
     k_scatter<<<grid_for(h->n_elems), 256, 0, s>>>(sa);
     e = cudaGetLastError();

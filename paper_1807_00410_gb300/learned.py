@@ -6,8 +6,9 @@ drawn per medium) and seeded sources (point sources and collimated-beam
 single-scatter sources), the library's own solver computes u with A u = Q
 (FP64 iterative refinement to 1e-6).  Each solved pair (Q, u), and random
 linear combinations of pairs of the same medium (still exact pairs, by
-linearity), gives one training sample: input features(r / |r|) and target
-(e - D^{-1} r) / |r| (pn_cnn_features / pn_cnn_targets).  The network is
+linearity), gives one training sample: input features(r / s) and target
+(e - D^{-1} r) / s with s the RMS of r over the unknowns (pn_cnn_features /
+pn_cnn_targets; the preconditioner scales the same way).  The network is
 trained with pn_cnn_train_step (forward, relative-L2 loss, backward and Adam,
 all on the GPU with the library's kernels).
 
@@ -103,10 +104,11 @@ def make_dataset(seeds, R: int, n_src: int, n_mix: int, torch, log=print):
             r = sum(float(wk) * p[0] for wk, p in zip(w, pairs))
             e = sum(float(wk) * p[1] for wk, p in zip(w, pairs))
             combos.append((r, e))
+        n_unknowns = sysm.layout.n_active
         for r, e in combos:
-            nr = float(torch.linalg.vector_norm(r.double()))
-            feats.append(sysm.cnn_features(r, 1.0 / nr))
-            tgts.append(sysm.cnn_targets(e, r, 1.0 / nr))
+            rms = float(torch.linalg.vector_norm(r.double())) / math.sqrt(n_unknowns)
+            feats.append(sysm.cnn_features(r, 1.0 / rms))
+            tgts.append(sysm.cnn_targets(e, r, 1.0 / rms))
         for p in pairs:
             p[2].close()
         if (i + 1) % 10 == 0:
@@ -119,9 +121,11 @@ def train(net, X, Y, steps: int, batch: int, lr: float, torch, log=print, seed: 
     S = X.shape[0]
     losses = []
     t0 = time.time()
+    warm = max(1, steps // 20)
     for it in range(steps):
         idx = torch.randint(0, S, (batch,), generator=gen).cuda()
-        lr_it = lr * 0.5 * (1.0 + math.cos(math.pi * it / steps))  # cosine schedule
+        # linear warm-up, then cosine decay
+        lr_it = lr * min(1.0, (it + 1) / warm) * 0.5 * (1.0 + math.cos(math.pi * it / steps))
         losses.append(net.train_step(X[idx], Y[idx], lr_it))
         if (it + 1) % max(1, steps // 10) == 0:
             log(f"  train: step {it + 1}/{steps} loss {np.mean(losses[-20:]):.4f} ({time.time() - t0:.1f} s)")
@@ -193,7 +197,7 @@ def main(argv=None):
     ap.add_argument("--mix", type=int, default=4)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--eval-r", type=int, default=64)
     ap.add_argument("--eval-media", type=int, default=8)
     args = ap.parse_args(argv)
@@ -217,6 +221,17 @@ def main(argv=None):
             np.save(args.out, net.get_params())
     else:
         net.set_params(np.load(args.weights))
+    xe = torch.randn((1, args.eval_r, args.eval_r, args.eval_r, K + 3), device="cuda")
+    for _ in range(3):
+        net.forward(xe)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.forward(xe)
+    e1.record()
+    e1.synchronize()
+    report["net_forward_ms"] = e0.elapsed_time(e1) / 10
     rows = compare(net, list(range(90000, 90000 + args.eval_media)), args.eval_r, torch)
     report["eval"] = rows
     report["plain_ms_mean"] = float(np.mean([r["plain"]["ms"] for r in rows]))
