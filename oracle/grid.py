@@ -28,8 +28,9 @@ interpolated to an unknown's location as the arithmetic mean of the adjacent
 voxel centres that lie inside the domain (section "Precomputation": parameters
 are interpolated to the staggered locations; the rule itself is a reading).
 
-A periodic test mode (all axes wrap, R locations per axis for every class)
-exists only for the exact closed-form pins.
+A periodic test mode (R locations per axis for every class, wrap-around;
+all axes, or a chosen subset of them) exists only for the exact closed-form
+pins and for pinning the 2D reduction (z-periodic, z-independent data).
 
 Oracle vector order: coefficient-major, k = l^2 + l + m, each coefficient's
 grid in C order [z][y][x] with its own extents.
@@ -53,22 +54,25 @@ def parity_class(l: int, m: int):
 class Layout:
     """Unknown locations of one P_N system on an R^3 grid of the unit cube."""
 
-    def __init__(self, N: int, R: int, periodic: bool = False):
+    def __init__(self, N: int, R: int, periodic=False):
+        """periodic: bool (all axes) or a tuple of three bools (x, y, z)."""
         if R < 2:
             raise ValueError("grid must have at least 2 cells per axis")
         self.N = N
         self.R = R
         self.h = 1.0 / R
-        self.periodic = periodic
+        if isinstance(periodic, (tuple, list)):
+            self.periodic_axes = tuple(bool(v) for v in periodic)
+        else:
+            self.periodic_axes = (bool(periodic),) * 3
+        self.periodic = any(self.periodic_axes)
         self.K = n_coeffs(N)
         self.lm = lm_list(N)
         self.classes = [parity_class(l, m) for (l, m) in self.lm]
         self.shapes = []  # (nz, ny, nx) per k
         for c in self.classes:
-            if periodic:
-                self.shapes.append((R, R, R))
-            else:
-                self.shapes.append((R + c[2], R + c[1], R + c[0]))
+            ext = [R if self.periodic_axes[d] else R + c[d] for d in range(3)]  # x, y, z
+            self.shapes.append((ext[2], ext[1], ext[0]))
         sizes = [int(np.prod(s)) for s in self.shapes]
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         self.n = int(self.offsets[-1])
@@ -108,18 +112,19 @@ def _face_average(F: np.ndarray, axis: int, periodic: bool) -> np.ndarray:
     return np.moveaxis(G, 0, axis)
 
 
-def interpolate_to_class(F: np.ndarray, cls, periodic: bool) -> np.ndarray:
+def interpolate_to_class(F: np.ndarray, cls, periodic) -> np.ndarray:
     """Centre field F[z, y, x] (R^3) -> values at the locations of parity class cls.
 
     The mean over the adjacent in-domain centres is a tensor product of 1D
-    means, applied along each odd axis.
+    means, applied along each odd axis.  periodic: bool or (x, y, z) bools.
     """
+    per = tuple(periodic) if isinstance(periodic, (tuple, list)) else (bool(periodic),) * 3
     G = np.asarray(F, dtype=np.float64)
     px, py, pz = cls
     if px:
-        G = _face_average(G, 2, periodic)
+        G = _face_average(G, 2, per[0])
     if py:
-        G = _face_average(G, 1, periodic)
+        G = _face_average(G, 1, per[1])
     if pz:
-        G = _face_average(G, 0, periodic)
+        G = _face_average(G, 0, per[2])
     return G

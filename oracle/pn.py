@@ -74,7 +74,8 @@ def diagonal(layout: Layout, medium: Medium) -> np.ndarray:
     for k, (l, m) in enumerate(layout.lm):
         c = layout.classes[k]
         fl = scattering_factor_printed(l, medium.g)
-        parts.append(interpolate_to_class(st, c, layout.periodic) - fl * interpolate_to_class(ss, c, layout.periodic))
+        per = layout.periodic_axes
+        parts.append(interpolate_to_class(st, c, per) - fl * interpolate_to_class(ss, c, per))
     return layout.join(parts)
 
 
@@ -88,7 +89,7 @@ def rhs(layout: Layout, medium: Medium) -> np.ndarray:
             parts.append(Q.copy() if k == 0 else np.zeros(layout.shapes[k]))
     elif Q.shape == (layout.K, R, R, R):
         for k in range(layout.K):
-            parts.append(interpolate_to_class(Q[k], layout.classes[k], layout.periodic))
+            parts.append(interpolate_to_class(Q[k], layout.classes[k], layout.periodic_axes))
     else:
         raise ValueError("Q must have shape (R,R,R) or (K,R,R,R)")
     return layout.join(parts)
@@ -125,7 +126,7 @@ def transport_coo(layout: Layout):
                 snz, sny, snx = layout.shapes[kp]
                 for sign, which in ((+1.0, 0), (-1.0, 1)):
                     nb = list(idx)
-                    pl, mi, vp, vm = _neighbour_index(idx[d], ck[d], R, layout.periodic)
+                    pl, mi, vp, vm = _neighbour_index(idx[d], ck[d], R, layout.periodic_axes[d])
                     nb[d] = pl if which == 0 else mi
                     valid = vp if which == 0 else vm
                     col = layout.offsets[kp] + (nb[2] * sny + nb[1]) * snx + nb[0]
@@ -137,7 +138,7 @@ def transport_coo(layout: Layout):
     return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0)
 
 
-def assemble(N: int, R: int, medium: Medium, periodic: bool = False) -> System:
+def assemble(N: int, R: int, medium: Medium, periodic=False) -> System:
     """Explicit sparse A (CSR, FP64) and right-hand side, row by row as the
     paper's runtime does (section "Runtime": the stencil is executed for every
     unknown to fill A and Q)."""
@@ -176,7 +177,7 @@ def apply_matrix_free(layout: Layout, medium: Medium, u: np.ndarray, transpose: 
                 src = parts[kp]
                 n_out = layout.shapes[k][ax]
                 i = np.arange(n_out)
-                pl, mi, vp, vm = _neighbour_index(i, ck[d], R, layout.periodic)
+                pl, mi, vp, vm = _neighbour_index(i, ck[d], R, layout.periodic_axes[d])
                 plus = np.zeros(layout.shapes[k])
                 minus = np.zeros(layout.shapes[k])
                 sl_out = [slice(None)] * 3

@@ -144,3 +144,29 @@ def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndar
     """Uniform random values (test vectors)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, size=shape)
+
+
+def checkerboard_2d(R: int = 71, blocks: int = 7, sigma_a: float = 10.0, sigma_s: float = 1.0,
+                    source: float = 1.0):
+    """The 2D checkerboard workload (section "2D checkerboard": a 7 x 7
+    domain at 71 x 71 cells, unit blocks alternately purely absorbing,
+    sigma_a = 10, and purely scattering, sigma_s = 1) on R x R cells.
+
+    The paper gives neither the pattern's phase nor the source; the reading
+    here: cell (iy, ix) belongs to unit block (floor(y), floor(x)) of its
+    centre (x, y) in [0, blocks)^2; block (i, j) absorbs when i + j is odd
+    and scatters otherwise; an isotropic source of unit strength per unit
+    area fills the centre block (which scatters).  The problem is scaled to
+    the unit square (cell size h = 1 / R): extinction and source scale by
+    `blocks`, which leaves sigma h and Q h, and so the solution, unchanged.
+
+    Returns (sigma_t, albedo, Q00), float64 arrays [y][x] of shape (R, R).
+    """
+    c = (np.arange(R) + 0.5) * blocks / R
+    by, bx = np.meshgrid(np.floor(c).astype(int), np.floor(c).astype(int), indexing="ij")
+    absorbing = (by + bx) % 2 == 1
+    sigma_t = np.where(absorbing, sigma_a, sigma_s) * float(blocks)
+    albedo = np.where(absorbing, 0.0, 1.0)
+    mid = blocks // 2
+    Q00 = np.where((by == mid) & (bx == mid), source, 0.0) * float(blocks)
+    return sigma_t, albedo, Q00
