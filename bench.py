@@ -59,6 +59,12 @@ def parse():
                     help="time only the FP32 operator on the P_N cloud medium given by --apply-n / --apply-r")
     ap.add_argument("--threshold-sweep", action="store_true",
                     help="iterations / time to 1e-6 vs the sigma_t threshold on the 64^3 cloud medium")
+    ap.add_argument("--checkerboard", action="store_true",
+                    help="2D checkerboard (7 x 7 blocks, 71 x 71 cells): P1 and P5 solve time to 1e-10")
+    ap.add_argument("--batched", action="store_true",
+                    help="many-instance workload: batched solve of --batch-count systems vs one-by-one solves")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-seed", type=int, default=0)
     ap.add_argument("--apply-n", type=int, default=7)
     ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
@@ -453,8 +459,122 @@ def run_threshold_sweep(args):
                       "point source, FP32 GMRES + FP64 IR to 1e-6", "rows": rows}), flush=True)
 
 
+def run_checkerboard(args):
+    """The 2D checkerboard (section "2D checkerboard": 7 x 7 unit blocks at
+    71 x 71 cells, absorbing blocks sigma_a = 10, scattering blocks sigma_s =
+    1) through the 2D reduction: solve time to the paper's residual 1e-10 for
+    P1 and P5 (FP32 GMRES inside FP64 refinement), CUDA events around the
+    solve, best of --steps after --warmup solves."""
+    import torch
+
+    import pn_inputs
+    from paper_1807_00410_gb300 import System
+    torch.cuda.set_device(0)
+    st, al, Q = pn_inputs.checkerboard_2d(71)
+    rows = []
+    for N in (1, 3, 5):
+        sysm = System(N, 71, st, al, 0.0, Q, dims=2)
+        times = []
+        for it in range(args.warmup + args.steps):
+            u = sysm.zeros(torch.float64)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s = sysm.solve(u, solver="ir", tol=1e-10, restart=30, ortho=args.ortho, max_iter=500000,
+                           max_outer=100)
+            e1.record()
+            e1.synchronize()
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        rows.append({"N": N, "dof": sysm.layout.n_active, "ms": min(times), "ms_median": statistics.median(times),
+                     "iterations": s["iterations"], "outer": s["outer_iterations"],
+                     "rel_residual": s["rel_residual"], "launches": s["launches"]})
+        sysm.close()
+    print(json.dumps({"mode": "checkerboard", "workload": "2D checkerboard, 7 x 7 unit blocks on 71 x 71 cells, "
+                      "sigma_a 10 / sigma_s 1, unit source in the centre block, vacuum boundary; FP32 GMRES(30) "
+                      "+ FP64 IR to 1e-10", "rows": rows}), flush=True)
+
+
+def run_batched(args):
+    """The many-instance workload (--batch-count systems, grids 24..96 cells
+    per axis, orders {1, 3, 5}, fBm extinction in [0.1, 60], point or beam
+    sources): wall time of one batched solve to 1e-6 (CUDA events around
+    pn_batch_solve, best of --steps after --warmup), against the same systems
+    solved one after another with pn_solve (FP32 GMRES + FP64 refinement, the
+    same restart and tolerance)."""
+    import numpy as np
+    import torch
+
+    import pn_inputs
+    from paper_1807_00410_gb300 import Batch, System
+    from paper_1807_00410_gb300 import pn as ppn
+    torch.cuda.set_device(0)
+    inst = pn_inputs.batch_instances(args.batch_count, args.batch_seed)
+    systems = []
+    for b in inst:
+        st = torch.tensor(b.sigma_t, dtype=torch.float64, device="cuda")
+        if b.source[0] == "point":
+            Q = torch.zeros((b.R,) * 3, dtype=torch.float64, device="cuda")
+            Q[b.source[1][0], b.source[1][1], b.source[1][2]] = float(b.R ** 3)
+        else:
+            _, axis, sign, radius, centre = b.source
+            Q = ppn.single_scatter_beam(b.N, st, b.albedo, b.g, axis, sign, radius, centre)
+        systems.append(System(b.N, b.R, st, b.albedo, b.g, Q))
+    dof = sum(s.layout.n_active for s in systems)
+    batch = Batch(systems, restart=args.restart, tune=True)
+    tiling = batch.tiling()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    times, stats = [], None
+    for it in range(args.warmup + args.steps):
+        us = [s.zeros(torch.float64) for s in systems]
+        ms, stats = timed(lambda: batch.solve(us, tol=1e-6, max_iter=200000, raise_on_error=False))
+        if it >= args.warmup:
+            times.append(ms)
+    its = [st["iterations"] for st in stats]
+    ok = sum(1 for st in stats if st["status"] == 0)
+
+    def one_by_one():
+        out = []
+        for s in systems:
+            u = s.zeros(torch.float64)
+            out.append(s.solve(u, solver="ir", tol=1e-6, restart=args.restart, ortho=args.ortho, max_iter=200000,
+                               raise_on_error=False))
+        return out
+    seq_ms, seq_stats = timed(one_by_one)
+    best = min(times)
+    print(json.dumps({
+        "mode": "batched", "workload": f"{len(systems)} instances (pn_inputs.batch_instances, seed "
+        f"{args.batch_seed}): grids 24..96 per axis, N in {{1,3,5}}, fBm sigma_t in [0.1, 60], albedo 0.7..0.99, "
+        f"g 0..0.7, point or beam source; FP32 GMRES({args.restart}) + FP64 IR to 1e-6",
+        "instances": len(systems), "dof": dof, "ms": best, "ms_median": statistics.median(times),
+        "solves_per_s": len(systems) / (best * 1e-3), "converged": ok,
+        "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
+        "launches": stats[0]["launches"], "tiling": tiling,
+        "one_by_one_ms": seq_ms, "one_by_one_converged": sum(1 for st in seq_stats if st["status"] == 0),
+        "one_by_one_launches": int(sum(st["launches"] for st in seq_stats)),
+        "speedup_vs_one_by_one": seq_ms / best, "steps": args.steps, "warmup": args.warmup}), flush=True)
+    batch.close()
+    for s in systems:
+        s.close()
+
+
 def main():
     args = parse()
+    if args.batched:
+        run_batched(args)
+        return
+    if args.checkerboard:
+        run_checkerboard(args)
+        return
     if args.threshold_sweep:
         run_threshold_sweep(args)
         return

@@ -73,6 +73,7 @@ extern "C" {
 #define PN_ERR_NOT_CONVERGED -4  /* solver hit max_iter; x holds the last iterate */
 #define PN_ERR_BREAKDOWN     -5  /* Krylov breakdown (zero norm denominator) */
 #define PN_ERR_NONFINITE     -6  /* NaN or Inf met in a residual or inner product */
+#define PN_ERR_TIMEOUT       -7  /* a bounded device-side wait (grid barrier) ran out */
 #define PN_ERR_UNSUPPORTED   -8  /* valid request this build does not implement */
 #define PN_ERR_TOO_LARGE     -9  /* request exceeds a fixed capacity of the library */
 
@@ -122,6 +123,25 @@ typedef struct {
  * available from pn_last_error(NULL).
  */
 int pn_create(pn_handle** out, int N, int R, const pn_medium* medium, int boundary, void* stream);
+
+/*
+ * Create a handle for the 2D reduction of the P_N system (section "2D
+ * checkerboard": parameters, source and boundary independent of z, so every
+ * coefficient with l + m odd vanishes and the z-derivatives drop out) on R^2
+ * cells of the unit square, R in [2, 16384].  The medium's arrays are
+ * indexed [y][x], R^2 each; a PN_Q_CENTRE_MOMENTS source holds one R^2 field
+ * per coefficient with l + m even, in increasing k = l^2 + l + m.
+ * The handle's layout (pn_get_layout): K = (N+1)(N+2)/2 planes, the parity
+ * classes with pz = 0 (0..3), each plane one slice of R+1 rows of pitch_x
+ * (pitch_y elements used, plane_stride = pitch_y rounded up to 32); plane_k
+ * holds the 3D coefficient index k.  Every operator, vector, solver and
+ * unstagger entry point accepts the handle (pn_unstagger then writes K x R^2
+ * in the order of the coefficient list); the learned preconditioner
+ * (pn_cnn_features, pn_cnn_targets, pn_cnn_output, pn_cnn_precondition,
+ * PN_SOLVER_IR_FGMRES) is 3D only and returns PN_ERR_UNSUPPORTED.
+ * Errors and ownership as for pn_create.
+ */
+int pn_create_2d(pn_handle** out, int N, int R, const pn_medium* medium, int boundary, void* stream);
 
 /* Free every buffer the handle owns.  NULL is accepted. */
 int pn_destroy(pn_handle* h);
@@ -301,21 +321,95 @@ int pn_cnn_train_step(pn_cnn* net, const float* in, const float* target, int B, 
 int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype, double* out, void* stream);
 
 /*
- * The learned preconditioner M(v) = s net(features(v / s)) + D^{-1} v with
+ * The learned preconditioner M(v) = s net(features(v / s)) + P v with
  * s = |v| / sqrt(n), n the number of unknowns (an extension; the paper has
  * no preconditioner).  features(u): for each
  * voxel (x, y, z) < R, channel p = u in plane p at slot (x, y, z), then
  * log(sigma_t h), sigma_s / sigma_t and g (c_in = K + 3); the network's K
- * output channels return to slot (x, y, z) of each plane; D is the
- * collision-minus-scattering diagonal.  R must be a multiple of 8.
- * pn_cnn_features writes scale * features(v) ([R^3][K+3], FP32, device);
- * pn_cnn_targets writes the training target scale * (e - D^{-1} r) at the
- * cells' own slots ([R^3][K]); pn_cnn_precondition writes z = M(v) (device
- * FP32 padded vectors; allocates scratch; synchronises).
+ * output channels return to slot (x, y, z) of each plane.  P is the fixed
+ * diagonal 1 / (D + 1/h), D the collision-minus-scattering diagonal (the
+ * Jacobi inverse where D dominates, h times the identity where transport
+ * does).  R must be a multiple of 8.  All vectors are device FP32 in the
+ * padded layout of pn_get_layout; network tensors are device FP32
+ * channels-last.
+ * pn_cnn_features writes scale * features(v) ([R^3][K+3]);
+ * pn_cnn_targets writes scale * (e - P r) at the cells' own slots ([R^3][K];
+ * r may be NULL: scale * e, the gather of a vector to the network layout);
+ * pn_cnn_output writes z = scale * net_out + P v (net_out [R^3][K] scattered
+ * to the cells' own slots, or NULL; v may be NULL), the map from network
+ * output to a P_N vector used by M and by residual-loss training;
+ * pn_cnn_precondition writes z = M(v) (allocates scratch; synchronises).
  */
 int pn_cnn_features(pn_handle* h, const float* v, double scale, float* out, void* stream);
 int pn_cnn_targets(pn_handle* h, const float* e, const float* r, double scale, float* out, void* stream);
+int pn_cnn_output(pn_handle* h, const float* net_out, double scale, const float* v, float* z, void* stream);
 int pn_cnn_precondition(pn_handle* h, pn_cnn* net, const float* v, float* z, void* stream);
+
+/*
+ * Batched solver: many systems of different grid sizes and orders solved
+ * together (an extension; the paper solves one system at a time).  Every
+ * phase is one kernel launch over all instances (the operator over
+ * (instance, plane, slot chunk) items with each instance's own couplings, the
+ * vector kernels over (instance, element chunk) items, persistent grids of a
+ * multiple of the SM count); one restart cycle of the inner GMRES(m) (4 m + 5
+ * launches, no host synchronisation inside) is captured once as a CUDA graph
+ * and replayed; instances converge independently (per-instance flags gate
+ * every work item, and an instance that reached its target freezes itself
+ * inside the cycle).
+ *
+ * pn_batch_create: `handles` (count >= 1) are borrowed and must outlive the
+ * batch; 3D and 2D handles may be mixed.  restart in [1, 16].  Allocates, per
+ * instance, restart + 3 FP32 vectors, one FP64 vector and the FP64 Arnoldi
+ * scalars; synchronises `stream`.  Errors: PN_ERR_ARG, PN_ERR_ALLOC,
+ * PN_ERR_CUDA.
+ * pn_batch_apply: y_i = A_i x_i for every instance in one launch; x, y are
+ * host arrays of `count` device pointers (each instance's padded layout,
+ * 16-byte aligned, not aliased), dtype PN_F32 or PN_F64.  Stream-ordered on
+ * `stream`.
+ * pn_batch_solve: solves every A_i u_i = Q_i by FP64 iterative refinement
+ * around the batched FP32 GMRES(restart) (opts->solver must be
+ * PN_SOLVER_IR_GMRES, opts->restart the batch's restart; tol, inner_tol,
+ * max_iter (inner iterations per instance) and max_outer as for pn_solve).
+ * u: host array of `count` device pointers to FP64 vectors (initial guesses,
+ * overwritten by the solutions); stats: host array of `count` records (status
+ * per instance; seconds and launches are the whole batch's).  Synchronises
+ * `stream` first and the batch's own stream before returning.  Returns PN_OK
+ * when every instance converged, else the first failing instance's status.
+ * pn_batch_set_tiling / pn_batch_get_tiling: operator chunk (slots, multiple
+ * of 256), vector chunk (elements, multiple of 1024) and CTAs per SM of the
+ * two kinds of persistent grid.
+ * pn_batch_tune: the autotuner: times the batched operator over operator
+ * chunk {4096, 16384, 65536} x {2, 4, 8} CTAs per SM, and the Arnoldi vector
+ * kernels over vector chunk {16384, 65536, 262144} x {2, 4, 8}, on this
+ * batch, and keeps the fastest of each (read them with pn_batch_get_tiling).
+ * pn_batch_set_mode: PN_BATCH_GRAPH (default) replays the captured cycle;
+ * PN_BATCH_PERSISTENT runs each cycle as ONE cooperative launch (a grid of
+ * resident CTAs, two per SM) whose phases are separated by grid barriers.
+ * Every barrier wait is bounded by spin_limit polls of about 100 ns; when one
+ * runs out the kernel ends and pn_batch_solve returns PN_ERR_TIMEOUT (the
+ * iterates are then those of the last completed cycle plus a partial one).
+ * pn_batch_barrier_test: one cooperative launch of `blocks` CTAs (at most the
+ * resident count) running a single barrier that expects `expected` >= blocks
+ * arrivals with the given spin limit: PN_OK and *timed_out = 0 when it
+ * completes (expected == blocks), PN_ERR_TIMEOUT and *timed_out = 1 when the
+ * wait runs out (expected > blocks), for tests of the timeout path.
+ */
+#define PN_BATCH_GRAPH      0
+#define PN_BATCH_PERSISTENT 1
+typedef struct pn_batch pn_batch;
+int pn_batch_create(pn_batch** out, pn_handle* const* handles, int count, int restart, void* stream);
+int pn_batch_destroy(pn_batch* batch);
+const char* pn_batch_last_error(const pn_batch* batch);
+int pn_batch_apply(pn_batch* batch, const void* const* x, void* const* y, int dtype, void* stream);
+int pn_batch_solve(pn_batch* batch, double* const* u, const pn_solve_opts* opts, pn_solve_stats* stats,
+                   void* stream);
+int pn_batch_set_tiling(pn_batch* batch, int64_t op_chunk, int64_t vec_chunk, int op_ctas_per_sm,
+                        int vec_ctas_per_sm);
+int pn_batch_get_tiling(const pn_batch* batch, int64_t* op_chunk, int64_t* vec_chunk, int* op_ctas_per_sm,
+                        int* vec_ctas_per_sm);
+int pn_batch_tune(pn_batch* batch, void* stream);
+int pn_batch_set_mode(pn_batch* batch, int mode, long long spin_limit);
+int pn_batch_barrier_test(int blocks, int expected, long long spin_limit, int* timed_out, void* stream);
 
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */

@@ -73,7 +73,7 @@ int dev_alloc(pn_handle* h, T** p, size_t count, const char* what) {
 // Writes one padded plane from a voxel-centre field: every active slot gets
 // the mean of its adjacent in-domain centres, every other slot 0.
 __global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int64_t pitch_x,
-                             int64_t pitch_y, int64_t plane_stride, double* out_d, float* out_f) {
+                             int64_t pitch_y, int64_t nzb, int64_t plane_stride, double* out_d, float* out_f) {
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < plane_stride;
          s += int64_t(gridDim.x) * blockDim.x) {
         const int x = int(s % pitch_x);
@@ -81,7 +81,7 @@ __global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int
         const int y = int(t % (R + 1));
         const int z = int(t / (R + 1));
         double v = 0.0;
-        if (s < pitch_y * (R + 1) && x < R + px && y < R + py && z < R + pz) {
+        if (s < pitch_y * nzb && x < R + px && y < R + py && z < R + pz) {
             const int x0 = px ? max(x - 1, 0) : x, x1 = px ? min(x, R - 1) : x;
             const int y0 = py ? max(y - 1, 0) : y, y1 = py ? min(y, R - 1) : y;
             const int z0 = pz ? max(z - 1, 0) : z, z1 = pz ? min(z, R - 1) : z;
@@ -185,11 +185,19 @@ void pn_default_solve_opts(pn_solve_opts* o) {
     o->precond = nullptr;
 }
 
-int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// pn_create (dims 3) and pn_create_2d (dims 2, the z-independent reduction:
+// coefficients with l + m even, x and y transport only, R^2 centre fields).
+int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream, int dims) {
     if (!out) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: out is NULL");
     *out = nullptr;
     if (N < 0 || N > PN_MAX_N) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: N must be in [0, 7]");
-    if (R < 2 || R > 1024) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: R must be in [2, 1024]");
+    if (R < 2 || R > (dims == 3 ? 1024 : 16384))
+        return pn_fail(nullptr, PN_ERR_ARG, dims == 3 ? "pn_create: R must be in [2, 1024]"
+                                                      : "pn_create_2d: R must be in [2, 16384]");
     if (!m || !m->sigma_t) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: medium or sigma_t is NULL");
     if (m->dtype != PN_F32 && m->dtype != PN_F64) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: bad medium dtype");
     if (boundary != PN_BC_VACUUM) return pn_fail(nullptr, PN_ERR_UNSUPPORTED, "pn_create: only PN_BC_VACUUM is built");
@@ -203,34 +211,40 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
     if (!h) return pn_fail(nullptr, PN_ERR_ALLOC, "pn_create: host allocation failed");
     cudaGetDevice(&h->device);
     h->N = N;
-    h->K = (N + 1) * (N + 1);
+    h->dims = dims;
     h->R = R;
     h->h = 1.0 / R;
     h->g = m->g;
     h->pitch_x = round_up(R + 1, 4);
     h->pitch_y = h->pitch_x * (R + 1);
-    h->plane_stride = round_up(h->pitch_y * (R + 1), 32);
-    h->n_elems = h->plane_stride * h->K;
+    h->nz_box = dims == 3 ? R + 1 : 1;
+    h->plane_stride = round_up(h->pitch_y * h->nz_box, 32);
 
-    // planes grouped by parity class, coefficient order within a class
-    const int K = h->K;
-    std::vector<int> cls_of_k(K);
+    // planes grouped by parity class, coefficient order within a class; the
+    // 2D reduction keeps the classes with pz = 0 (l + m even)
+    const int K3 = (N + 1) * (N + 1);
+    std::vector<int> cls_of_k(K3), idx2(K3, -1);
     for (int l = 0, k = 0; l <= N; ++l)
         for (int mm = -l; mm <= l; ++mm, ++k) {
             int px, py, pz;
             pn::parity_bits(l, mm, px, py, pz);
             cls_of_k[k] = px + 2 * py + 4 * pz;
         }
+    for (int k = 0, j = 0; k < K3; ++k)
+        if (cls_of_k[k] < 4) idx2[k] = j++;  // position in the 2D coefficient list
+    for (int q = 0; q < PN_MAX_K; ++q) h->plane_k[q] = h->plane_class[q] = h->plane_of_k[q] = -1;
     int p = 0;
-    for (int c = 0; c < 8; ++c)
-        for (int k = 0; k < K; ++k)
+    for (int c = 0; c < (dims == 3 ? 8 : 4); ++c)
+        for (int k = 0; k < K3; ++k)
             if (cls_of_k[k] == c) {
                 h->plane_k[p] = k;
                 h->plane_class[p] = c;
                 h->plane_of_k[k] = p;
                 ++p;
             }
-    for (int q = K; q < PN_MAX_K; ++q) h->plane_k[q] = h->plane_class[q] = -1;
+    h->K = p;
+    h->n_elems = h->plane_stride * h->K;
+    const int K = h->K;
 
     std::vector<double> A;
     pn::transport_couplings(N, A);
@@ -244,6 +258,7 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
         P.k = k;
         P.l = l;
         P.m = k - l * l - l;
+        P.kc = dims == 3 ? k : idx2[k];
         P.cls = h->plane_class[q];
         P.px = P.cls & 1;
         P.py = (P.cls >> 1) & 1;
@@ -251,12 +266,16 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
         P.fl_d = l == 0 ? 1.0 : std::pow(m->g, l);
         P.fl_f = float(P.fl_d);
         P.t0 = int(h->terms.size());
-        for (int d = 0; d < 3; ++d)
-            for (int kp = 0; kp < K; ++kp) {
-                const double a = A[(size_t(d) * K + k) * K + kp];
+        for (int d = 0; d < dims; ++d)
+            for (int kp = 0; kp < K3; ++kp) {
+                const double a = A[(size_t(d) * K3 + k) * K3 + kp];
                 if (a == 0.0) continue;
                 pn::Term t;
                 t.q = h->plane_of_k[kp];
+                if (t.q < 0) {  // A_x, A_y never couple l + m even to odd: unreachable
+                    delete h;
+                    return pn_fail(nullptr, PN_ERR_ARG, "pn_create: coupling to a coefficient outside the layout");
+                }
                 t.axis = d;
                 t.cd = a * R;  // A_d / h
                 t.cf = float(t.cd);
@@ -264,11 +283,11 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
             }
         P.t1 = int(h->terms.size());
         h->planes[q] = P;
-        h->n_active += int64_t(R + P.px) * (R + P.py) * (R + P.pz);
+        h->n_active += int64_t(R + P.px) * (R + P.py) * (dims == 3 ? R + P.pz : 1);
     }
 
     int rc = PN_OK;
-    const int64_t V = int64_t(R) * R * R;
+    const int64_t V = dims == 3 ? int64_t(R) * R * R : int64_t(R) * R;
     std::vector<double> st, al;
 #define PN_TRY(x)                       \
     do {                                \
@@ -342,8 +361,9 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
         const unsigned char* base = (const unsigned char*)m->Q;
         const size_t esz = m->dtype == PN_F32 ? 4 : 8;
         for (int q = 0; q < h->n_q_planes && rc == PN_OK; ++q) {
-            // q_mode 0: plane 0 is coefficient 0 (class 0 comes first)
-            const int k = h->n_q_planes == 1 ? 0 : h->plane_k[q];
+            // q_mode 0: plane 0 is coefficient 0 (class 0 comes first); in 2D
+            // the moments come in the order of the 2D coefficient list
+            const int k = h->n_q_planes == 1 ? 0 : (dims == 3 ? h->plane_k[q] : idx2[h->plane_k[q]]);
             rc = load_field(nullptr, base + size_t(k) * V * esz, V, m->dtype, m->on_device, qk);
             if (rc != PN_OK) break;
             cudaError_t e = cudaMemcpy(tmp, qk.data(), V * 8, cudaMemcpyHostToDevice);
@@ -353,7 +373,7 @@ int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, v
             }
             const pn::Plane& P = h->planes[q];
             k_fill_plane<<<8 * pn_sm_count(), 256, 0, s>>>(tmp, R, P.px, P.py, P.pz, h->pitch_x, h->pitch_y,
-                                                         h->plane_stride, h->d_q_d + q * h->plane_stride,
+                                                         h->nz_box, h->plane_stride, h->d_q_d + q * h->plane_stride,
                                                          h->d_q_f + q * h->plane_stride);
             e = cudaStreamSynchronize(s);
             if (e == cudaSuccess) e = cudaGetLastError();
@@ -385,6 +405,18 @@ fail:
     free_all(h);
     delete h;
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pn_create(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream) {
+    return create_impl(out, N, R, m, boundary, stream, 3);
+}
+
+int pn_create_2d(pn_handle** out, int N, int R, const pn_medium* m, int boundary, void* stream) {
+    return create_impl(out, N, R, m, boundary, stream, 2);
 }
 
 int pn_destroy(pn_handle* h) {

@@ -23,7 +23,8 @@ struct Term {
 
 // Per-plane description.
 struct Plane {
-    int k, l, m;       // coefficient
+    int k, l, m;       // coefficient (k = l^2 + l + m)
+    int kc;            // its index in the handle's coefficient list (3D: k; 2D: among l + m even)
     int cls;           // px + 2 py + 4 pz
     int px, py, pz;    // parity bits
     int t0, t1;        // term range [t0, t1) in the term table
@@ -50,6 +51,8 @@ int pn_sm_count();
 
 struct pn_handle {
     int N = 0, K = 0, R = 0;
+    int dims = 3;        // 3: R^3 cells; 2: the z-independent reduction on R^2 cells
+    int64_t nz_box = 0;  // z-slices of a plane box: R + 1 (3D) or 1 (2D)
     double h = 0.0;
     double g = 0.0;  // Henyey-Greenstein mean cosine
     int64_t pitch_x = 0, pitch_y = 0, plane_stride = 0, n_elems = 0, n_active = 0;
@@ -63,7 +66,7 @@ struct pn_handle {
     // device copies of the tables
     pn::Plane* d_planes = nullptr;
     pn::Term* d_terms = nullptr;
-    // voxel-centre fields (clamped sigma_t, sigma_s = albedo sigma_t), R^3 each
+    // voxel-centre fields (clamped sigma_t, sigma_s = albedo sigma_t), R^3 (2D: R^2) each
     float* d_st_f = nullptr;
     float* d_ss_f = nullptr;
     double* d_st_d = nullptr;

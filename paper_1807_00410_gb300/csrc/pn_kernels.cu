@@ -10,47 +10,9 @@
 #include <cstdint>
 
 #include "pn_internal.h"
+#include "pn_op.cuh"
 
 namespace pn {
-
-template <typename T>
-struct OpArgs {
-    const T* x;
-    T* y;
-    const T* q;        // source planes (n_q) or null
-    int n_q;
-    const T* bvec;     // residual against this full vector instead of Q (or null)
-    const T* st;       // clamped sigma_t at voxel centres, R^3
-    const T* ss;       // sigma_s at voxel centres, R^3
-    const Plane* planes;
-    const Term* terms;
-    int R;
-    int64_t pitch_x, pitch_y, plane_stride;
-    double* partials;  // residual: per-block sums of r^2
-};
-
-template <typename T> __device__ __forceinline__ T term_coef(const Term& t);
-template <> __device__ __forceinline__ float term_coef<float>(const Term& t) { return t.cf; }
-template <> __device__ __forceinline__ double term_coef<double>(const Term& t) { return t.cd; }
-template <typename T> __device__ __forceinline__ T plane_fl(const Plane& p);
-template <> __device__ __forceinline__ float plane_fl<float>(const Plane& p) { return p.fl_f; }
-template <> __device__ __forceinline__ double plane_fl<double>(const Plane& p) { return p.fl_d; }
-
-// Mean of a centre field over the in-domain voxel centres adjacent to slot
-// (x, y, z) of a grid with parity bits (px, py, pz).  Along an odd axis the
-// candidates are slots i-1 and i; clamping both into [0, R) repeats the single
-// in-domain centre at a boundary face, which leaves the mean unchanged.
-template <typename T>
-__device__ __forceinline__ T centre_mean(const T* F, int R, int x, int y, int z, int px, int py, int pz) {
-    const int x0 = px ? max(x - 1, 0) : x, x1 = px ? min(x, R - 1) : x;
-    const int y0 = py ? max(y - 1, 0) : y, y1 = py ? min(y, R - 1) : y;
-    const int z0 = pz ? max(z - 1, 0) : z, z1 = pz ? min(z, R - 1) : z;
-    const int64_t R2 = int64_t(R) * R;
-    T s = F[z0 * R2 + y0 * R + x0] + F[z0 * R2 + y0 * R + x1] + F[z0 * R2 + y1 * R + x0] +
-          F[z0 * R2 + y1 * R + x1] + F[z1 * R2 + y0 * R + x0] + F[z1 * R2 + y0 * R + x1] +
-          F[z1 * R2 + y1 * R + x0] + F[z1 * R2 + y1 * R + x1];
-    return s * T(0.125);
-}
 
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double red[32];
@@ -68,44 +30,13 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;  // valid in thread 0
 }
 
-// One output of the operator at slot (x, y, z) of plane p (active slot).
-template <typename T, int MODE>
-__device__ __forceinline__ T op_point(const OpArgs<T>& a, int p, const Plane& P, int x, int y, int z, int64_t s) {
-    const int R = a.R;
-    const int64_t pbase = int64_t(p) * a.plane_stride;
-    const T diag = centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
-                   plane_fl<T>(P) * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
-    T acc = diag * a.x[pbase + s];
-    T tr = T(0);
-    for (int ti = P.t0; ti < P.t1; ++ti) {
-        const Term tm = a.terms[ti];
-        int i, b;
-        int64_t stride;
-        if (tm.axis == 0) { i = x; b = P.px; stride = 1; }
-        else if (tm.axis == 1) { i = y; b = P.py; stride = a.pitch_x; }
-        else { i = z; b = P.pz; stride = a.pitch_y; }
-        const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
-        // plus neighbour at slot i + 1 - b (exists iff < R + 1 - b),
-        // minus neighbour at slot i - b (exists iff >= 0)
-        const T vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
-        const T vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
-        tr += term_coef<T>(tm) * (vp - vm);
-    }
-    acc = (MODE == OP_APPLY_T) ? acc - tr : acc + tr;
-    if (MODE == OP_RESIDUAL) {
-        const T bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : T(0));
-        return bq - acc;
-    }
-    return acc;
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_op_naive(OpArgs<T> a) {
     const int p = blockIdx.y;
     const Plane P = a.planes[p];
     const int R = a.R;
     const int ny = R + 1;
-    const int64_t box = a.pitch_y * int64_t(R + 1);
+    const int64_t box = a.pitch_y * int64_t(a.nzb);
     const int64_t pbase = int64_t(p) * a.plane_stride;
     double racc = 0.0;
     T rrun = T(0);  // residual squares summed in T per thread, flushed to FP64 every 16
@@ -190,8 +121,14 @@ static int slab_grid_x(const pn_handle* h) {
     return int(g < 1 ? 1 : g);
 }
 
+static bool use_tiled(const pn_handle* h, int dtype) {
+    // the tiled kernel (3D only) forms addresses with 32-bit element offsets
+    // of up to 16 planes: it needs plane_stride * 16 < 2^32 (R <= 1000 or so)
+    return dtype == PN_F32 && h->dims == 3 && h->plane_stride * 16 < (int64_t(1) << 32);
+}
+
 int op_partial_count(const pn_handle* h, int dtype) {
-    if (dtype == PN_F32 && h->plane_stride * 16 < (int64_t(1) << 32)) return tiled_partial_count(h);
+    if (use_tiled(h, dtype)) return tiled_partial_count(h);
     return naive_grid_x(h) * h->K;
 }
 
@@ -202,7 +139,8 @@ static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T*
     a.x = x; a.y = y; a.q = q; a.n_q = h->n_q_planes; a.bvec = bvec;
     a.st = st; a.ss = ss;
     a.planes = h->d_planes; a.terms = h->d_terms;
-    a.R = h->R; a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
+    a.R = h->R; a.nzb = int(h->nz_box);
+    a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
     a.partials = partials;
     dim3 grid(naive_grid_x(h), h->K);
     if (mode == OP_APPLY) k_op_naive<T, OP_APPLY><<<grid, 256, 0, s>>>(a);
@@ -213,13 +151,13 @@ static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T*
 
 cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
                       double* partials, cudaStream_t s, const void* bvec) {
-    // the tiled kernel forms addresses with 32-bit element offsets of up to
-    // MAXC planes: it needs plane_stride * 16 < 2^32 (R <= 1000 or so)
-    const bool tiled_ok = h->plane_stride * 16 < (int64_t(1) << 32);
-    if (dtype == PN_F32 && tiled_ok) {
+    if (use_tiled(h, dtype)) {
         // tiled kernel for x < x_end, face-column kernel for the rest
         return launch_tiled(h, mode, (const float*)x, (float*)y, (const float*)bvec, partials, s);
     }
+    if (dtype == PN_F32)
+        return op_t<float>(h, mode, (const float*)x, (float*)y, h->d_st_f, h->d_ss_f, h->d_q_f, (const float*)bvec,
+                           partials, s);
     return op_t<double>(h, mode, (const double*)x, (double*)y, h->d_st_d, h->d_ss_d, h->d_q_d,
                         (const double*)bvec, partials, s);
 }

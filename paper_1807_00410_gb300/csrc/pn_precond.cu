@@ -1,17 +1,24 @@
 // Learned preconditioner glue: P_N vectors <-> network tensors, and the
 // preconditioner application used inside flexible GMRES.
 //
-//   M(v) = s net(features(v / s)) + D^{-1} v,   s = |v| / sqrt(n) (RMS of v over
+//   M(v) = s net(features(v / s)) + P v,   s = |v| / sqrt(n) (RMS of v over
 //   the n unknowns, so the network sees values of order one)
+//
+// P is a fixed row-scaled diagonal, P = diag(1 / (D + 1/h)) with D the
+// collision-minus-scattering diagonal and 1/h the scale of the transport
+// couplings of a row: in optically thick cells it is the Jacobi inverse
+// D^{-1}, in thin cells (where D^{-1} would amplify every rough component by
+// 1/D) it is h times the identity.  P covers every unknown, including the
+// x = R, y = R, z = R face slots the network does not see, so M is never
+// rank-deficient.
 //
 // features(u) at voxel (x, y, z) < R: channel p = u of plane p at slot
 // (x, y, z) (the cell's own slot on every staggered grid), then
 // log(sigma_t h), sigma_s / sigma_t and g.  The network's K output channels
-// go back to slot (x, y, z) of each plane; the Jacobi term D^{-1} v (D the
-// collision-minus-scattering diagonal) covers every unknown, including the
-// x = R, y = R, z = R face slots the network does not see, so M is never
-// rank-deficient.  The network is trained on pairs (r, e) with A e = r:
-// input features(r / s), target (e - D^{-1} r) / s, s = RMS of r.
+// go back to slot (x, y, z) of each plane.  Training either fits pairs
+// (r, e) with A e = r (target (e - P r) / s) or minimises |A M(r) - r|^2 /
+// |r|^2 directly, with the gradient A^T (A M(r) - r) gathered back to the
+// cell slots (pn_cnn_output, pn_cnn_targets).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,6 +38,13 @@ __device__ __forceinline__ float centre_mean_f(const float* F, int R, int x, int
     return 0.125f * (F[z0 * R2 + y0 * R + x0] + F[z0 * R2 + y0 * R + x1] + F[z0 * R2 + y1 * R + x0] +
                      F[z0 * R2 + y1 * R + x1] + F[z1 * R2 + y0 * R + x0] + F[z1 * R2 + y0 * R + x1] +
                      F[z1 * R2 + y1 * R + x0] + F[z1 * R2 + y1 * R + x1]);
+}
+
+// D + 1/h at slot (x, y, z) of plane P (the fixed part's row scale)
+__device__ __forceinline__ float fixed_row(const float* st, const float* ss, int R, int x, int y, int z,
+                                           const pn::Plane& P) {
+    return centre_mean_f(st, R, x, y, z, P.px, P.py, P.pz) - P.fl_f * centre_mean_f(ss, R, x, y, z, P.px, P.py, P.pz) +
+           float(R);
 }
 
 struct FeatArgs {
@@ -72,8 +86,8 @@ __global__ void k_features(FeatArgs a) {
     }
 }
 
-// z = scale * net_out (slots < R) + jac * D^{-1} v  over the whole padded vector;
-// target mode (e != null): out[v][c] = scale * (e - D^{-1} r) at slots < R.
+// z = scale * net_out (slots < R) + P v over the whole padded vector (either
+// term may be absent).
 struct ScatterArgs {
     const float* net_out;  // [R^3][K] or null
     const double* nrm2;    // device |v|^2: scale = |v| * scale field (or null: scale field)
@@ -105,18 +119,15 @@ __global__ void k_scatter(ScatterArgs a) {
             if (x < R + P.px && y < R + P.py && zz < R + P.pz) {
                 if (a.net_out && x < R && y < R && zz < R)
                     out = sc * a.net_out[((int64_t(zz) * R + y) * R + x) * a.K + p];
-                if (a.v) {
-                    const float d = centre_mean_f(a.st, R, x, y, zz, P.px, P.py, P.pz) -
-                                    P.fl_f * centre_mean_f(a.ss, R, x, y, zz, P.px, P.py, P.pz);
-                    out += a.v[i] / d;
-                }
+                if (a.v) out += a.v[i] / fixed_row(a.st, a.ss, R, x, y, zz, P);
             }
         }
         a.z[i] = out;
     }
 }
 
-// target[v][c] = scale * (e - D^{-1} r) at the cell's own slots
+// target[v][c] = scale * (e - P r) at the cell's own slots (r may be null:
+// scale * e, the gather of a padded vector to the network's layout)
 __global__ void k_targets(const float* e, const float* r, float scale, const pn::Plane* planes, const float* st,
                           const float* ss, int R, int K, int64_t pitch_x, int64_t pitch_y, int64_t plane_stride,
                           float* out) {
@@ -127,8 +138,7 @@ __global__ void k_targets(const float* e, const float* r, float scale, const pn:
         const int x = int(v % R), y = int((v / R) % R), z = int(v / (int64_t(R) * R));
         const pn::Plane P = planes[c];
         const int64_t off = int64_t(c) * plane_stride + z * pitch_y + y * pitch_x + x;
-        const float d = centre_mean_f(st, R, x, y, z, P.px, P.py, P.pz) - P.fl_f * centre_mean_f(ss, R, x, y, z, P.px, P.py, P.pz);
-        out[i] = scale * (e[off] - r[off] / d);
+        out[i] = r ? scale * (e[off] - r[off] / fixed_row(st, ss, R, x, y, z, P)) : scale * e[off];
     }
 }
 
@@ -170,6 +180,7 @@ extern "C" {
 
 int pn_cnn_features(pn_handle* h, const float* v, double scale, float* out, void* stream) {
     if (!h || !v || !out) return PN_ERR_ARG;
+    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_features: 3D handles only");
     const int64_t V = int64_t(h->R) * h->R * h->R;
     FeatArgs fa{v, nullptr, scale, h->d_st_f, h->d_ss_f, float(h->g), h->R, h->K, h->pitch_x, h->pitch_y,
                 h->plane_stride, out};
@@ -179,7 +190,8 @@ int pn_cnn_features(pn_handle* h, const float* v, double scale, float* out, void
 }
 
 int pn_cnn_targets(pn_handle* h, const float* e, const float* r, double scale, float* out, void* stream) {
-    if (!h || !e || !r || !out) return PN_ERR_ARG;
+    if (!h || !e || !out) return PN_ERR_ARG;
+    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_targets: 3D handles only");
     const int64_t V = int64_t(h->R) * h->R * h->R;
     k_targets<<<grid_for(V * h->K), 256, 0, (cudaStream_t)stream>>>(e, r, float(scale), h->d_planes, h->d_st_f,
                                                                       h->d_ss_f, h->R, h->K, h->pitch_x, h->pitch_y,
@@ -188,8 +200,19 @@ int pn_cnn_targets(pn_handle* h, const float* e, const float* r, double scale, f
     return er == cudaSuccess ? PN_OK : pn_cuda_fail(h, er, "pn_cnn_targets");
 }
 
+int pn_cnn_output(pn_handle* h, const float* net_out, double scale, const float* v, float* z, void* stream) {
+    if (!h || !z) return PN_ERR_ARG;
+    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_output: 3D handles only");
+    ScatterArgs sa{net_out, nullptr, scale, v, z, h->d_planes, h->d_st_f, h->d_ss_f, h->R, h->K, h->pitch_x,
+                   h->pitch_y, h->plane_stride};
+    k_scatter<<<grid_for(h->n_elems), 256, 0, (cudaStream_t)stream>>>(sa);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PN_OK : pn_cuda_fail(h, e, "pn_cnn_output");
+}
+
 int pn_cnn_precondition(pn_handle* h, struct pn_cnn* net, const float* v, float* z, void* stream) {
     if (!h || !net || !v || !z) return PN_ERR_ARG;
+    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_precondition: 3D handles only");
     if (h->R % 8) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_precondition: R must be a multiple of 8");
     const int64_t V = int64_t(h->R) * h->R * h->R;
     float* scratch = nullptr;

@@ -507,7 +507,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
     double* S = h->d_scalars;
     // workspace: V (m+1 vectors), [Z (m vectors), preconditioner scratch],
     // then FP64 H ((m+1) x m), cs, sn, g, y, add
-    if (net && (sizeof(T) != 4 || h->R % 8)) net = nullptr;  // the network runs on FP32, R % 8 == 0
+    if (net && (sizeof(T) != 4 || h->R % 8 || h->dims != 3)) net = nullptr;  // the network runs on FP32, R % 8 == 0
     const int64_t V3 = int64_t(h->R) * h->R * h->R;
     const size_t zbytes = net ? size_t(m) * n * sizeof(T) + size_t(V3) * (2 * h->K + 3) * sizeof(float) + 256 : 0;
     const size_t vbytes = size_t(m + 1) * n * sizeof(T) + zbytes;
@@ -751,6 +751,8 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
         return pn_fail(h, PN_ERR_ARG, "pn_solve: unknown solver");
     if (o.solver == PN_SOLVER_IR_FGMRES && !o.precond)
         return pn_fail(h, PN_ERR_ARG, "pn_solve: PN_SOLVER_IR_FGMRES needs opts->precond");
+    if (o.solver == PN_SOLVER_IR_FGMRES && h->dims != 3)
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the learned preconditioner is 3D only");
     if (o.solver == PN_SOLVER_IR_FGMRES && h->R % 8)
         return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the learned preconditioner needs R % 8 == 0");
     if (o.solver < PN_SOLVER_IR_GMRES && o.precision != PN_F32 && o.precision != PN_F64)

@@ -90,9 +90,9 @@ __global__ void k_beam(BeamArgs<T> a) {
 }
 
 template <typename T>
-__global__ void k_unstagger(const T* x, T* out, const pn::Plane* planes, int R, int64_t pitch_x, int64_t pitch_y,
-                            int64_t plane_stride, int K) {
-    const int64_t V = int64_t(R) * R * R;
+__global__ void k_unstagger(const T* x, T* out, const pn::Plane* planes, int R, int nzc, int64_t pitch_x,
+                            int64_t pitch_y, int64_t plane_stride, int K) {
+    const int64_t V = int64_t(R) * R * nzc;  // cells (nzc = R; 1 for the 2D reduction, whose planes have pz = 0)
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < V * K; t += int64_t(gridDim.x) * blockDim.x) {
         const int p = int(t / V);
         const int64_t c = t % V;
@@ -105,7 +105,7 @@ __global__ void k_unstagger(const T* x, T* out, const pn::Plane* planes, int R, 
                 for (int dx = 0; dx <= P.px; ++dx)
                     acc += b[(zi + dz) * pitch_y + (yi + dy) * pitch_x + xi + dx];
         const int n = (1 + P.px) * (1 + P.py) * (1 + P.pz);
-        out[int64_t(P.k) * V + c] = acc / T(n);
+        out[int64_t(P.kc) * V + c] = acc / T(n);
     }
 }
 
@@ -160,15 +160,16 @@ extern "C" int pn_single_scatter_beam(int N, int R, const void* sigma_t, const v
 extern "C" int pn_unstagger(pn_handle* h, const void* x, void* out, int dtype, void* stream) {
     if (!h) return PN_ERR_ARG;
     if (!x || !out || (dtype != PN_F32 && dtype != PN_F64)) return pn_fail(h, PN_ERR_ARG, "pn_unstagger: bad argument");
-    const int64_t V = int64_t(h->R) * h->R * h->R;
+    const int nzc = h->dims == 3 ? h->R : 1;
+    const int64_t V = int64_t(h->R) * h->R * nzc;
     const int blocks = int(std::min<int64_t>((V * h->K + 255) / 256, 8 * int64_t(pn_sm_count()) * 8));
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == PN_F32)
-        k_unstagger<float><<<blocks, 256, 0, s>>>((const float*)x, (float*)out, h->d_planes, h->R, h->pitch_x,
+        k_unstagger<float><<<blocks, 256, 0, s>>>((const float*)x, (float*)out, h->d_planes, h->R, nzc, h->pitch_x,
                                                   h->pitch_y, h->plane_stride, h->K);
     else
-        k_unstagger<double><<<blocks, 256, 0, s>>>((const double*)x, (double*)out, h->d_planes, h->R, h->pitch_x,
-                                                   h->pitch_y, h->plane_stride, h->K);
+        k_unstagger<double><<<blocks, 256, 0, s>>>((const double*)x, (double*)out, h->d_planes, h->R, nzc,
+                                                   h->pitch_x, h->pitch_y, h->plane_stride, h->K);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_unstagger");
     return PN_OK;

@@ -1,22 +1,27 @@
 """Training and evaluation of the learned preconditioner (an extension of
 the paper's solver; the paper has no network).
 
-Data: for seeded random media (value-noise fBm extinction, albedo and g
-drawn per medium) and seeded sources (point sources and collimated-beam
-single-scatter sources), the library's own solver computes u with A u = Q
-(FP64 iterative refinement to 1e-6).  Each solved pair (Q, u), and random
-linear combinations of pairs of the same medium (still exact pairs, by
-linearity), gives one training sample: input features(r / s) and target
-(e - D^{-1} r) / s with s the RMS of r over the unknowns (pn_cnn_features /
-pn_cnn_targets; the preconditioner scales the same way).  The network is
-trained with pn_cnn_train_step (forward, relative-L2 loss, backward and Adam,
-all on the GPU with the library's kernels).
+The preconditioner is M(v) = s net(features(v / s)) + P v with s the RMS of
+v over the unknowns and P = diag(1 / (D + 1/h)) (pn_cnn_output).  FGMRES
+applies M to Krylov vectors, so the network is trained on the residual loss
 
-The discrete P_N system in cell units depends only on sigma_t h, albedo and g,
-so media for a grid of R cells are drawn with sigma_t in [lo, hi] * R / 64 to
-match the optical thickness per cell of the 64^3 workload; the network (fully
-convolutional, fed log(sigma_t h)) is trained on small grids and applied to
-64^3 ones.
+    L(r) = |A M(r) - r|^2 / |r|^2
+
+over vectors r that look like those: the sources themselves (point sources
+and collimated-beam single-scatter sources), residuals Q - A x_k of partial
+GMRES solves (k iterations), normalised Krylov powers A^j Q, and random
+combinations of these for the same medium.  Its gradient with respect to the
+network output is s gather(2 A^T (A M(r) - r)) / |r|^2, computed with the
+library's own operator and transpose (pn_apply, pn_apply_t, pn_cnn_targets
+as the gather); forward, backward and Adam run in the library's kernels
+(pn_cnn_forward, pn_cnn_backward, pn_cnn_adam_step).
+
+Media are seeded value-noise fBm extinction fields with albedo and g drawn
+per medium.  The discrete P_N system in cell units depends only on
+sigma_t h, albedo and g, so media for a grid of R cells are drawn with
+sigma_t in [lo, hi] * R / 64 to match the optical thickness per cell of the
+64^3 workload; the network (fully convolutional, fed log(sigma_t h)) is
+trained on small grids and applied to 64^3 ones.
 
 Usage:
     python -m paper_1807_00410_gb300.learned train --out weights.npy
@@ -116,6 +121,137 @@ def make_dataset(seeds, R: int, n_src: int, n_mix: int, torch, log=print):
     return torch.stack(feats), torch.stack(tgts)
 
 
+def source_vectors(seed: int, R: int, n_src: int, torch):
+    """([r32 padded source vectors], System of the medium) for the seeded
+    medium and sources."""
+    from paper_1807_00410_gb300 import System
+    from paper_1807_00410_gb300 import pn as ppn
+    st, albedo, g = medium(seed, R)
+    st_d = torch.tensor(st, dtype=torch.float64, device="cuda")
+    vecs, keep = [], None
+    for spec in sources(seed, R, n_src):
+        if spec[0] == "point":
+            Q = np.zeros((R, R, R))
+            Q[spec[1]] = float(R ** 3)
+            sysm = System(N_ORDER, R, st_d, albedo, g, torch.tensor(Q, dtype=torch.float64, device="cuda"))
+        else:
+            _, axis, sign, radius, centre = spec
+            sysm = System(N_ORDER, R, st_d, albedo, g,
+                          ppn.single_scatter_beam(N_ORDER, st_d, albedo, g, axis, sign, radius, centre))
+        r = sysm.zeros(torch.float32)
+        sysm.residual(sysm.zeros(torch.float32), r)  # r = Q
+        vecs.append((r, sysm))
+    return vecs
+
+
+def residual_pool(seed: int, R: int, n_src: int, torch, partial=(5, 15, 45), powers=(1, 3), n_mix: int = 4,
+                  rng=None):
+    """(System, (n, n_elems) FP32 unit-RMS residual vectors) for one medium."""
+    rng = rng or np.random.Generator(np.random.PCG64(seed))
+    pairs = source_vectors(seed, R, n_src, torch)
+    sysm = pairs[0][1]
+    n_act = sysm.layout.n_active
+    out = []
+
+    def add(v):
+        nv = float(torch.linalg.vector_norm(v.double()))
+        if nv > 0.0 and math.isfinite(nv):
+            out.append(v * (math.sqrt(n_act) / nv))
+
+    for r, sq in pairs:
+        add(r)
+        for k in partial:
+            x = sq.zeros(torch.float32)
+            # stops after k iterations, unconverged: its residual is the sample
+            sq.solve(x, solver="gmres", tol=1e-12, restart=15, ortho="cgs1", max_iter=k, raise_on_error=False)
+            rk = sq.zeros(torch.float32)
+            sq.residual(x, rk)
+            add(rk)
+        w = r
+        for j in range(1, max(powers) + 1):
+            w2 = sq.zeros(torch.float32)
+            sq.apply(w, w2)
+            w = w2 * (1.0 / max(float(torch.linalg.vector_norm(w2.double())), 1e-300))
+            if j in powers:
+                add(w)
+    base = list(out)
+    for _ in range(n_mix):
+        c = rng.standard_normal(len(base))
+        add(sum(float(ck) * v for ck, v in zip(c, base)))
+    for _, sq in pairs[1:]:
+        sq.close()
+    return sysm, torch.stack(out)
+
+
+def fgmres_residuals(net, seed: int, R: int, n_src: int, torch, cycles=(2, 5), restart: int = 15):
+    """Residuals Q - A x_c that flexible GMRES with the current network leaves
+    after c restart cycles, one per source and c (unit RMS, FP32): the
+    components the network does not yet remove, which dominate the later
+    Krylov vectors."""
+    out = []
+    for r, sq in source_vectors(seed, R, n_src, torch):
+        n_act = sq.layout.n_active
+        for c in cycles:
+            u = sq.zeros(torch.float64)
+            sq.solve(u, solver="ir_fgmres", tol=1e-12, restart=restart, ortho="cgs1", max_iter=c * restart,
+                     max_outer=1, precond=net, raise_on_error=False)
+            r64 = sq.zeros(torch.float64)
+            sq.residual(u, r64)
+            nv = float(torch.linalg.vector_norm(r64))
+            if nv > 0.0 and math.isfinite(nv):
+                out.append((r64 * (math.sqrt(n_act) / nv)).float())
+        sq.close()
+    return out
+
+
+def residual_loss_step(net, sysm, rs, lr: float, torch):
+    """One Adam step on mean_b |A M(r_b) - r_b|^2 / |r_b|^2 (rs: (B, n_elems)
+    unit-RMS vectors of one medium).  Returns the loss before the step (a
+    device tensor)."""
+    B = rs.shape[0]
+    n_act = sysm.layout.n_active
+    X = torch.stack([sysm.cnn_features(rs[b], 1.0) for b in range(B)])
+    out = net.forward(X)
+    grads, loss = [], torch.zeros((), dtype=torch.float64, device=rs.device)
+    Az = sysm.zeros(torch.float32)
+    g = sysm.zeros(torch.float32)
+    for b in range(B):
+        z = sysm.cnn_output(out[b], 1.0, v=rs[b])
+        sysm.apply(z, Az)
+        q = Az - rs[b]
+        loss = loss + torch.sum(q.double() ** 2) / n_act
+        sysm.apply_t(q, g)
+        grads.append(sysm.cnn_targets(g, None, 2.0 / n_act / B))
+    net.backward(torch.stack(grads))
+    net.adam_step(lr)
+    return loss / B
+
+
+def train_residual(net, pools, steps: int, batch: int, lr: float, torch, log=print, seed: int = 0):
+    """Residual-loss training over [(System, vectors)] pools; one medium per step."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    losses = []
+    t0 = time.time()
+    warm = max(1, steps // 20)
+    pending = []
+    for it in range(steps):
+        sysm, vecs = pools[int(rng.integers(len(pools)))]
+        idx = torch.as_tensor(rng.integers(0, vecs.shape[0], size=batch), device=vecs.device)
+        lr_it = lr * min(1.0, (it + 1) / warm) * 0.5 * (1.0 + math.cos(math.pi * it / steps))
+        pending.append(residual_loss_step(net, sysm, vecs[idx], lr_it, torch))
+        if len(pending) >= 50:
+            losses += [float(v) for v in torch.stack(pending).cpu()]
+            pending = []
+        if (it + 1) % max(1, steps // 10) == 0:
+            if pending:
+                losses += [float(v) for v in torch.stack(pending).cpu()]
+                pending = []
+            log(f"  train: step {it + 1}/{steps} residual loss {np.mean(losses[-50:]):.4f} ({time.time() - t0:.1f} s)")
+    if pending:
+        losses += [float(v) for v in torch.stack(pending).cpu()]
+    return losses
+
+
 def train(net, X, Y, steps: int, batch: int, lr: float, torch, log=print, seed: int = 0):
     gen = torch.Generator(device="cpu").manual_seed(seed)
     S = X.shape[0]
@@ -198,6 +334,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--loss", choices=["residual", "supervised"], default="residual")
+    ap.add_argument("--rounds", type=int, default=1,
+                    help="residual loss: after each round, add the residuals FGMRES with the network leaves "
+                         "to the pools and train again")
     ap.add_argument("--eval-r", type=int, default=64)
     ap.add_argument("--eval-media", type=int, default=8)
     args = ap.parse_args(argv)
@@ -208,12 +348,34 @@ def main(argv=None):
     if args.cmd == "train":
         net.set_params(init_params(K + 3, K, seed=1))
         t0 = time.time()
-        X, Y = make_dataset(list(range(1000, 1000 + args.media)), args.train_r, args.sources, args.mix, torch)
+        media = list(range(1000, 1000 + args.media))
+        if args.loss == "residual":
+            pools = []
+            for i, seed in enumerate(media):
+                pools.append(residual_pool(seed, args.train_r, args.sources, torch, n_mix=args.mix))
+                if (i + 1) % 25 == 0:
+                    print(f"  data: {i + 1}/{len(media)} media ({time.time() - t0:.1f} s)", flush=True)
+            report["samples"] = int(sum(p[1].shape[0] for p in pools))
+        else:
+            X, Y = make_dataset(media, args.train_r, args.sources, args.mix, torch)
+            report["samples"] = int(X.shape[0])
         report["data_seconds"] = time.time() - t0
-        report["samples"] = int(X.shape[0])
         t0 = time.time()
-        losses = train(net, X, Y, args.steps, args.batch, args.lr, torch)
+        if args.loss == "residual":
+            losses = train_residual(net, pools, args.steps, args.batch, args.lr, torch)
+            for rnd in range(1, args.rounds):
+                t1 = time.time()
+                for i, seed in enumerate(media):
+                    extra = fgmres_residuals(net, seed, args.train_r, args.sources, torch)
+                    if extra:
+                        sysm, vecs = pools[i]
+                        pools[i] = (sysm, torch.cat([vecs, torch.stack(extra)]))
+                print(f"  round {rnd}: added FGMRES residuals ({time.time() - t1:.1f} s)", flush=True)
+                losses = train_residual(net, pools, args.steps, args.batch, args.lr * 0.5, torch, seed=rnd)
+        else:
+            losses = train(net, X, Y, args.steps, args.batch, args.lr, torch)
         torch.cuda.synchronize()
+        report["loss"] = args.loss
         report["train_seconds"] = time.time() - t0
         report["loss_start"] = float(np.mean(losses[:20]))
         report["loss_end"] = float(np.mean(losses[-50:]))

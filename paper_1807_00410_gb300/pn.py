@@ -40,12 +40,14 @@ ERROR_NAMES = {
 }
 
 # Every symbol the header declares (checked by the CPU test-suite).
-EXPORTS = ["pn_create", "pn_destroy", "pn_get_layout", "pn_last_error", "pn_apply", "pn_apply_t",
+EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_error", "pn_apply", "pn_apply_t",
            "pn_residual", "pn_dot", "pn_axpby", "pn_default_solve_opts", "pn_solve", "pn_profile_get",
            "pn_dot_noalloc", "pn_single_scatter_beam", "pn_unstagger", "pn_cnn_create", "pn_cnn_destroy",
            "pn_cnn_last_error", "pn_cnn_num_params", "pn_cnn_set_params", "pn_cnn_get_params", "pn_cnn_get_grads",
            "pn_cnn_forward", "pn_cnn_backward", "pn_cnn_adam_step", "pn_cnn_train_step", "pn_cnn_features",
-           "pn_cnn_targets", "pn_cnn_precondition"]
+           "pn_cnn_targets", "pn_cnn_output", "pn_cnn_precondition", "pn_batch_create", "pn_batch_destroy",
+           "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
+           "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -94,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     sig = {
         "pn_create": (i, [ctypes.POINTER(vp), i, i, ctypes.POINTER(_Medium), i, vp]),
+        "pn_create_2d": (i, [ctypes.POINTER(vp), i, i, ctypes.POINTER(_Medium), i, vp]),
         "pn_destroy": (i, [vp]),
         "pn_get_layout": (i, [vp, ctypes.POINTER(_Layout)]),
         "pn_last_error": (ctypes.c_char_p, [vp]),
@@ -121,7 +124,19 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_cnn_train_step": (i, [vp, vp, vp, i, i, i, i, d, ctypes.POINTER(d), vp]),
         "pn_cnn_features": (i, [vp, vp, d, vp, vp]),
         "pn_cnn_targets": (i, [vp, vp, vp, d, vp, vp]),
+        "pn_cnn_output": (i, [vp, vp, d, vp, vp, vp]),
         "pn_cnn_precondition": (i, [vp, vp, vp, vp, vp]),
+        "pn_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), i, i, vp]),
+        "pn_batch_destroy": (i, [vp]),
+        "pn_batch_last_error": (ctypes.c_char_p, [vp]),
+        "pn_batch_apply": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
+        "pn_batch_solve": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveStats), vp]),
+        "pn_batch_set_tiling": (i, [vp, i64, i64, i, i]),
+        "pn_batch_get_tiling": (i, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i),
+                                    ctypes.POINTER(i)]),
+        "pn_batch_tune": (i, [vp, vp]),
+        "pn_batch_set_mode": (i, [vp, i, ctypes.c_longlong]),
+        "pn_batch_barrier_test": (i, [i, i, ctypes.c_longlong, ctypes.POINTER(i), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -144,14 +159,26 @@ class Layout:
     n_active: int
     plane_k: list
     plane_class: list
+    dims: int = 3   # 2: the z-independent reduction (one z-slice per plane, l + m even)
 
     def plane_of_k(self, k: int) -> int:
         return self.plane_k.index(k)
 
+    @property
+    def nz_box(self) -> int:
+        """z-slices of a plane box."""
+        return self.R + 1 if self.dims == 3 else 1
+
     def active_shape(self, p: int):
         c = self.plane_class[p]
         R = self.R
-        return (R + ((c >> 2) & 1), R + ((c >> 1) & 1), R + (c & 1))  # (z, y, x)
+        nz = R + ((c >> 2) & 1) if self.dims == 3 else 1
+        return (nz, R + ((c >> 1) & 1), R + (c & 1))  # (z, y, x)
+
+    def coefficient_index(self, p: int) -> int:
+        """Position of plane p's coefficient in the handle's coefficient list
+        (3D: k; 2D: among the l + m even coefficients in increasing k)."""
+        return self.plane_k[p] if self.dims == 3 else sorted(self.plane_k).index(self.plane_k[p])
 
 
 def _torch():
@@ -236,10 +263,16 @@ class System:
     [z][y][x]; Q is either an (R, R, R) field of Q^{0,0} or a (K, R, R, R)
     array of centre moments.  numpy inputs are passed as host arrays (the
     library copies them); torch CUDA tensors are passed as device pointers.
+
+    dims=2 builds the z-independent 2D reduction (pn_create_2d): fields are
+    (R, R) arrays [y][x], K = (N+1)(N+2)/2 coefficients with l + m even, and
+    moment sources are (K, R, R) in increasing k.
     """
 
     def __init__(self, N: int, R: int, sigma_t, albedo, g: float, Q=None, sigma_t_min: float = 0.0,
-                 stream=None):
+                 stream=None, dims: int = 3):
+        if dims not in (2, 3):
+            raise ValueError("dims must be 2 or 3")
         self._lib = load_library()
         self._h = ctypes.c_void_p()
         keep = []
@@ -274,7 +307,8 @@ class System:
             al_p, _, _ = arr(al)
             m.albedo = al_p
         m.g = float(g)
-        K = (N + 1) ** 2
+        K = (N + 1) ** 2 if dims == 3 else (N + 1) * (N + 2) // 2
+        cells = (R,) * dims
         if Q is not None:
             q = Q
             if _is_torch(sigma_t) and not _is_torch(q):
@@ -284,26 +318,29 @@ class System:
             if _is_torch(q):
                 q = q.to(keep[0].dtype)
             shape = tuple(q.shape)
-            if shape == (R, R, R):
+            if shape == cells:
                 m.q_mode = PN_Q_CENTRE_00
-            elif shape == (K, R, R, R):
+            elif shape == (K,) + cells:
                 m.q_mode = PN_Q_CENTRE_MOMENTS
             else:
-                raise ValueError(f"Q must have shape {(R, R, R)} or {(K, R, R, R)}, got {shape}")
+                raise ValueError(f"Q must have shape {cells} or {(K,) + cells}, got {shape}")
             q_p, _, _ = arr(q)
             m.Q = q_p
         m.dtype = st_dt
         m.on_device = st_dev
         m.sigma_t_min = float(sigma_t_min)
-        rc = self._lib.pn_create(ctypes.byref(self._h), int(N), int(R), ctypes.byref(m), PN_BC_VACUUM,
-                                 _stream_ptr(stream) if (st_dev or stream is not None) else ctypes.c_void_p(0))
+        if tuple(np.shape(sigma_t)) != cells:
+            raise ValueError(f"sigma_t must have shape {cells}")
+        create = self._lib.pn_create if dims == 3 else self._lib.pn_create_2d
+        rc = create(ctypes.byref(self._h), int(N), int(R), ctypes.byref(m), PN_BC_VACUUM,
+                    _stream_ptr(stream) if (st_dev or stream is not None) else ctypes.c_void_p(0))
         if rc != PN_OK:
             raise PnError(rc, self._lib.pn_last_error(None).decode())
         lay = _Layout()
         self._check(self._lib.pn_get_layout(self._h, ctypes.byref(lay)))
         self.layout = Layout(lay.N, lay.K, lay.R, lay.pitch_x, lay.pitch_y, lay.plane_stride, lay.n_elems,
-                             lay.n_active, list(lay.plane_k)[:lay.K], list(lay.plane_class)[:lay.K])
-        self.N, self.R, self.K = N, R, K
+                             lay.n_active, list(lay.plane_k)[:lay.K], list(lay.plane_class)[:lay.K], dims)
+        self.N, self.R, self.K, self.dims = N, R, K, dims
 
     # -- plumbing -------------------------------------------------------------
     def _check(self, rc):
@@ -426,13 +463,27 @@ class System:
         return out
 
     def cnn_targets(self, e, r, scale: float, stream=None):
-        """Training target scale * (e - D^{-1} r) at the cells' own slots: (R, R, R, K)."""
+        """scale * (e - P r) at the cells' own slots: (R, R, R, K); r None:
+        scale * e (P = diag(1 / (D + 1/h)), the preconditioner's fixed part)."""
         torch = _torch()
         R, K = self.layout.R, self.layout.K
         out = torch.empty((R, R, R, K), dtype=torch.float32, device=e.device)
-        self._check(self._lib.pn_cnn_targets(self._h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(r.data_ptr()),
-                                             float(scale), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        rp = ctypes.c_void_p(r.data_ptr()) if r is not None else ctypes.c_void_p(0)
+        self._check(self._lib.pn_cnn_targets(self._h, ctypes.c_void_p(e.data_ptr()), rp, float(scale),
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
+
+    def cnn_output(self, net_out, scale: float, v=None, z=None, stream=None):
+        """z = scale * net_out (R, R, R, K) at the cells' own slots + P v (v
+        optional; net_out None: P v alone), a padded FP32 vector."""
+        torch = _torch()
+        if z is None:
+            z = self.zeros(torch.float32)
+        no = ctypes.c_void_p(net_out.data_ptr()) if net_out is not None else ctypes.c_void_p(0)
+        vp_ = ctypes.c_void_p(v.data_ptr()) if v is not None else ctypes.c_void_p(0)
+        self._check(self._lib.pn_cnn_output(self._h, no, float(scale), vp_, ctypes.c_void_p(z.data_ptr()),
+                                            _stream_ptr(stream)))
+        return z
 
     def precondition(self, net, v, stream=None):
         """z = M(v) with the learned network (padded FP32 vectors)."""
@@ -446,37 +497,133 @@ class System:
         torch = _torch()
         xp, dt = self._vec(x)
         R = self.layout.R
-        out = torch.empty((self.layout.K, R, R, R), dtype=x.dtype, device=x.device)
+        out = torch.empty((self.layout.K,) + (R,) * self.dims, dtype=x.dtype, device=x.device)
         self._check(self._lib.pn_unstagger(self._h, xp, ctypes.c_void_p(out.data_ptr()), dt, _stream_ptr(stream)))
         return out
 
     # -- layout marshalling -------------------------------------------------
     def to_planes(self, vec):
-        """Padded vector -> list of K numpy arrays in coefficient order k,
-        each the active (z, y, x) region of its staggered grid."""
+        """Padded vector -> list of K numpy arrays in coefficient order (3D: k;
+        2D: the l + m even coefficients in increasing k), each the active
+        (z, y, x) region of its staggered grid ((y, x) in 2D)."""
         lay = self.layout
         v = vec.detach().cpu().numpy() if _is_torch(vec) else np.asarray(vec)
-        R = lay.R
+        R, nzb = lay.R, lay.nz_box
         out = [None] * lay.K
         for p in range(lay.K):
-            box = v[p * lay.plane_stride: p * lay.plane_stride + lay.pitch_y * (R + 1)]
-            box = box.reshape(R + 1, R + 1, lay.pitch_x)
+            box = v[p * lay.plane_stride: p * lay.plane_stride + lay.pitch_y * nzb]
+            box = box.reshape(nzb, R + 1, lay.pitch_x)
             nz, ny, nx = lay.active_shape(p)
-            out[lay.plane_k[p]] = box[:nz, :ny, :nx].copy()
+            a = box[:nz, :ny, :nx].copy()
+            out[lay.coefficient_index(p)] = a if lay.dims == 3 else a[0]
         return out
 
     def from_planes(self, planes, dtype=None, device="cuda"):
-        """List of K per-coefficient arrays (coefficient order) -> padded vector."""
+        """List of K per-coefficient arrays (order of to_planes) -> padded vector."""
         torch = _torch()
         lay = self.layout
-        R = lay.R
+        R, nzb = lay.R, lay.nz_box
         host = np.zeros(lay.n_elems, dtype=np.float64)
         for p in range(lay.K):
             nz, ny, nx = lay.active_shape(p)
-            box = host[p * lay.plane_stride: p * lay.plane_stride + lay.pitch_y * (R + 1)].reshape(
-                R + 1, R + 1, lay.pitch_x)
-            box[:nz, :ny, :nx] = np.asarray(planes[lay.plane_k[p]], dtype=np.float64).reshape(nz, ny, nx)
+            box = host[p * lay.plane_stride: p * lay.plane_stride + lay.pitch_y * nzb].reshape(nzb, R + 1, lay.pitch_x)
+            box[:nz, :ny, :nx] = np.asarray(planes[lay.coefficient_index(p)], dtype=np.float64).reshape(nz, ny, nx)
         return torch.as_tensor(host, dtype=dtype or torch.float32).to(device)
+
+
+class Batch:
+    """Many systems solved together (pn_batch_*): one launch per phase over
+    every instance, the restart cycle replayed as a CUDA graph.  The systems
+    are borrowed and must stay open while the batch lives."""
+
+    def __init__(self, systems, restart: int = 15, tune: bool = False, stream=None):
+        self._lib = load_library()
+        self.systems = list(systems)
+        self._h = ctypes.c_void_p()
+        n = len(self.systems)
+        hs = (ctypes.c_void_p * n)(*[s_._h.value for s_ in self.systems])
+        rc = self._lib.pn_batch_create(ctypes.byref(self._h), hs, n, int(restart), _stream_ptr(stream))
+        if rc != PN_OK:
+            raise PnError(rc, "pn_batch_create failed")
+        self.restart = int(restart)
+        if tune:
+            self.tune(stream)
+
+    def _check(self, rc):
+        if rc != PN_OK:
+            raise PnError(rc, self._lib.pn_batch_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.pn_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, stream=None) -> dict:
+        self._check(self._lib.pn_batch_tune(self._h, _stream_ptr(stream)))
+        return self.tiling()
+
+    def tiling(self) -> dict:
+        oc, vc = ctypes.c_int64(), ctypes.c_int64()
+        om, vm = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.pn_batch_get_tiling(self._h, ctypes.byref(oc), ctypes.byref(vc), ctypes.byref(om),
+                                                  ctypes.byref(vm)))
+        return {"op_chunk": oc.value, "vec_chunk": vc.value, "op_ctas_per_sm": om.value, "vec_ctas_per_sm": vm.value}
+
+    def set_mode(self, persistent: bool, spin_limit: int = 1 << 24):
+        """persistent=True: one cooperative launch per restart cycle with
+        bounded grid barriers; False: the captured CUDA graph (default)."""
+        self._check(self._lib.pn_batch_set_mode(self._h, 1 if persistent else 0, int(spin_limit)))
+
+    def set_tiling(self, op_chunk: int, vec_chunk: int, op_ctas_per_sm: int, vec_ctas_per_sm: int):
+        self._check(self._lib.pn_batch_set_tiling(self._h, int(op_chunk), int(vec_chunk), int(op_ctas_per_sm),
+                                                  int(vec_ctas_per_sm)))
+
+    def apply(self, xs, ys, stream=None):
+        """y_i = A_i x_i for every instance, one launch (FP32 or FP64)."""
+        n = len(self.systems)
+        dt = _dtype_code(xs[0])
+        xa = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        self._check(self._lib.pn_batch_apply(self._h, xa, ya, dt, _stream_ptr(stream)))
+
+    def solve(self, us, tol: float = 1e-6, max_iter: int = 100000, inner_tol: float = 1e-2, max_outer: int = 50,
+              stream=None, raise_on_error: bool = True):
+        """Solve every A_i u_i = Q_i in place (FP64 u_i, initial guesses).
+        Returns one stats dict per instance."""
+        torch = _torch()
+        n = len(self.systems)
+        for u in us:
+            if u.dtype != torch.float64 or not u.is_cuda:
+                raise TypeError("batched refinement keeps every u in FP64 on the GPU")
+        o = _SolveOpts()
+        self._lib.pn_default_solve_opts(ctypes.byref(o))
+        o.solver = SOLVERS["ir"]
+        o.precision = PN_F64
+        o.tol, o.max_iter, o.restart = float(tol), int(max_iter), self.restart
+        o.inner_tol, o.max_outer = float(inner_tol), int(max_outer)
+        st = (_SolveStats * n)()
+        ua = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+        rc = self._lib.pn_batch_solve(self._h, ua, ctypes.byref(o), st, _stream_ptr(stream))
+        out = [{"status": st[i].status, "iterations": st[i].iterations, "outer_iterations": st[i].outer_iterations,
+                "rel_residual": st[i].rel_residual, "seconds": st[i].seconds, "launches": st[i].launches}
+               for i in range(n)]
+        if rc != PN_OK and raise_on_error:
+            raise PnError(rc, self._lib.pn_batch_last_error(self._h).decode() + f" (stats {out})")
+        return out
+
+
+def barrier_test(blocks: int, expected: int, spin_limit: int, stream=None):
+    """(return code, timed_out) of pn_batch_barrier_test."""
+    lib = load_library()
+    t = ctypes.c_int(-1)
+    rc = lib.pn_batch_barrier_test(int(blocks), int(expected), int(spin_limit), ctypes.byref(t), _stream_ptr(stream))
+    return rc, t.value
 
 
 class Net:

@@ -170,3 +170,44 @@ def checkerboard_2d(R: int = 71, blocks: int = 7, sigma_a: float = 10.0, sigma_s
     mid = blocks // 2
     Q00 = np.where((by == mid) & (bx == mid), source, 0.0) * float(blocks)
     return sigma_t, albedo, Q00
+
+
+@dataclass
+class BatchInstance:
+    """One instance of a batched workload: order, grid, centre fields and a
+    source given either as a point (Q^{0,0} at `voxel`) or as a collimated
+    beam (axis, sign, radius, centre), to be turned into moments by the
+    single-scatter source builder."""
+    N: int
+    R: int
+    sigma_t: np.ndarray
+    albedo: float
+    g: float
+    source: tuple
+
+
+def batch_instances(count: int = 64, base_seed: int = 0, r_lo: int = 24, r_hi: int = 96, orders=(1, 3, 5),
+                    sig_lo: float = 0.1, sig_hi: float = 60.0):
+    """The many-instance workload: instance i (seed base_seed + i) draws its
+    grid R uniformly in [r_lo, r_hi], its order from `orders`, an fBm
+    extinction field mapped onto [sig_lo, sig_hi], albedo ~ U[0.7, 0.99],
+    g ~ U[0, 0.7], and a point source (a seeded voxel in the middle half) or a
+    collimated beam of radius 0.1 along a seeded axis and direction, with
+    equal probability."""
+    out = []
+    for i in range(count):
+        seed = base_seed + i
+        rng = np.random.Generator(np.random.PCG64(seed + 7919))
+        R = int(rng.integers(r_lo, r_hi + 1))
+        N = int(orders[int(rng.integers(len(orders)))])
+        albedo = float(rng.uniform(0.7, 0.99))
+        g = float(rng.uniform(0.0, 0.7))
+        st = sig_lo + (sig_hi - sig_lo) * value_noise_fbm(R, seed)
+        if rng.uniform() < 0.5:
+            v = tuple(int(t) for t in rng.integers(R // 4, R - R // 4, size=3))
+            src = ("point", v)
+        else:
+            src = ("beam", int(rng.integers(3)), int(rng.choice([-1, 1])), 0.1,
+                   (float(rng.uniform(0.3, 0.7)), float(rng.uniform(0.3, 0.7))))
+        out.append(BatchInstance(N, R, st, albedo, g, src))
+    return out

@@ -145,7 +145,9 @@ def test_features_layout():
     gpu.close()
 
 
-def test_zero_network_preconditioner_is_jacobi():
+def test_zero_network_preconditioner_is_the_fixed_diagonal():
+    """With a zero network M(v) = P v, P = diag(1 / (D + 1/h)), D the
+    oracle's collision-minus-scattering diagonal."""
     from oracle import pn as opn
     from paper_1807_00410_gb300 import Net
     p, med, gpu = _p3_system(16, 3)
@@ -160,8 +162,32 @@ def test_zero_network_preconditioner_is_jacobi():
     D = lay_o.split(opn.diagonal(lay_o, med))
     got = gpu.to_planes(z)
     for k in range(K):
-        np.testing.assert_allclose(got[k], np.asarray(planes[k], np.float32) / D[k], rtol=2e-5, atol=1e-7)
+        np.testing.assert_allclose(got[k], np.asarray(planes[k], np.float32) / (D[k] + 16.0), rtol=2e-5, atol=1e-7)
     net.close()
+    gpu.close()
+
+
+def test_output_scatter_and_gather_are_adjoint():
+    """pn_cnn_output (network layout -> padded vector) and pn_cnn_targets with
+    r = NULL (padded vector -> network layout) are transposes of each other,
+    which the residual-loss gradient relies on; the scatter leaves the face
+    slots x, y or z = R and the padding at zero."""
+    _, _, gpu = _p3_system(16, 7)
+    lay = gpu.layout
+    R, K = lay.R, lay.K
+    g = torch.Generator(device="cpu").manual_seed(5)
+    a = torch.randn((R, R, R, K), generator=g).cuda()
+    w = torch.randn(lay.n_elems, generator=g).cuda()
+    z = gpu.cnn_output(a, 0.75)
+    lhs = float(torch.dot(z.double(), w.double()))
+    rhs = 0.75 * float(torch.dot(a.double().ravel(), gpu.cnn_targets(w, None, 1.0).double().ravel()))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+    planes = gpu.to_planes(z)
+    an = a.cpu().numpy()
+    for k in range(K):
+        q = lay.plane_of_k(k)
+        np.testing.assert_allclose(planes[k][:R, :R, :R], 0.75 * an[..., q], rtol=1e-6)
+        assert not np.any(planes[k][R:]) and not np.any(planes[k][:, R:]) and not np.any(planes[k][:, :, R:])
     gpu.close()
 
 
