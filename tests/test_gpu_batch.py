@@ -146,3 +146,44 @@ def test_autotuner_keeps_a_valid_tiling_and_solves():
     batch.close()
     for s in systems:
         s.close()
+
+
+def test_persistent_mode_equals_graph_mode():
+    """One cooperative launch per cycle (phases separated by bounded grid
+    barriers) computes exactly what the captured graph computes: the same
+    work items, partials and reduction order."""
+    from paper_1807_00410_gb300 import Batch
+    cases = [(1, 12, 3, 41), (3, 14, 3, 42), (5, 8, 3, 43), (3, 16, 2, 44)]
+    systems, descs = zip(*[_instance(*c) for c in cases])
+    batch = Batch(systems, restart=10)
+    ug = [s.zeros(torch.float64) for s in systems]
+    sg = batch.solve(ug, tol=1e-6)
+    batch.set_mode(True)
+    up = [s.zeros(torch.float64) for s in systems]
+    sp = batch.solve(up, tol=1e-6)
+    assert [a["iterations"] for a in sg] == [a["iterations"] for a in sp]
+    assert all(torch.equal(a, b) for a, b in zip(ug, up))
+    assert sp[0]["launches"] < sg[0]["launches"]
+    for s, d, u in zip(systems, descs, up):
+        lay, A, b = _oracle(d)
+        uh = lay.join(s.to_planes(u))
+        assert np.linalg.norm(b - A @ uh) / np.linalg.norm(b) <= 1.0001e-6
+    batch.close()
+    for s in systems:
+        s.close()
+
+
+def test_grid_barrier_completes_and_its_bounded_wait_runs_out():
+    """A barrier that every CTA reaches completes; one that expects a CTA
+    which does not exist gives up after its poll limit (a few ms here),
+    reports PN_ERR_TIMEOUT, and the context stays usable."""
+    from paper_1807_00410_gb300.pn import barrier_test
+    assert barrier_test(16, 16, 1 << 22) == (0, 0)
+    assert barrier_test(16, 17, 20000) == (-7, 1)
+    s, d = _instance(3, 10, 3, 51)
+    x = s.zeros(torch.float32) + 1.0
+    y = s.zeros(torch.float32)
+    s.apply(x, y)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(y).all())
+    s.close()
