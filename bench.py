@@ -40,7 +40,12 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic per launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel class and
 # workload; None until a capture of the current kernel exists.
-NCU_TRAFFIC = {}
+# DRAM traffic of the dominant kernel from one ncu capture of the current
+# kernel (profiles/k_mdot_givens_f32_p5_64_ir_solve.md): dram bytes read +
+# written over the algorithmic bytes of the same launch.  Launches differ in
+# the number of basis vectors, so the ratio is applied to this run's average
+# algorithmic bytes per launch.  Set to {} when the kernel changes.
+NCU_TRAFFIC = {("mdot", "p5_64"): 1.083}
 
 
 def parse():
@@ -323,9 +328,10 @@ def run_ours(args):
     d = kinds[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
     kernel_names = {"apply": "k_apply_tiled<5,4,OP_APPLY> + k_op_slab", "residual": "k_apply_tiled<*,OP_RESIDUAL>",
-                    "mdot": "k_mdot_f32<16>", "maxpy": "k_maxpy_f32<16>", "dot": "k_dot_f32",
+                    "mdot": "k_mdot_givens_f32 (fused CGS1 step)", "maxpy": "k_maxpy_f32<16>", "dot": "k_dot_f32",
                     "vector": "vector updates"}
-    traffic = NCU_TRAFFIC.get((dom, "p5_64"))
+    ratio = NCU_TRAFFIC.get((dom, "p5_64"))
+    traffic = ratio * d["bytes"] / d["launches"] if ratio else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "kernel": kernel_names.get(dom, dom),
                 "kind": dom, "launches_per_step": d["launches"] / args.steps,

@@ -343,7 +343,9 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
     // scratch
     h->red_blocks = pn::reduce_blocks();
     PN_TRY(dev_alloc(nullptr, &h->d_partials,
-                     size_t(std::max(h->red_blocks * (PN_MAX_MDOT + 1), std::max(pn::op_partial_count(h, PN_F32), pn::op_partial_count(h, PN_F64)))), "partials"));
+                     size_t(std::max(std::max(h->red_blocks, 4 * pn_sm_count()) * (PN_MAX_MDOT + 1),
+                                             std::max(pn::op_partial_count(h, PN_F32), pn::op_partial_count(h, PN_F64)))),
+                     "partials"));
     PN_TRY(dev_alloc(nullptr, &h->d_scalars, size_t(PN_NSCALARS), "scalars"));
     if (cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
         h->h_pinned = nullptr;

@@ -21,9 +21,10 @@ namespace {
 
 // scalar slots in h->d_scalars
 enum { S_RR = 0, S_QQ = 1, S_G0 = 2, S_G1 = 3, S_BETA2 = 4, S_RES = 5, S_SCALE = 6, S_NRM2 = 7, S_MAXPY = 64,
-       S_PNRM = 65 };
+       S_PNRM = 65, S_TICKET = 66 };
 
 int nb_vec() { return 4 * pn_sm_count(); }
+int nb_mdot() { return 4 * pn_sm_count(); }  // the fused CGS1 step (partials: nb_mdot * (PN_MAX_MDOT + 1))
 
 __device__ __forceinline__ double warp_block_sum(double v) {
     __shared__ double red[32];
@@ -255,17 +256,16 @@ void launch_maxpy<double>(int nb, cudaStream_t s, int64_t n, double* w, const do
 //   S[S_NRM2] = ||w||^2 after orthogonalisation.
 // Applies the previous rotations, forms rotation j, updates g and writes
 // |g[j+1]| to S[S_RES] and 1/||w|| to S[S_SCALE].
-__global__ void k_givens(double* H, int ldh, const double* add, double* cs, double* sn, double* g, int j,
-                         double* S, int pythagoras) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void givens_core(double* H, int ldh, const double* add, double* cs, double* sn,
+                                            double* g, int j, double* S, int pythagoras, double nrm2_in) {
     double* col = H + int64_t(j) * ldh;
-    double nrm2 = S[S_NRM2];
+    double nrm2 = nrm2_in;
     if (pythagoras) {
         // single Gram-Schmidt pass: ||w - V h||^2 = ||w||^2 - ||h||^2 for orthonormal V
         double hh = 0.0;
         for (int i = 0; i <= j; ++i) hh += col[i] * col[i];
         nrm2 = nrm2 - hh;
-        if (!(nrm2 > 1e-14 * S[S_NRM2])) nrm2 = 1e-14 * S[S_NRM2];
+        if (!(nrm2 > 1e-14 * nrm2_in)) nrm2 = 1e-14 * nrm2_in;
     } else {
         for (int i = 0; i <= j; ++i) col[i] += add[i];
     }
@@ -288,6 +288,87 @@ __global__ void k_givens(double* H, int ldh, const double* add, double* cs, doub
     g[j + 1] = -s * g[j];
     g[j] = c * g[j];
     S[S_RES] = fabs(g[j + 1]);
+}
+
+__global__ void k_givens(double* H, int ldh, const double* add, double* cs, double* sn, double* g, int j,
+                         double* S, int pythagoras) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    givens_core(H, ldh, add, cs, sn, g, j, S, pythagoras, S[S_NRM2]);
+}
+
+// One fused CGS1 step for j + 1 <= PN_MAX_MDOT basis vectors (FP32):
+//  * every block: V_i . w (i <= j) and w . w over its grid-stride share, each
+//    thread summing its products in FP32, each warp's 32 sums added in FP32,
+//    the block's 8 warp sums added in FP64, one FP64 partial per block;
+//  * the last block to finish (ticket counter) adds the partials in block
+//    order (deterministic), writes the projections to `add` and the
+//    Hessenberg column, and runs the Givens update with |w - V h|^2 =
+//    |w|^2 - |h|^2 (what k_reduce + k_cgs1_gather + k_givens do in three
+//    launches), then resets the ticket.
+__global__ void __launch_bounds__(256) k_mdot_givens_f32(int64_t n4, const float4* V, int64_t vstride4, int nv,
+                                                         const float4* w, double* partials, unsigned int* ticket,
+                                                         double* H, int ldh, double* add, double* cs, double* sn,
+                                                         double* g, int j, double* S) {
+    constexpr int NV = PN_MAX_MDOT;
+    float part[NV + 1];
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 wi = w[i];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nv) {
+                const float4 q = V[v * vstride4 + i];
+                part[v] = fmaf(q.w, wi.w, fmaf(q.z, wi.z, fmaf(q.y, wi.y, fmaf(q.x, wi.x, part[v]))));
+            }
+        }
+        part[NV] = fmaf(wi.w, wi.w, fmaf(wi.z, wi.z, fmaf(wi.y, wi.y, fmaf(wi.x, wi.x, part[NV]))));
+    }
+    __shared__ double red[NV + 1][8];
+    __shared__ double tot[NV + 1];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) {
+        if (v < nv || v == NV) {
+            float t = part[v];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) red[v][warp] = double(t);
+        }
+    }
+    __syncthreads();
+    const int nb = gridDim.x;
+    if (threadIdx.x <= NV && (int(threadIdx.x) < nv || threadIdx.x == NV)) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[threadIdx.x][q];
+        partials[int64_t(threadIdx.x) * nb + blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == unsigned(nb - 1)) ? 1 : 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int v = warp; v <= NV; v += 8) {
+        if (v < nv || v == NV) {
+            double t = 0.0;
+            for (int b = lane; b < nb; b += 32) t += __ldcg(partials + int64_t(v) * nb + b);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) tot[v] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* col = H + int64_t(j) * ldh;
+        for (int i = 0; i <= j; ++i) {
+            add[i] = tot[i];
+            col[i] = tot[i];
+        }
+        S[S_NRM2] = tot[NV];
+        givens_core(H, ldh, add, cs, sn, g, j, S, 1, tot[NV]);
+        *ticket = 0u;
+    }
 }
 
 // CGS1 bookkeeping: the first chunk's reduction wrote nv0 projections and
@@ -524,6 +605,8 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
     double* g = sn + (m + 1);
     double* y = g + (m + 1);
     double* add = y + (m + 1);
+    // the fused CGS1 kernel's ticket counter starts at zero
+    c.ok(cudaMemsetAsync(S + S_TICKET, 0, sizeof(double), c.s), "gmres: ticket");
     const double bnorm = std::sqrt(bnorm2);
     const double target = tol * (bnorm > 0.0 ? bnorm : 1.0);
     int total = 0;
@@ -575,7 +658,21 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
             c.pb();
             c.lk(pn::launch_op(h, pn::OP_APPLY, av, w, dt, nullptr, c.s), "gmres: A v");
             c.pe(PN_PROF_APPLY, c.ob(pn::OP_APPLY, es, false));
-            if (ortho == PN_ORTHO_CGS1) {
+            if (ortho == PN_ORTHO_CGS1 && sizeof(T) == 4 && j + 1 <= PN_MAX_MDOT) {
+                // classical Gram-Schmidt once, one fused launch for the
+                // projections, |w|^2, their reduction and the Givens update;
+                // the new vector is normalised by the maxpy below
+                c.pb();
+                k_mdot_givens_f32<<<nb_mdot(), 256, 0, c.s>>>(
+                    n / 4, (const float4*)V, n / 4, j + 1, (const float4*)w, h->d_partials,
+                    reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add, cs, sn, g, j, S);
+                c.launched("gmres: mdot");
+                c.pe(PN_PROF_MDOT, c.vb(j + 2, es));
+                c.pb();
+                launch_maxpy<T>(nb, c.s, n, w, V, n, j + 1, add, -1.0, S + S_SCALE);
+                c.launched("gmres: maxpy");
+                c.pe(PN_PROF_MAXPY, c.vb(j + 3, es));
+            } else if (ortho == PN_ORTHO_CGS1) {
                 // classical Gram-Schmidt once: all projections and ||w||^2 in one
                 // pass over the basis; the new vector is normalised by the last
                 // update.  The projections stay unrotated in `add` (the Givens
