@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 512 << 20
 # written over the algorithmic bytes of the same launch.  Launches differ in
 # the number of basis vectors, so the ratio is applied to this run's average
 # algorithmic bytes per launch.  Set to {} when the kernel changes.
-NCU_TRAFFIC = {("mdot", "p5_64"): 1.083}
+NCU_TRAFFIC = {("mdot", "p5_64", "f32"): 1.083}
 
 
 def parse():
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=15)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
     ap.add_argument("--ortho", choices=["cgs2", "cgs1"], default="cgs1")
+    ap.add_argument("--basis", choices=["f32", "f16"], default="f16",
+                    help="element type of the stored Krylov basis of the inner FP32 GMRES (the other one is "
+                         "timed too and reported under alt_basis)")
     ap.add_argument("--no-apply-scan", action="store_true", help="skip the separate operator throughput scan")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU oracle timing")
@@ -248,6 +251,7 @@ def apply_scan(torch, System, pn_inputs, hbm_peak):
         p = maker()
         sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
         lay = sysm.layout
+        tiling = sysm.tune_apply()
         x = torch.rand(lay.n_elems, dtype=torch.float32, device="cuda")
         ys = [torch.empty_like(x) for _ in range(2)]
         for i in range(3):
@@ -265,7 +269,8 @@ def apply_scan(torch, System, pn_inputs, hbm_peak):
         bytes_alg = (2 * lay.n_active + 2 * V) * 4
         gbs = bytes_alg / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs,
-                     "frac_of_hbm": gbs / hbm_peak, "dof": lay.n_active, "bytes_per_apply": bytes_alg}
+                     "frac_of_hbm": gbs / hbm_peak, "dof": lay.n_active, "bytes_per_apply": bytes_alg,
+                     "ctas_per_sm": tiling["ctas_per_sm"]}
         sysm.close()
         del x, ys
         torch.cuda.empty_cache()
@@ -285,10 +290,11 @@ def run_ours(args):
     p = pn_inputs.p5_64_fbm(rank)
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
     lay = sysm.layout
+    tiling = sysm.tune_apply()  # the operator's z-chunking, picked by timing (setup, untimed)
     u = sysm.zeros(torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     opts = dict(solver="ir", tol=1e-6, restart=args.restart, inner_tol=args.inner_tol, max_iter=30000,
-                check_every=5, ortho=args.ortho)
+                check_every=5, ortho=args.ortho, basis=args.basis)
     for _ in range(args.warmup):
         u.zero_()
         sysm.solve(u, **opts)
@@ -299,21 +305,40 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     t_wall0 = time.perf_counter()
-    step_ms, stats, prof = [], [], {}
+    step_ms, stats, prof, prof_ms = [], [], {}, []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed solves (the value); then the same solves again with the
+    # library's per-launch CUDA events on (the kernel breakdown and roofline),
+    # so that the events' own cost stays out of the value
+    for profiled in (False, True):
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 between timed solves
+            u.zero_()
+            e0.record()
+            st = sysm.solve(u, profile=profiled, **opts)
+            e1.record()
+            e1.synchronize()
+            if not profiled:
+                step_ms.append(e0.elapsed_time(e1))
+                stats.append(st)
+                continue
+            prof_ms.append(e0.elapsed_time(e1))
+            for kind, v in sysm.profile().items():
+                agg = prof.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0})
+                for key in agg:
+                    agg[key] += v[key]
+    # the same solves with the other basis element type, for comparison
+    alt = "f32" if args.basis == "f16" else "f16"
+    alt_opts = dict(opts, basis=alt)
+    alt_ms, alt_st = [], None
     for k in range(args.steps):
-        flush.fill_(float(k))  # evict L2 between timed solves
+        flush.fill_(float(k))
         u.zero_()
         e0.record()
-        st = sysm.solve(u, profile=True, **opts)
+        alt_st = sysm.solve(u, **alt_opts)
         e1.record()
         e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        stats.append(st)
-        for kind, v in sysm.profile().items():
-            agg = prof.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0})
-            for key in agg:
-                agg[key] += v[key]
+        alt_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - t_wall0
@@ -327,17 +352,20 @@ def run_ours(args):
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     d = kinds[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-    kernel_names = {"apply": "k_apply_tiled<5,4,OP_APPLY> + k_op_slab", "residual": "k_apply_tiled<*,OP_RESIDUAL>",
-                    "mdot": "k_mdot_givens_f32 (fused CGS1 step)", "maxpy": "k_maxpy_f32<16>", "dot": "k_dot_f32",
-                    "vector": "vector updates"}
-    ratio = NCU_TRAFFIC.get((dom, "p5_64"))
+    f16 = args.basis == "f16"
+    kernel_names = {"apply": "k_apply_tiled<5,4,OP_APPLY> + k_face_x", "residual": "k_apply_tiled<*,OP_RESIDUAL>",
+                    "mdot": "k_mdot16_givens (fused CGS1 step, FP16 basis)" if f16 else
+                    "k_mdot_givens_f32 (fused CGS1 step)",
+                    "maxpy": "k_maxpy16 (FP16 basis) + k_update16" if f16 else "k_maxpy_f32<16>",
+                    "dot": "k_dot_f32", "vector": "vector updates"}
+    ratio = NCU_TRAFFIC.get((dom, "p5_64", args.basis))
     traffic = ratio * d["bytes"] / d["launches"] if ratio else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "kernel": kernel_names.get(dom, dom),
                 "kind": dom, "launches_per_step": d["launches"] / args.steps,
                 "avg_launch_us": d["ms"] * 1e3 / d["launches"],
                 "bytes_per_launch": d["bytes"] / d["launches"], "peak_source": f"{peak_src} hbm_gbs",
-                "share_of_step": d["ms"] / sum(step_ms)}
+                "share_of_step": d["ms"] / sum(prof_ms), "profiled_ms_per_step": sum(prof_ms) / len(prof_ms)}
     breakdown = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                      "gb_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
                  for k, v in prof.items()}
@@ -385,14 +413,18 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "solve/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f16-basis+f32+f64" if args.basis == "f16" else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart, "ortho": args.ortho,
+                       "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"],
                        "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
                        "replicas": "one independent problem per GPU (seed = rank)"},
             "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
                       "rel_residual": stats[-1]["rel_residual"], "wall_s": wall},
             "roofline": roofline,
             "breakdown": breakdown,
+            "alt_basis": {"basis": alt, "ms_per_step": sum(alt_ms) / len(alt_ms),
+                          "iterations": alt_st["iterations"], "rel_residual": alt_st["rel_residual"]},
             "apply": scan,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -417,6 +449,7 @@ def run_apply_only(args):
     p = pn_inputs.cloud_point(args.apply_n, args.apply_r, 0)
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
     lay = sysm.layout
+    tiling = sysm.tune_apply()
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand(lay.n_elems, dtype=torch.float32, device="cuda", generator=g)
     ys = [torch.empty_like(x) for _ in range(2)]
@@ -436,7 +469,8 @@ def run_apply_only(args):
     print(json.dumps({"mode": "apply-only", "workload": f"P{p.N} {p.R}^3 cloud FP32 apply", "ms": ms,
                       "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac": gbs / hbm_peak,
                       "peak": hbm_peak, "peak_source": peak_src, "dof": lay.n_active,
-                      "bytes_per_apply": bytes_alg, "steps": args.steps, "warmup": args.warmup}), flush=True)
+                      "bytes_per_apply": bytes_alg, "ctas_per_sm": tiling["ctas_per_sm"], "steps": args.steps,
+                      "warmup": args.warmup}), flush=True)
     sysm.close()
 
 

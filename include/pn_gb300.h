@@ -202,10 +202,19 @@ typedef struct {
                             the new vector by Pythagoras, half the traffic) */
     void* precond;       /* PN_SOLVER_IR_FGMRES: the pn_cnn network (c_in = K + 3,
                             c_out = K) of pn_cnn_precondition; R a multiple of 8 */
+    int basis;           /* PN_SOLVER_IR_GMRES: element type of the stored Krylov basis,
+                            PN_BASIS_F32 (default) or PN_BASIS_F16 (FP16 values of
+                            sqrt(n) v, FP32 arithmetic, one Gram-Schmidt pass,
+                            restart <= 16): about 40 % fewer bytes per Arnoldi
+                            step; the stored basis rounds at ~5e-4 relative, so
+                            inner_tol should stay >= 1e-3 */
 } pn_solve_opts;
 
 #define PN_ORTHO_CGS2 0
 #define PN_ORTHO_CGS1 1
+
+#define PN_BASIS_F32 0
+#define PN_BASIS_F16 1
 
 typedef struct {
     int status;          /* return code of the solve */
@@ -219,7 +228,8 @@ typedef struct {
 } pn_solve_stats;
 
 /* Fill *opts with defaults (CGLS, FP64, tol 1e-6, max_iter 100000, m 60,
- * inner_tol 1e-2, max_outer 50, check_every 10, profile 0, ortho CGS2). */
+ * inner_tol 1e-2, max_outer 50, check_every 10, profile 0, ortho CGS2,
+ * precond NULL, basis PN_BASIS_F32). */
 void pn_default_solve_opts(pn_solve_opts* opts);
 
 /*
@@ -379,9 +389,10 @@ int pn_cnn_precondition(pn_handle* h, pn_cnn* net, const float* v, float* z, voi
  * of 256), vector chunk (elements, multiple of 1024) and CTAs per SM of the
  * two kinds of persistent grid.
  * pn_batch_tune: the autotuner: times the batched operator over operator
- * chunk {4096, 16384, 65536} x {2, 4, 8} CTAs per SM, and the Arnoldi vector
- * kernels over vector chunk {16384, 65536, 262144} x {2, 4, 8}, on this
- * batch, and keeps the fastest of each (read them with pn_batch_get_tiling).
+ * chunk {4096, 16384, 65536} x {2, 4, 8} CTAs per SM, the per-instance tiled
+ * operator path against the best of those, and the Arnoldi vector kernels
+ * over vector chunk {16384, 65536, 262144} x {2, 4, 8}, on this batch, and
+ * keeps the fastest of each (pn_batch_get_tiling, pn_batch_get_op_path).
  * pn_batch_set_mode: PN_BATCH_GRAPH (default) replays the captured cycle;
  * PN_BATCH_PERSISTENT runs each cycle as ONE cooperative launch (a grid of
  * resident CTAs, two per SM) whose phases are separated by grid barriers.
@@ -410,6 +421,27 @@ int pn_batch_get_tiling(const pn_batch* batch, int64_t* op_chunk, int64_t* vec_c
 int pn_batch_tune(pn_batch* batch, void* stream);
 int pn_batch_set_mode(pn_batch* batch, int mode, long long spin_limit);
 int pn_batch_barrier_test(int blocks, int expected, long long spin_limit, int* timed_out, void* stream);
+/* Arnoldi-step operator of the graph mode: 1 = every 3D instance the tiled
+ * FP32 kernel serves gets its own gated launch on one of eight side streams
+ * (independent branches of the captured graph, run concurrently; the rest
+ * share one generic launch), 0 = one generic launch over all instances.
+ * Default 1; pn_batch_tune keeps the faster.  The persistent mode always uses
+ * the generic launch (a cooperative kernel cannot launch others). */
+int pn_batch_set_op_path(pn_batch* batch, int tiled);
+int pn_batch_get_op_path(const pn_batch* batch, int* tiled);
+
+/*
+ * Tile plan of the FP32 operator (3D handles): the z-marching tiled kernel
+ * splits each (x, y) tile column into z chunks so that about ctas_per_sm CTAs
+ * per SM are launched (default 4; larger values shorten the chunks).
+ * pn_tune_apply times the FP32 apply for ctas_per_sm in {1, 2, 4, 8} on this
+ * handle (allocates two scratch vectors; synchronises `stream`), keeps the
+ * fastest and reports it and its time (either output may be NULL);
+ * pn_set_apply_tiling sets it directly (1..16).  Results do not depend on the
+ * plan except for the order of the residual's FP64 partial sums.
+ */
+int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms);
+int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm);
 
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */

@@ -183,6 +183,7 @@ void pn_default_solve_opts(pn_solve_opts* o) {
     o->profile = 0;
     o->ortho = PN_ORTHO_CGS2;
     o->precond = nullptr;
+    o->basis = PN_BASIS_F32;
 }
 
 }  // extern "C"
@@ -343,8 +344,10 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
     // scratch
     h->red_blocks = pn::reduce_blocks();
     PN_TRY(dev_alloc(nullptr, &h->d_partials,
-                     size_t(std::max(std::max(h->red_blocks, 4 * pn_sm_count()) * (PN_MAX_MDOT + 1),
-                                             std::max(pn::op_partial_count(h, PN_F32), pn::op_partial_count(h, PN_F64)))),
+                     size_t(std::max(std::max(h->red_blocks, 8 * pn_sm_count()) * (PN_MAX_MDOT + 1),
+                                             std::max(h->dims == 3 ? pn::tiled_partial_bound(h) : 0,
+                                                      std::max(pn::op_partial_count(h, PN_F32),
+                                                               pn::op_partial_count(h, PN_F64))))),
                      "partials"));
     PN_TRY(dev_alloc(nullptr, &h->d_scalars, size_t(PN_NSCALARS), "scalars"));
     if (cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
@@ -504,6 +507,60 @@ int pn_dot(pn_handle* h, const void* x, const void* y, double* out, int dtype, v
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_dot");
     *out = h->h_pinned[0];
+    return PN_OK;
+}
+
+int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm) {
+    if (!h) return PN_ERR_ARG;
+    if (ctas_per_sm < 1 || ctas_per_sm > 16) return pn_fail(h, PN_ERR_ARG, "pn_set_apply_tiling: ctas_per_sm in [1, 16]");
+    h->tile_ctas_per_sm = ctas_per_sm;
+    return PN_OK;
+}
+
+int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms) {
+    if (!h) return PN_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* x = nullptr;
+    float* y = nullptr;
+    if (cudaMalloc(&x, size_t(h->n_elems) * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&y, size_t(h->n_elems) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        if (x) cudaFree(x);
+        return pn_fail(h, PN_ERR_ALLOC, "pn_tune_apply: vectors");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(x, 0, size_t(h->n_elems) * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int cands[] = {1, 2, 4, 8};
+    int best = h->tile_ctas_per_sm;
+    float best_t = 1e30f;
+    for (int c : cands) {
+        if (e != cudaSuccess) break;
+        h->tile_ctas_per_sm = c;
+        float tsum = 0.0f;
+        for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = pn::launch_op(h, pn::OP_APPLY, x, y, PN_F32, nullptr, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep >= 2) tsum += ms;  // two warm-ups
+        }
+        if (e == cudaSuccess && tsum / 5.0f < best_t) {
+            best_t = tsum / 5.0f;
+            best = c;
+        }
+    }
+    h->tile_ctas_per_sm = best;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    if (e != cudaSuccess) return pn_cuda_fail(h, e, "pn_tune_apply");
+    if (ctas_per_sm) *ctas_per_sm = best;
+    if (best_ms) *best_ms = best_t;
     return PN_OK;
 }
 

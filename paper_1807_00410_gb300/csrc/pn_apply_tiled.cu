@@ -119,6 +119,7 @@ struct Args {
     float fl[8];         // g^l
     unsigned char pcls[64];  // parity class of plane p
     double* partials;    // residual: per-CTA FP64 sums of r^2
+    const int* live;     // null, or a device flag: the launch does nothing while it is 0
 };
 
 // Load n values of one class at slot z of this thread's column; inactive
@@ -368,6 +369,7 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
 
 template <int N, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
+    if (a.live && !*a.live) return;  // uniform over the grid
     extern __shared__ float smem[];
     const int tx = threadIdx.x, ty = threadIdx.y, grp = threadIdx.z;
     const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
@@ -482,6 +484,7 @@ __device__ __forceinline__ void face_zero(const Args& a, size_t rowoff) {
 // clears the plane tails.
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
+    if (a.live && !*a.live) return;  // uniform over the grid
     constexpr Tab T = TabN<N>::value;
     constexpr int K = T.K;
     const int R = a.R;
@@ -559,8 +562,10 @@ TiledPlan plan_for(const pn_handle* h) {
     const int nxt = (R + tiled::TX - 1) / tiled::TX;
     const int nyt = (R + 1 + TY - 1) / TY;
     const int sms = pn_sm_count();
-    // z chunks: enough CTAs for about 4 per SM, chunks of at least 4 slices
-    int nzc = std::max(1, (4 * sms + nxt * nyt - 1) / (nxt * nyt));
+    // z chunks: enough CTAs for about tile_ctas_per_sm per SM, chunks of at
+    // least 4 slices
+    const int target = std::max(1, h->tile_ctas_per_sm) * sms;
+    int nzc = std::max(1, (target + nxt * nyt - 1) / (nxt * nyt));
     nzc = std::min(nzc, std::max(1, (R + 1) / 4));
     const int zc = (R + 1 + nzc - 1) / nzc;
     nzc = (R + 1 + zc - 1) / zc;
@@ -621,10 +626,22 @@ int tiled_partial_count(const pn_handle* h) {
     return int(p.grid.x * p.grid.y * p.grid.z) + face_blocks(h);
 }
 
+int tiled_partial_bound(const pn_handle* h) {
+    const int nxt = (h->R + tiled::TX - 1) / tiled::TX;
+    const int nyt = (h->R + 1 + kTY - 1) / kTY;
+    const int nzc_max = std::max(1, (h->R + 1) / 4);
+    return nxt * nyt * nzc_max + face_blocks(h);
+}
+
 int tiled_x_end(const pn_handle* h) { return plan_for<kTY>(h).x_end; }
 
 cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,
                          double* partials, cudaStream_t s) {
+    return launch_tiled_gated(h, mode, x, y, bvec, partials, nullptr, s);
+}
+
+cudaError_t launch_tiled_gated(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,
+                               double* partials, const int* live, cudaStream_t s) {
     const TiledPlan p = plan_for<kTY>(h);
     tiled::Args a{};
     a.x = x;
@@ -644,6 +661,7 @@ cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y,
     for (int l = 0; l < 8; ++l) a.fl[l] = l == 0 ? 1.0f : float(std::pow(h->g, l));
     for (int q = 0; q < 64; ++q) a.pcls[q] = q < h->K ? (unsigned char)h->plane_class[q] : 0;
     a.partials = partials;
+    a.live = live;
     if (mode == OP_RESIDUAL) return launch_mode<OP_RESIDUAL>(h, a, p, s);
     return launch_mode<OP_APPLY>(h, a, p, s);
 }

@@ -40,6 +40,8 @@ constexpr int kRun = 8;            // float4 products summed in FP32 before each
 struct BInst {
     // operator (from the handle)
     int R, K, n_q, nzb;
+    int generic;     // 1: the Arnoldi-step operator runs in the generic batched launch
+    int pad_;
     int64_t pitch_x, pitch_y, plane_stride, n;
     const pn::Plane* planes;
     const pn::Term* terms;
@@ -88,10 +90,11 @@ struct VecChunk {
     int64_t e0;      // first element (multiple of 4)
 };
 
-enum Gate { G_LIVE = 0, G_RUN = 1, G_NOT_DONE = 2, G_ALL = 3 };
+enum Gate { G_LIVE = 0, G_RUN = 1, G_NOT_DONE = 2, G_ALL = 3, G_LIVE_GENERIC = 4 };
 
 __device__ __forceinline__ bool gate_ok(const BState& s, int gate) {
-    return gate == G_ALL || (gate == G_LIVE && s.live) || (gate == G_RUN && s.run) || (gate == G_NOT_DONE && !s.done);
+    return gate == G_ALL || ((gate == G_LIVE || gate == G_LIVE_GENERIC) && s.live) || (gate == G_RUN && s.run) ||
+           (gate == G_NOT_DONE && !s.done);
 }
 
 __device__ __forceinline__ double bsum(double v) {
@@ -119,7 +122,8 @@ __device__ __forceinline__ void ph_op(const BInst* __restrict__ I, const BState*
                                       int ncta) {
     for (int c = cta; c < nch; c += ncta) {
         const OpChunk k = ch[c];
-        const bool go = gate_ok(st[k.inst], gate);  // uniform over the block
+        // uniform over the block
+        const bool go = gate_ok(st[k.inst], gate) && (gate != G_LIVE_GENERIC || I[k.inst].generic);
         double racc = 0.0;
         if (go) {
             const BInst& in = I[k.inst];
@@ -659,6 +663,13 @@ struct pn_batch {
     cudaStream_t s = nullptr;
     cudaGraphExec_t cycle = nullptr;
     int mode = 0;                   // PN_BATCH_GRAPH or PN_BATCH_PERSISTENT
+    int use_tiled = 1;              // Arnoldi-step operator: per-instance tiled launches on graph branches
+    int n_tiled = 0, n_generic = 0;
+    static constexpr int NSIDE = 8;
+    cudaStream_t side[NSIDE] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[NSIDE] = {};
+    int* d_zero = nullptr;          // a device 0: a gated launch that does nothing
     GridBar* d_bar = nullptr;
     long long spin_limit = 1LL << 24;  // barrier polls (~100 ns each) before PN_ERR_TIMEOUT
     std::string err;
@@ -767,6 +778,38 @@ void launch_op32(pn_batch* b, size_t px, size_t py, size_t pb, int gate, bool re
                                                            b->cho, X, Y, nullptr, gate, nullptr);
 }
 
+// y_i = A_i V_j(i) -> V_{j+1}(i) for live instances: the tiled operator of
+// every tiled-capable instance as its own launch on one of the side streams
+// (independent graph branches that run concurrently), gated by the
+// instance's live flag, and one generic launch for the others.
+void launch_step_apply(pn_batch* b, int j, const int* const* live) {
+    if (!b->use_tiled || b->n_tiled == 0) {
+        launch_op32(b, size_t(P_V0 + j) * b->n, size_t(P_V0 + j + 1) * b->n, 0, G_LIVE, false);
+        return;
+    }
+    cudaEventRecord(b->ev_fork, b->s);
+    for (int k = 0; k < pn_batch::NSIDE; ++k) cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+    int q = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const BInst& in = b->inst[i];
+        if (in.generic) continue;
+        pn::launch_tiled_gated(b->hs[i], pn::OP_APPLY, in.V + size_t(j) * in.n, in.V + size_t(j + 1) * in.n, nullptr,
+                               nullptr, live[i], b->side[q++ % pn_batch::NSIDE]);
+    }
+    if (b->n_generic > 0)
+        launch_op32(b, size_t(P_V0 + j) * b->n, size_t(P_V0 + j + 1) * b->n, 0, G_LIVE_GENERIC, false);
+    for (int k = 0; k < pn_batch::NSIDE; ++k) {
+        cudaEventRecord(b->ev_join[k], b->side[k]);
+        cudaStreamWaitEvent(b->s, b->ev_join[k], 0);
+    }
+}
+
+std::vector<const int*> live_flags(const pn_batch* b) {
+    std::vector<const int*> f(b->n);
+    for (int i = 0; i < b->n; ++i) f[i] = &b->d_state[i].live;
+    return f;
+}
+
 void launch_cycle(pn_batch* b) {
     const int gv = grid_of(b, b->vc.size(), b->vec_mult);
     const int nch = int(b->vc.size());
@@ -778,8 +821,9 @@ void launch_cycle(pn_batch* b) {
     launch_op32(b, p_d32(b), P_V0, p_r32(b), G_RUN, true);
     kb_cycle_init<<<b->n, 32, 0, b->s>>>(b->d_inst, b->d_state, oc_first, oc_count, b->d_part_op, b->m);
     kb_scale0<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv);
+    const std::vector<const int*> live = live_flags(b);
     for (int j = 0; j < b->m; ++j) {
-        launch_op32(b, size_t(P_V0 + j) * b->n, size_t(P_V0 + j + 1) * b->n, 0, G_LIVE, false);
+        launch_step_apply(b, j, live.data());
         kb_mdot<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, j, b->d_part_vec);
         kb_givens<<<b->n, 32, 0, b->s>>>(b->d_inst, b->d_state, vc_first, vc_count, b->d_part_vec, j, b->m);
         kb_maxpy<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, j);
@@ -790,6 +834,16 @@ void launch_cycle(pn_batch* b) {
 
 int ensure_graph(pn_batch* b) {
     if (b->cycle) return PN_OK;
+    if (b->use_tiled && b->n_tiled > 0) {
+        // one gated launch per tiled instance outside the capture (a device 0
+        // flag: nothing runs) sets the kernels' shared-memory attributes
+        for (int i = 0; i < b->n; ++i)
+            if (!b->inst[i].generic)
+                pn::launch_tiled_gated(b->hs[i], pn::OP_APPLY, b->inst[i].V, b->inst[i].V + b->inst[i].n, nullptr,
+                                       nullptr, b->d_zero, b->s);
+        const cudaError_t e0 = cudaStreamSynchronize(b->s);
+        if (e0 != cudaSuccess) return bcuda(b, e0, "pn_batch: preparing the tiled operator");
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "pn_batch: begin capture");
@@ -864,6 +918,12 @@ void free_batch(pn_batch* b) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->h_state) cudaFreeHost(b->h_state);
+    for (int k = 0; k < pn_batch::NSIDE; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->d_zero) cudaFree(b->d_zero);
     if (b->s) cudaStreamDestroy(b->s);
 }
 
@@ -933,6 +993,19 @@ int pn_batch_create(pn_batch** out, pn_handle* const* handles, int count, int re
         delete b;
         return PN_ERR_ALLOC;
     }
+    for (int k = 0; k < pn_batch::NSIDE && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_zero, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_zero, 0, sizeof(int), b->s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        delete b;
+        return PN_ERR_CUDA;
+    }
     b->inst.resize(count);
     std::vector<void*> ptrs(b->ptr_count, nullptr);
     for (int i = 0; i < count; ++i) {
@@ -941,6 +1014,10 @@ int pn_batch_create(pn_batch** out, pn_handle* const* handles, int count, int re
         in.R = h->R;
         in.K = h->K;
         in.n_q = h->n_q_planes;
+        in.generic = pn::tiled_serves(h) ? 0 : 1;
+        in.pad_ = 0;
+        if (in.generic) ++b->n_generic;
+        else ++b->n_tiled;
         in.nzb = int(h->nz_box);
         in.pitch_x = h->pitch_x;
         in.pitch_y = h->pitch_y;
@@ -1025,6 +1102,22 @@ int pn_batch_set_mode(pn_batch* b, int mode, long long spin_limit) {
     return PN_OK;
 }
 
+int pn_batch_set_op_path(pn_batch* b, int tiled) {
+    if (!b) return PN_ERR_ARG;
+    b->use_tiled = tiled ? 1 : 0;
+    if (b->cycle) {
+        cudaGraphExecDestroy(b->cycle);
+        b->cycle = nullptr;
+    }
+    return PN_OK;
+}
+
+int pn_batch_get_op_path(const pn_batch* b, int* tiled) {
+    if (!b || !tiled) return PN_ERR_ARG;
+    *tiled = (b->use_tiled && b->n_tiled > 0) ? 1 : 0;
+    return PN_OK;
+}
+
 int pn_batch_barrier_test(int blocks, int expected, long long spin_limit, int* timed_out, void* stream) {
     if (blocks < 1 || expected < blocks || spin_limit < 1 || !timed_out) return PN_ERR_ARG;
     int occ = 0;
@@ -1081,14 +1174,20 @@ int pn_batch_tune(pn_batch* b, void* stream) {
         return bfail(b, PN_ERR_CUDA, "pn_batch_tune: events");
     }
     const int jmid = b->m / 2;
-    auto time_it = [&](bool op) -> float {
+    const std::vector<const int*> live = live_flags(b);
+    auto time_it = [&](int what) -> float {  // 0: vector kernels, 1: generic operator, 2: tiled branches
         const int gv = grid_of(b, b->vc.size(), b->vec_mult);
         const int nch = int(b->vc.size());
         float best = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, b->s);
-            if (op) {
+            if (what == 1) {
                 launch_op32(b, size_t(P_V0) * b->n, size_t(P_V0 + 1) * b->n, 0, G_LIVE, false);
+            } else if (what == 2) {
+                const int keep = b->use_tiled;
+                b->use_tiled = 1;
+                launch_step_apply(b, 0, live.data());
+                b->use_tiled = keep;
             } else {
                 kb_mdot<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, jmid, b->d_part_vec);
                 kb_maxpy<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, jmid);
@@ -1112,7 +1211,7 @@ int pn_batch_tune(pn_batch* b, void* stream) {
             b->cho = oc;
             b->op_mult = mu;
             if ((rc = build_lists(b)) != PN_OK) break;
-            const float t = time_it(true);
+            const float t = time_it(1);
             if (t < 0.0f) {
                 rc = bcuda(b, cudaGetLastError(), "pn_batch_tune");
                 break;
@@ -1125,13 +1224,19 @@ int pn_batch_tune(pn_batch* b, void* stream) {
         }
     b->cho = bo;
     b->op_mult = bmo;
+    if (rc == PN_OK && (rc = build_lists(b)) == PN_OK && b->n_tiled > 0) {
+        // the Arnoldi-step operator: per-instance tiled launches vs the generic launch
+        const float tt = time_it(2);
+        if (tt < 0.0f) rc = bcuda(b, cudaGetLastError(), "pn_batch_tune");
+        else b->use_tiled = tt < best_op ? 1 : 0;
+    }
     for (int64_t vcn : vec_chunks) {
         if (rc != PN_OK) break;
         for (int mu : mults) {
             b->chv = vcn;
             b->vec_mult = mu;
             if ((rc = build_lists(b)) != PN_OK) break;
-            const float t = time_it(false);
+            const float t = time_it(0);
             if (t < 0.0f) {
                 rc = bcuda(b, cudaGetLastError(), "pn_batch_tune");
                 break;
@@ -1198,6 +1303,7 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     const pn_solve_opts o = *opts;
     if (o.solver != PN_SOLVER_IR_GMRES) return bfail(b, PN_ERR_UNSUPPORTED, "pn_batch_solve: only PN_SOLVER_IR_GMRES is batched");
     if (o.restart != b->m) return bfail(b, PN_ERR_ARG, "pn_batch_solve: opts->restart must equal the batch's restart");
+    if (o.basis != PN_BASIS_F32) return bfail(b, PN_ERR_UNSUPPORTED, "pn_batch_solve: the batch keeps an FP32 basis");
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_outer < 1 || !(o.inner_tol > 0.0))
         return bfail(b, PN_ERR_ARG, "pn_batch_solve: bad tolerances or caps");
     for (int i = 0; i < b->n; ++i)

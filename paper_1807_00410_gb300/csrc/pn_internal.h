@@ -52,6 +52,7 @@ int pn_sm_count();
 struct pn_handle {
     int N = 0, K = 0, R = 0;
     int dims = 3;        // 3: R^3 cells; 2: the z-independent reduction on R^2 cells
+    int tile_ctas_per_sm = 4;  // z-chunking target of the tiled FP32 operator (pn_tune_apply)
     int64_t nz_box = 0;  // z-slices of a plane box: R + 1 (3D) or 1 (2D)
     double h = 0.0;
     double g = 0.0;  // Henyey-Greenstein mean cosine
@@ -117,7 +118,14 @@ int op_partial_count(const pn_handle* h, int dtype);
 // plane box; one FP64 residual partial per CTA.
 cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,
                          double* partials, cudaStream_t s);
+// The same with a device flag: the launch does nothing while *live == 0 (for
+// launches recorded once into a CUDA graph and replayed while instances finish).
+cudaError_t launch_tiled_gated(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,
+                               double* partials, const int* live, cudaStream_t s);
+// Whether the tiled FP32 operator serves this handle.
+bool tiled_serves(const pn_handle* h);
 int tiled_partial_count(const pn_handle* h);
+int tiled_partial_bound(const pn_handle* h);  // over every z-chunking pn_tune_apply may choose
 int tiled_x_end(const pn_handle* h);
 
 // partials[b] = per-block sum of a_i * b_i (FP64); then *out = sum of partials.

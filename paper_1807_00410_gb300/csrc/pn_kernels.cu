@@ -127,6 +127,8 @@ static bool use_tiled(const pn_handle* h, int dtype) {
     return dtype == PN_F32 && h->dims == 3 && h->plane_stride * 16 < (int64_t(1) << 32);
 }
 
+bool tiled_serves(const pn_handle* h) { return use_tiled(h, PN_F32); }
+
 int op_partial_count(const pn_handle* h, int dtype) {
     if (use_tiled(h, dtype)) return tiled_partial_count(h);
     return naive_grid_x(h) * h->K;

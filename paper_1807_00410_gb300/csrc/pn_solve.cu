@@ -9,6 +9,7 @@
 //    matrix, Givens rotations and the triangular solve in FP64 on the device.
 //  * IR: iterative refinement; the residual and the iterate are FP64, each
 //    correction comes from an FP32 GMRES solve of A d = r / ||r||.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -24,7 +25,9 @@ enum { S_RR = 0, S_QQ = 1, S_G0 = 2, S_G1 = 3, S_BETA2 = 4, S_RES = 5, S_SCALE =
        S_PNRM = 65, S_TICKET = 66 };
 
 int nb_vec() { return 4 * pn_sm_count(); }
-int nb_mdot() { return 4 * pn_sm_count(); }  // the fused CGS1 step (partials: nb_mdot * (PN_MAX_MDOT + 1))
+// the fused CGS1 step: one full wave (its 42-46 registers allow 5 CTAs of 256
+// threads per SM); partials: nb_mdot * (PN_MAX_MDOT + 1) doubles
+int nb_mdot() { return 5 * pn_sm_count(); }
 
 __device__ __forceinline__ double warp_block_sum(double v) {
     __shared__ double red[32];
@@ -574,6 +577,282 @@ int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
     return PN_OK;
 }
 
+// ---- GMRES with the Krylov basis stored in FP16 -----------------------------
+//
+// The basis vectors are stored as FP16 values of sigma * v (sigma = sqrt of the
+// number of unknowns, so the entries of a unit vector are of order one and
+// stay inside FP16's range); every product, sum and update is FP32, and the
+// cross-block sums and the Arnoldi scalars FP64, as in the FP32 path.  The
+// newest basis vector is also kept in FP32 for the operator.  The stored
+// basis carries a relative rounding of about 5e-4 per entry, far below the
+// inner solve's relative target (1e-2 by default): the refinement's FP64
+// residual corrects what the inner solve leaves.  Per Arnoldi step the vector
+// kernels move about (26 + 4 j) bytes per unknown instead of (28 + 8 j).
+
+__device__ __forceinline__ void h8_to_f(const uint4 u, float (&f)[8]) {
+    const __half2* h = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __half22float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 f_to_h8(const float (&f)[8]) {
+    uint4 u;
+    __half2* h = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2half2_rn(f[2 * k], f[2 * k + 1]);
+    return u;
+}
+
+// The fused CGS1 step of the FP16-basis path: projections (V16_i . w) / sigma
+// for i < nv, |w|^2, the deterministic last-block reduction and the Givens
+// update (as k_mdot_givens_f32).  n8 = n / 8; w is FP32.
+__global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* V16, int64_t vstride8, int nv,
+                                                       const float4* w, float inv_sigma, double* partials,
+                                                       unsigned int* ticket, double* H, int ldh, double* add,
+                                                       double* cs, double* sn, double* g, int j, double* S) {
+    constexpr int NV = PN_MAX_MDOT;
+    float part[NV + 1];
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += stride) {
+        const float4 wa = w[2 * i], wb = w[2 * i + 1];
+        const float wf[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nv) {
+                float q[8];
+                h8_to_f(V16[v * vstride8 + i], q);
+                float t = part[v];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t = fmaf(q[k], wf[k], t);
+                part[v] = t;
+            }
+        }
+        float t = part[NV];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t = fmaf(wf[k], wf[k], t);
+        part[NV] = t;
+    }
+    __shared__ double red[NV + 1][8];
+    __shared__ double tot[NV + 1];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) {
+        if (v < nv || v == NV) {
+            float t = part[v];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) red[v][warp] = double(t);
+        }
+    }
+    __syncthreads();
+    const int nb = gridDim.x;
+    if (threadIdx.x <= NV && (int(threadIdx.x) < nv || threadIdx.x == NV)) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[threadIdx.x][q];
+        partials[int64_t(threadIdx.x) * nb + blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == unsigned(nb - 1)) ? 1 : 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int v = warp; v <= NV; v += 8) {
+        if (v < nv || v == NV) {
+            double t = 0.0;
+            for (int b = lane; b < nb; b += 32) t += __ldcg(partials + int64_t(v) * nb + b);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) tot[v] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* col = H + int64_t(j) * ldh;
+        for (int i = 0; i <= j; ++i) {
+            const double hi = tot[i] * double(inv_sigma);
+            add[i] = hi;
+            col[i] = hi;
+        }
+        S[S_NRM2] = tot[NV];
+        givens_core(H, ldh, add, cs, sn, g, j, S, 1, tot[NV]);
+        *ticket = 0u;
+    }
+}
+
+// w' = (w - sum_{i < nv} add[i] V16_i / sigma) * S[S_SCALE];
+// V16_out = fp16(sigma w'), vcur = w'.
+__global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* w, const uint4* V16, int64_t vstride8,
+                                                 int nv, const double* add, float inv_sigma, float sigma,
+                                                 const double* S, uint4* V16_out, float4* vcur) {
+    constexpr int NV = PN_MAX_MDOT;
+    float cj[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
+    const float sc = float(S[S_SCALE]);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 wa = w[2 * i], wb = w[2 * i + 1];
+        float acc[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nv) {
+                float q[8];
+                h8_to_f(V16[v * vstride8 + i], q);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = fmaf(cj[v], q[k], acc[k]);
+            }
+        }
+        float hs[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            acc[k] *= sc;
+            hs[k] = acc[k] * sigma;
+        }
+        V16_out[i] = f_to_h8(hs);
+        vcur[2 * i] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        vcur[2 * i + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+}
+
+// First basis vector: r / beta (beta^2 = S[S_BETA2]) into V16_0 (scaled) and vcur.
+__global__ void __launch_bounds__(256) k_first16(int64_t n8, const float4* r, float sigma, const double* S,
+                                                 uint4* V16_0, float4* vcur) {
+    const double b2 = S[S_BETA2];
+    const float inv = b2 > 0.0 ? float(1.0 / sqrt(b2)) : 0.0f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 a = r[2 * i], b = r[2 * i + 1];
+        const float f[8] = {a.x * inv, a.y * inv, a.z * inv, a.w * inv, b.x * inv, b.y * inv, b.z * inv, b.w * inv};
+        float hs[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) hs[k] = f[k] * sigma;
+        V16_0[i] = f_to_h8(hs);
+        vcur[2 * i] = make_float4(f[0], f[1], f[2], f[3]);
+        vcur[2 * i + 1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
+}
+
+// x += sum_{i < nv} y_i V16_i / sigma.
+__global__ void __launch_bounds__(256) k_update16(int64_t n8, float4* x, const uint4* V16, int64_t vstride8, int nv,
+                                                  const double* y, float inv_sigma) {
+    constexpr int NV = PN_MAX_MDOT;
+    float yj[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) yj[v] = v < nv ? float(y[v]) * inv_sigma : 0.0f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 a = x[2 * i], b = x[2 * i + 1];
+        float acc[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nv) {
+                float q[8];
+                h8_to_f(V16[v * vstride8 + i], q);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = fmaf(yj[v], q[k], acc[k]);
+            }
+        }
+        x[2 * i] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        x[2 * i + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+}
+
+// Restarted GMRES(m), CGS1, FP32 arithmetic with the basis in FP16 (m <= 16).
+// Same contract as gmres<float>.
+int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, int m, int max_iter, int check_every,
+              int* iters, double* rel_out) {
+    pn_handle* h = c.h;
+    const int64_t n = h->n_elems;  // a multiple of 32
+    const int64_t n8 = n / 8;
+    const int nb = nb_vec();
+    double* S = h->d_scalars;
+    const float sigma = float(std::sqrt(double(h->n_active)));
+    const float inv_sigma = 1.0f / sigma;
+    const size_t v16bytes = size_t(m + 1) * n * sizeof(__half);
+    const size_t fbytes = 2 * size_t(n) * sizeof(float);  // w and vcur
+    const size_t vbytes = ((v16bytes + 255) / 256) * 256 + fbytes;
+    const int ldh = m + 1;
+    const size_t dcount = size_t(ldh) * m + 4 * size_t(m + 1) + 16 * size_t(m + 1);
+    int rc = ensure_work(h, vbytes + dcount * sizeof(double) + 256);
+    if (rc != PN_OK) return rc;
+    __half* V16 = (__half*)h->d_work;
+    float* w = (float*)((char*)h->d_work + ((v16bytes + 255) / 256) * 256);
+    float* vcur = w + n;
+    double* H = (double*)((char*)h->d_work + ((vbytes + 255) / 256) * 256);
+    double* cs = H + size_t(ldh) * m;
+    double* sn = cs + (m + 1);
+    double* g = sn + (m + 1);
+    double* y = g + (m + 1);
+    double* add = y + (m + 1);
+    c.ok(cudaMemsetAsync(S + S_TICKET, 0, sizeof(double), c.s), "gmres16: ticket");
+    const double bnorm = std::sqrt(bnorm2);
+    const double target = tol * (bnorm > 0.0 ? bnorm : 1.0);
+    const double ob = c.ob(pn::OP_APPLY, 4.0, false);
+    int total = 0;
+    double res = 0.0;
+    const int every = check_every > 0 ? check_every : 1;
+    const int64_t vs8 = n / 8;
+    for (;;) {
+        c.pb();
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, w, PN_F32, h->d_partials, c.s, bvec), "gmres16: residual");
+        c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, 4.0, bvec != nullptr));
+        c.pb();
+        c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, PN_F32), 1, S + S_BETA2, c.s),
+             "gmres16: reduce");
+        c.pe(PN_PROF_SCALAR, 0.0);
+        double b2 = 0.0;
+        if (!c.read(S_BETA2, 1, &b2)) return c.rc;
+        res = std::sqrt(b2);
+        if (!std::isfinite(res)) return pn_fail(h, PN_ERR_NONFINITE, "gmres16: non-finite residual");
+        if (res <= target || total >= max_iter) break;
+        c.pb();
+        k_gm_init<<<1, 32, 0, c.s>>>(g, m, S);
+        k_first16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, sigma, S, (uint4*)V16, (float4*)vcur);
+        c.launched("gmres16: init", 2);
+        c.pe(PN_PROF_VECTOR, double(h->n_active) * (4.0 + 2.0 + 4.0));
+        int j = 0;
+        for (; j < m && total < max_iter; ++j) {
+            c.pb();
+            c.lk(pn::launch_op(h, pn::OP_APPLY, vcur, w, PN_F32, nullptr, c.s), "gmres16: A v");
+            c.pe(PN_PROF_APPLY, ob);
+            c.pb();
+            k_mdot16_givens<<<nb_mdot(), 256, 0, c.s>>>(n8, (const uint4*)V16, vs8, j + 1, (const float4*)w,
+                                                        inv_sigma, h->d_partials,
+                                                        reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add,
+                                                        cs, sn, g, j, S);
+            c.launched("gmres16: mdot");
+            c.pe(PN_PROF_MDOT, double(h->n_active) * (2.0 * (j + 1) + 4.0));
+            c.pb();
+            k_maxpy16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, (const uint4*)V16, vs8, j + 1, add, inv_sigma, sigma,
+                                           S, (uint4*)V16 + int64_t(j + 1) * vs8, (float4*)vcur);
+            c.launched("gmres16: maxpy");
+            c.pe(PN_PROF_MAXPY, double(h->n_active) * (4.0 + 2.0 * (j + 1) + 2.0 + 4.0));
+            ++total;
+            if ((j + 1) % every == 0 || j + 1 == m || total >= max_iter) {
+                double r1 = 0.0;
+                if (!c.read(S_RES, 1, &r1)) return c.rc;
+                if (!std::isfinite(r1)) return pn_fail(h, PN_ERR_NONFINITE, "gmres16: non-finite Hessenberg");
+                if (r1 <= target) {
+                    ++j;
+                    break;
+                }
+            }
+        }
+        c.pb();
+        k_gm_backsolve<<<1, 32, 0, c.s>>>(H, ldh, g, y, j);
+        k_update16<<<nb, 256, 0, c.s>>>(n8, (float4*)x, (const uint4*)V16, vs8, j, y, inv_sigma);
+        c.launched("gmres16: update", 2);
+        c.pe(PN_PROF_MAXPY, double(h->n_active) * (8.0 + 2.0 * j));
+        if (c.rc != PN_OK) return c.rc;
+    }
+    *iters += total;
+    *rel_out = bnorm > 0.0 ? res / bnorm : res;
+    return c.rc;
+}
+
 // Restarted GMRES(m) for A x = b (b = Q if bvec is null).  tol is relative to
 // ||b|| (bnorm2 = ||b||^2).  Adds the inner iterations to *iters.
 template <typename T>
@@ -813,8 +1092,11 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
         // inner tolerance: relative reduction, but not beyond what the outer target needs
         double itol = o.inner_tol;
         if (rel > 0.0 && o.tol / rel > itol) itol = std::min(0.5, o.tol / rel);
-        rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel,
-                          o.ortho, net, &st.precond_applications, &fell_back);
+        if (o.basis == PN_BASIS_F16 && !net)
+            rc = gmres_f16(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel);
+        else
+            rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner,
+                              &inner_rel, o.ortho, net, &st.precond_applications, &fell_back);
         if (fell_back) net = nullptr;
         if (rc != PN_OK) break;
         c.pb();
@@ -857,6 +1139,9 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
     if (o.solver != PN_SOLVER_CGLS && (o.restart < 1 || o.restart > 200))
         return pn_fail(h, PN_ERR_ARG, "pn_solve: restart must be in [1, 200]");
     if (o.ortho != PN_ORTHO_CGS2 && o.ortho != PN_ORTHO_CGS1) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad ortho");
+    if (o.basis != PN_BASIS_F32 && o.basis != PN_BASIS_F16) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad basis");
+    if (o.basis == PN_BASIS_F16 && (o.solver != PN_SOLVER_IR_GMRES || o.restart > PN_MAX_MDOT))
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the FP16 basis needs PN_SOLVER_IR_GMRES and restart <= 16");
     pn_solve_stats st{};
     Ctx c{h, (cudaStream_t)stream};
     pn_prof_reset(h, o.profile != 0);

@@ -95,6 +95,51 @@ def solve_pairs(seed: int, R: int, n_src: int, torch, tol: float = 1e-6):
     return pairs
 
 
+def hard_pairs(seed: int, R: int, n_src: int, torch, cycles=(0, 1, 3, 6, 10, 20), restart: int = 15):
+    """Supervised pairs (r_k, e_k) for one medium: for each source, the
+    residual r_k = Q - A x_k that plain GMRES(restart) leaves after k restart
+    cycles from zero and its exact error e_k = x* - x_k (x* solved to 1e-8).
+    The late residuals are dominated by the components restarted GMRES
+    converges slowly on, the ones a preconditioner must supply."""
+    out = []
+    for r0, sq in source_vectors(seed, R, n_src, torch):
+        xs = sq.zeros(torch.float64)
+        sq.solve(xs, solver="ir", tol=1e-8, restart=restart, ortho="cgs1", max_iter=100000, raise_on_error=False)
+        x = sq.zeros(torch.float32)
+        done = 0
+        for k in sorted(cycles):
+            if k > done:
+                sq.solve(x, solver="gmres", tol=1e-12, restart=restart, ortho="cgs1", max_iter=(k - done) * restart,
+                         raise_on_error=False)
+                done = k
+            r = sq.zeros(torch.float32)
+            sq.residual(x, r)
+            out.append((r, (xs - x.double()).float(), sq))
+        del r0
+    return out
+
+
+def make_hard_dataset(seeds, R: int, n_src: int, torch, log=print):
+    """Features and supervised targets of hard_pairs over the media (GPU)."""
+    feats, tgts = [], []
+    t0 = time.time()
+    for i, seed in enumerate(seeds):
+        pairs = hard_pairs(seed, R, n_src, torch)
+        n_act = pairs[0][2].layout.n_active
+        for r, e, sq in pairs:
+            rn = float(torch.linalg.vector_norm(r.double()))
+            if not (rn > 0.0 and math.isfinite(rn)):
+                continue
+            rms = rn / math.sqrt(n_act)
+            feats.append(sq.cnn_features(r, 1.0 / rms))
+            tgts.append(sq.cnn_targets(e, r, 1.0 / rms))
+        for sq in {id(p[2]): p[2] for p in pairs}.values():
+            sq.close()
+        if (i + 1) % 20 == 0:
+            log(f"  data: {i + 1}/{len(seeds)} media, {len(feats)} samples, {time.time() - t0:.1f} s")
+    return torch.stack(feats), torch.stack(tgts)
+
+
 def make_dataset(seeds, R: int, n_src: int, n_mix: int, torch, log=print):
     """Features (S, R, R, R, K+3) and targets (S, R, R, R, K) on the GPU."""
     feats, tgts = [], []
@@ -334,7 +379,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=5e-4)
-    ap.add_argument("--loss", choices=["residual", "supervised"], default="residual")
+    ap.add_argument("--loss", choices=["residual", "supervised", "hard"], default="hard",
+                    help="residual: |A M(r) - r|^2 on residual pools; supervised: exact errors of solved sources; "
+                         "hard: exact errors of the residuals plain GMRES leaves after k restart cycles")
     ap.add_argument("--rounds", type=int, default=1,
                     help="residual loss: after each round, add the residuals FGMRES with the network leaves "
                          "to the pools and train again")
@@ -356,6 +403,9 @@ def main(argv=None):
                 if (i + 1) % 25 == 0:
                     print(f"  data: {i + 1}/{len(media)} media ({time.time() - t0:.1f} s)", flush=True)
             report["samples"] = int(sum(p[1].shape[0] for p in pools))
+        elif args.loss == "hard":
+            X, Y = make_hard_dataset(media, args.train_r, args.sources, torch)
+            report["samples"] = int(X.shape[0])
         else:
             X, Y = make_dataset(media, args.train_r, args.sources, args.mix, torch)
             report["samples"] = int(X.shape[0])

@@ -47,7 +47,8 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_cnn_forward", "pn_cnn_backward", "pn_cnn_adam_step", "pn_cnn_train_step", "pn_cnn_features",
            "pn_cnn_targets", "pn_cnn_output", "pn_cnn_precondition", "pn_batch_create", "pn_batch_destroy",
            "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
-           "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test"]
+           "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
+           "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -73,7 +74,7 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
-                ("ortho", ctypes.c_int), ("precond", ctypes.c_void_p)]
+                ("ortho", ctypes.c_int), ("precond", ctypes.c_void_p), ("basis", ctypes.c_int)]
 
 
 class _SolveStats(ctypes.Structure):
@@ -135,6 +136,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_batch_get_tiling": (i, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i),
                                     ctypes.POINTER(i)]),
         "pn_batch_tune": (i, [vp, vp]),
+        "pn_tune_apply": (i, [vp, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
+        "pn_set_apply_tiling": (i, [vp, i]),
+        "pn_batch_set_op_path": (i, [vp, i]),
+        "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
         "pn_batch_set_mode": (i, [vp, i, ctypes.c_longlong]),
         "pn_batch_barrier_test": (i, [i, i, ctypes.c_longlong, ctypes.POINTER(i), vp]),
     }
@@ -419,7 +424,8 @@ class System:
 
     def solve(self, u, solver: str = "cgls", tol: float = 1e-6, max_iter: int = 100000, restart: int = 60,
               inner_tol: float = 1e-2, max_outer: int = 50, check_every: int = 10, stream=None,
-              raise_on_error: bool = True, profile: bool = False, ortho: str = "cgs2", precond=None) -> dict:
+              raise_on_error: bool = True, profile: bool = False, ortho: str = "cgs2", precond=None,
+              basis: str = "f32") -> dict:
         """Solve A u = Q in place (u is the initial guess).  Returns the stats."""
         up, dt = self._vec(u)
         o = _SolveOpts()
@@ -434,6 +440,7 @@ class System:
         o.inner_tol, o.max_outer, o.check_every = float(inner_tol), int(max_outer), int(check_every)
         o.profile = 1 if profile else 0
         o.ortho = {"cgs2": 0, "cgs1": 1}[ortho]
+        o.basis = {"f32": 0, "f16": 1}[basis]
         st = _SolveStats()
         rc = self._lib.pn_solve(self._h, up, ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
         stats = {"status": rc, "iterations": st.iterations, "outer_iterations": st.outer_iterations,
@@ -452,6 +459,15 @@ class System:
             self._check(self._lib.pn_profile_get(self._h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
             out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
         return out
+
+    def tune_apply(self, stream=None) -> dict:
+        """The operator autotuner (pn_tune_apply): keeps the fastest z-chunking."""
+        c, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.pn_tune_apply(self._h, _stream_ptr(stream), ctypes.byref(c), ctypes.byref(ms)))
+        return {"ctas_per_sm": c.value, "ms": ms.value}
+
+    def set_apply_tiling(self, ctas_per_sm: int):
+        self._check(self._lib.pn_set_apply_tiling(self._h, int(ctas_per_sm)))
 
     def cnn_features(self, v, scale: float = 1.0, stream=None):
         """Network input features of a padded FP32 vector: (R, R, R, K + 3)."""
@@ -573,7 +589,13 @@ class Batch:
         om, vm = ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.pn_batch_get_tiling(self._h, ctypes.byref(oc), ctypes.byref(vc), ctypes.byref(om),
                                                   ctypes.byref(vm)))
-        return {"op_chunk": oc.value, "vec_chunk": vc.value, "op_ctas_per_sm": om.value, "vec_ctas_per_sm": vm.value}
+        t = ctypes.c_int()
+        self._check(self._lib.pn_batch_get_op_path(self._h, ctypes.byref(t)))
+        return {"op_chunk": oc.value, "vec_chunk": vc.value, "op_ctas_per_sm": om.value, "vec_ctas_per_sm": vm.value,
+                "tiled_operator": bool(t.value)}
+
+    def set_op_path(self, tiled: bool):
+        self._check(self._lib.pn_batch_set_op_path(self._h, 1 if tiled else 0))
 
     def set_mode(self, persistent: bool, spin_limit: int = 1 << 24):
         """persistent=True: one cooperative launch per restart cycle with

@@ -57,7 +57,9 @@ def test_batched_apply_equals_single_and_oracle(tiling):
     batch = Batch(systems, restart=4)
     if tiling:
         batch.set_tiling(*tiling)
-        assert batch.tiling() == dict(zip(("op_chunk", "vec_chunk", "op_ctas_per_sm", "vec_ctas_per_sm"), tiling))
+        t = batch.tiling()
+        assert {k: t[k] for k in ("op_chunk", "vec_chunk", "op_ctas_per_sm", "vec_ctas_per_sm")} == dict(
+            zip(("op_chunk", "vec_chunk", "op_ctas_per_sm", "vec_ctas_per_sm"), tiling))
     g = torch.Generator(device="cpu").manual_seed(11)
     x64 = []
     for s in systems:
@@ -110,6 +112,32 @@ def test_batched_solve_meets_oracle_residual_and_matches_single():
         s.close()
 
 
+def test_tiled_and_generic_operator_paths_both_meet_the_oracle():
+    """Graph mode with per-instance tiled operator launches on concurrent
+    branches, and with the one generic launch: both solve every instance to
+    the oracle's 1e-6 and agree with each other to what that allows."""
+    from paper_1807_00410_gb300 import Batch
+    cases = [(1, 16, 3, 61), (3, 14, 3, 62), (5, 12, 3, 63), (3, 18, 2, 64), (7, 8, 3, 65)]
+    systems, descs = zip(*[_instance(*c) for c in cases])
+    batch = Batch(systems, restart=12)
+    out = {}
+    for tiled in (True, False):
+        batch.set_op_path(tiled)
+        assert batch.tiling()["tiled_operator"] == tiled
+        us = [s.zeros(torch.float64) for s in systems]
+        stats = batch.solve(us, tol=1e-6)
+        for s, d, u, st in zip(systems, descs, us, stats):
+            lay, A, b = _oracle(d)
+            assert st["status"] == 0
+            assert np.linalg.norm(b - A @ lay.join(s.to_planes(u))) / np.linalg.norm(b) <= 1.0001e-6
+        out[tiled] = us
+    for a, b in zip(out[True], out[False]):
+        assert float((a - b).norm() / b.norm()) <= 1e-5
+    batch.close()
+    for s in systems:
+        s.close()
+
+
 def test_batched_zero_source_and_iteration_cap():
     from paper_1807_00410_gb300 import Batch
     s0, _ = _instance(3, 10, 3, 31, source=False)
@@ -156,6 +184,7 @@ def test_persistent_mode_equals_graph_mode():
     cases = [(1, 12, 3, 41), (3, 14, 3, 42), (5, 8, 3, 43), (3, 16, 2, 44)]
     systems, descs = zip(*[_instance(*c) for c in cases])
     batch = Batch(systems, restart=10)
+    batch.set_op_path(False)  # the persistent cycle uses the generic batched operator
     ug = [s.zeros(torch.float64) for s in systems]
     sg = batch.solve(ug, tol=1e-6)
     batch.set_mode(True)

@@ -314,6 +314,71 @@ def test_ir_with_each_orthogonalisation_meets_oracle_residual(ortho):
     gpu.close()
 
 
+@pytest.mark.parametrize("N,R,restart", [(5, 12, 15), (1, 20, 16), (3, 17, 8)])
+def test_ir_with_fp16_basis_meets_oracle_residual(N, R, restart):
+    """The FP16-stored Krylov basis (FP32 arithmetic, FP64 refinement) gives a
+    solution with oracle residual <= 1e-6 that agrees with the FP32-basis
+    solve to the accuracy the residual allows (relative L2 of L00 <= 1e-5)."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(N, R, 11, 0.5, 40.0, 0.95, 0.3)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00)
+    S = opn.assemble(N, R, med)
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    u16 = gpu.zeros(torch.float64)
+    st16 = gpu.solve(u16, solver="ir", tol=1e-6, restart=restart, ortho="cgs1", basis="f16", profile=True)
+    assert gpu.profile()["mdot"]["launches"] > 0  # the profile of the last (FP16-basis) solve
+    u32 = gpu.zeros(torch.float64)
+    st32 = gpu.solve(u32, solver="ir", tol=1e-6, restart=restart, ortho="cgs1")
+    assert st16["rel_residual"] <= 1e-6
+    assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u16))) <= 1.0001e-6
+    a, b = gpu.to_planes(u16)[0], gpu.to_planes(u32)[0]
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-5
+    assert st16["iterations"] <= 1.5 * st32["iterations"] + 2 * restart
+    gpu.close()
+
+
+def test_apply_tiling_plans_give_identical_outputs_and_tuner_picks_one():
+    """Every z-chunking of the tiled FP32 operator computes each output with the
+    same operands in the same order: apply and residual vectors are bitwise
+    equal across plans; the autotuner keeps one of its candidates."""
+    from paper_1807_00410_gb300 import System
+    N, R = 5, 29
+    p = pn_inputs.fbm_point(N, R, 13, 0.5, 40.0, 0.95, 0.3)
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    g = torch.Generator(device="cpu").manual_seed(3)
+    lay_o = opn.Layout(N, R)
+    x = gpu.from_planes([torch.rand(sh, generator=g, dtype=torch.float64).numpy() for sh in lay_o.shapes],
+                        dtype=torch.float32)
+    ref_y, ref_r = gpu.zeros(torch.float32), gpu.zeros(torch.float32)
+    gpu.apply(x, ref_y)
+    gpu.residual(x, ref_r)
+    for c in (1, 2, 8, 16):
+        gpu.set_apply_tiling(c)
+        y, r = gpu.zeros(torch.float32), gpu.zeros(torch.float32)
+        gpu.apply(x, y)
+        gpu.residual(x, r)
+        assert torch.equal(y, ref_y) and torch.equal(r, ref_r)
+    t = gpu.tune_apply()
+    assert t["ctas_per_sm"] in (1, 2, 4, 8) and t["ms"] > 0
+    y = gpu.zeros(torch.float32)
+    gpu.apply(x, y)
+    assert torch.equal(y, ref_y)
+    gpu.close()
+
+
+def test_fp16_basis_rejected_outside_refinement():
+    from paper_1807_00410_gb300 import System
+    from paper_1807_00410_gb300.pn import PnError
+    N, R = 3, 8
+    p = pn_inputs.fbm_point(N, R, 12, 0.5, 40.0, 0.95, 0.3)
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    with pytest.raises(PnError):
+        gpu.solve(gpu.zeros(torch.float32), solver="gmres", basis="f16")
+    with pytest.raises(PnError):
+        gpu.solve(gpu.zeros(torch.float64), solver="ir", restart=20, basis="f16")
+    gpu.close()
+
+
 # --- source building and unstaggering ---------------------------------------------
 
 @pytest.mark.parametrize("dtype,axis,sign", [("f64", 0, 1), ("f64", 2, -1), ("f32", 1, 1)])
