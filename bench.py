@@ -236,7 +236,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-REF_ITERS_ESTIMATE = 300
+REF_ITERS_ESTIMATE = 845
 REF_OUTER_ESTIMATE = 4
 
 
