@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-apply-scan", action="store_true", help="skip the separate operator throughput scan")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the FP32 operator on the P_N cloud medium given by --apply-n / --apply-r")
     ap.add_argument("--threshold-sweep", action="store_true",
@@ -73,6 +74,8 @@ def parse():
                     help="many-instance workload: batched solve of --batch-count systems vs one-by-one solves")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-seed", type=int, default=0)
+    ap.add_argument("--batch-rmin", type=int, default=24)
+    ap.add_argument("--batch-rmax", type=int, default=96)
     ap.add_argument("--apply-n", type=int, default=7)
     ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
@@ -277,6 +280,56 @@ def apply_scan(torch, System, pn_inputs, hbm_peak):
     return out
 
 
+LEARNED_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1807_00410_gb300", "weights",
+                               "p3_unet_hard.npy")
+
+
+def learned_compare(torch, args, seeds=(90000, 90001)):
+    """Learned vs plain: held-out P3 64^3 fBm media (sigma_t in [0.5, 80],
+    albedo 0.8..0.99, g 0..0.6, point source) solved to 1e-6 by FP64
+    refinement around plain FP32 GMRES (the bench's basis) and around
+    flexible GMRES with the committed network (training: learned.py --loss
+    hard); CUDA events around each solve, best of two."""
+    import numpy as np
+
+    from paper_1807_00410_gb300 import Net, System
+    from paper_1807_00410_gb300 import learned as L
+    K = 16
+    net = Net(K + 3, K)
+    net.set_params(np.load(LEARNED_WEIGHTS))
+    rows = []
+    for seed in seeds:
+        st, albedo, g = L.medium(seed, 64)
+        Q = np.zeros((64, 64, 64))
+        Q[L.sources(seed, 64, 1)[0][1]] = float(64 ** 3)
+        sysm = System(3, 64, st, albedo, g, Q)
+        row = {"seed": seed}
+        for mode in ("plain", "learned"):
+            best = None
+            for _ in range(2):
+                u = sysm.zeros(torch.float64)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if mode == "plain":
+                    s = sysm.solve(u, solver="ir", tol=1e-6, restart=15, ortho="cgs1", basis=args.basis)
+                else:
+                    s = sysm.solve(u, solver="ir_fgmres", tol=1e-6, restart=15, ortho="cgs1", precond=net)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                if best is None or ms < best["ms"]:
+                    best = {"ms": ms, "iterations": s["iterations"], "rel_residual": s["rel_residual"],
+                            "fallback": s["fallback"], "precond_applications": s["precond_applications"]}
+            row[mode] = best
+        rows.append(row)
+        sysm.close()
+    net.close()
+    return {"workload": "P3 64^3 fBm sigma_t[0.5,80], held-out seeds, point source, to 1e-6",
+            "plain_ms_mean": float(np.mean([r["plain"]["ms"] for r in rows])),
+            "learned_ms_mean": float(np.mean([r["learned"]["ms"] for r in rows])), "rows": rows}
+
+
 def run_ours(args):
     import torch
 
@@ -370,6 +423,8 @@ def run_ours(args):
                      "gb_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
                  for k, v in prof.items()}
 
+    learned = None if (args.no_learned or rank != 0) else learned_compare(torch, args)
+
     # end-to-end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -426,6 +481,7 @@ def run_ours(args):
             "alt_basis": {"basis": alt, "ms_per_step": sum(alt_ms) / len(alt_ms),
                           "iterations": alt_st["iterations"], "rel_residual": alt_st["rel_residual"]},
             "apply": scan,
+            "learned": learned,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
@@ -549,7 +605,7 @@ def run_batched(args):
     from paper_1807_00410_gb300 import Batch, System
     from paper_1807_00410_gb300 import pn as ppn
     torch.cuda.set_device(0)
-    inst = pn_inputs.batch_instances(args.batch_count, args.batch_seed)
+    inst = pn_inputs.batch_instances(args.batch_count, args.batch_seed, r_lo=args.batch_rmin, r_hi=args.batch_rmax)
     systems = []
     for b in inst:
         st = torch.tensor(b.sigma_t, dtype=torch.float64, device="cuda")
@@ -593,7 +649,8 @@ def run_batched(args):
     best = min(times)
     print(json.dumps({
         "mode": "batched", "workload": f"{len(systems)} instances (pn_inputs.batch_instances, seed "
-        f"{args.batch_seed}): grids 24..96 per axis, N in {{1,3,5}}, fBm sigma_t in [0.1, 60], albedo 0.7..0.99, "
+        f"{args.batch_seed}): grids {args.batch_rmin}..{args.batch_rmax} per axis, N in {{1,3,5}}, fBm sigma_t in "
+        f"[0.1, 60], albedo 0.7..0.99, "
         f"g 0..0.7, point or beam source; FP32 GMRES({args.restart}) + FP64 IR to 1e-6",
         "instances": len(systems), "dof": dof, "ms": best, "ms_median": statistics.median(times),
         "solves_per_s": len(systems) / (best * 1e-3), "converged": ok,

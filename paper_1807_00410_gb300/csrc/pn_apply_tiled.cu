@@ -398,90 +398,98 @@ __global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
 }
 
 
-// Outputs of one face class C (p_x = 1) at x = R of row (y, z), from global
-// memory, with the same compile-time couplings as the tiled kernel.
+// Output of plane i of face class C (p_x = 1) at x = R of row (y, z), from
+// global memory, with the same compile-time couplings as the tiled kernel:
+// only this row's own terms are read (at most two loads per term).
 template <int N, int C, int MODE>
-__device__ __forceinline__ void face_class(const Args& a, int y, int z, size_t rowoff, float& rrun) {
+__device__ __forceinline__ void face_out(const Args& a, int y, int z, int i, float& rrun) {
     constexpr Tab T = TabN<N>::value;
     constexpr ClassTab CT = T.cls[C];
     constexpr int by = (C >> 1) & 1, bz = C >> 2;
-    constexpr int nX = T.cls[C ^ 1].n, nY = T.cls[C ^ 2].n, nZ = T.cls[C ^ 4].n;
     constexpr int pX = T.cls[C ^ 1].plane0, pY = T.cls[C ^ 2].plane0, pZ = T.cls[C ^ 4].plane0;
-    if (CT.n == 0) return;
     const int R = a.R;
     const uint32_t ps = a.plane_stride, py = a.pitch_y, px = uint32_t(a.pitch_x);
     const bool active = y < R + by && z < R + bz;
+    const size_t rowoff = size_t(uint32_t(z) * py) + uint32_t(y) * px;
     auto val = [&](int plane, int xx, int yy, int zz, int ext_y, int ext_z) -> float {
         if (yy < 0 || zz < 0 || yy >= ext_y || zz >= ext_z) return 0.0f;
         return __ldg(a.x + size_t(plane) * ps + size_t(uint32_t(zz) * py) + uint32_t(yy) * px + uint32_t(xx));
     };
-    float dx[MAXC], dy[MAXC], dz[MAXC];
-#pragma unroll
-    for (int j = 0; j < MAXC; ++j) {
-        // x: the centre class at slot R - 1 (its slot R lies outside the domain)
-        if (j < nX) dx[j] = active ? -val(pX + j, R - 1, y, z, R + by, R + bz) : 0.0f;
-        // y and z: neighbour class with the other bit, slots i + 1 - b and i - b
-        if (j < nY) dy[j] = active ? val(pY + j, R, y + 1 - by, z, R + 1 - by, R + bz) -
-                                         val(pY + j, R, y - by, z, R + 1 - by, R + bz)
-                                   : 0.0f;
-        if (j < nZ) dz[j] = active ? val(pZ + j, R, y, z + 1 - bz, R + by, R + 1 - bz) -
-                                         val(pZ + j, R, y, z - bz, R + by, R + 1 - bz)
-                                   : 0.0f;
-    }
-    // sigma at the face x = R: centre x = R - 1; mean over the y and z neighbours
-    float st = 0.0f, ss = 0.0f;
+    float tr = 0.0f;
+    int l = 0;
     if (active) {
+#pragma unroll
+        for (int ii = 0; ii < MAXC; ++ii) {
+            if (ii < CT.n && ii == i) {
+                l = CT.row[ii].l;
+                // x: the centre class at slot R - 1 (its slot R lies outside the domain)
+#pragma unroll
+                for (int q = 0; q < MAXT; ++q)
+                    if (q < CT.row[ii].nt[0])
+                        tr = fmaf(CT.row[ii].c[0][q], -val(pX + CT.row[ii].j[0][q], R - 1, y, z, R + by, R + bz), tr);
+                // y and z: the neighbour class with the other bit, slots i + 1 - b and i - b
+#pragma unroll
+                for (int q = 0; q < MAXT; ++q)
+                    if (q < CT.row[ii].nt[1]) {
+                        const int jj = pY + CT.row[ii].j[1][q];
+                        tr = fmaf(CT.row[ii].c[1][q],
+                                  val(jj, R, y + 1 - by, z, R + 1 - by, R + bz) - val(jj, R, y - by, z, R + 1 - by, R + bz),
+                                  tr);
+                    }
+#pragma unroll
+                for (int q = 0; q < MAXT; ++q)
+                    if (q < CT.row[ii].nt[2]) {
+                        const int jj = pZ + CT.row[ii].j[2][q];
+                        tr = fmaf(CT.row[ii].c[2][q],
+                                  val(jj, R, y, z + 1 - bz, R + by, R + 1 - bz) - val(jj, R, y, z - bz, R + by, R + 1 - bz),
+                                  tr);
+                    }
+            }
+        }
+    }
+    const size_t off = size_t(CT.plane0 + i) * ps + rowoff + uint32_t(R);
+    float out = 0.0f;
+    if (active) {
+        // sigma at the face x = R: centre x = R - 1, mean over the y and z neighbours
         const int64_t R2 = int64_t(R) * R;
         const int y0 = by ? max(y - 1, 0) : y, y1 = by ? min(y, R - 1) : y;
         const int z0 = bz ? max(z - 1, 0) : z, z1 = bz ? min(z, R - 1) : z;
         const int64_t c = R - 1;
-        st = 0.25f * (a.st[z0 * R2 + y0 * R + c] + a.st[z0 * R2 + y1 * R + c] + a.st[z1 * R2 + y0 * R + c] +
-                      a.st[z1 * R2 + y1 * R + c]);
-        ss = 0.25f * (a.ss[z0 * R2 + y0 * R + c] + a.ss[z0 * R2 + y1 * R + c] + a.ss[z1 * R2 + y0 * R + c] +
-                      a.ss[z1 * R2 + y1 * R + c]);
-    }
-    const float tscale = a.tsign * a.inv_h;
-#pragma unroll
-    for (int i = 0; i < MAXC; ++i) {
-        if (i < CT.n) {
-            float tr = 0.0f;
-#pragma unroll
-            for (int q = 0; q < MAXT; ++q) {
-                if (q < CT.row[i].nt[0]) tr = fmaf(CT.row[i].c[0][q], dx[CT.row[i].j[0][q]], tr);
-                if (q < CT.row[i].nt[1]) tr = fmaf(CT.row[i].c[1][q], dy[CT.row[i].j[1][q]], tr);
-                if (q < CT.row[i].nt[2]) tr = fmaf(CT.row[i].c[2][q], dz[CT.row[i].j[2][q]], tr);
-            }
-            const size_t off = size_t(CT.plane0 + i) * ps + rowoff + uint32_t(R);
-            float out = 0.0f;
-            if (active) {
-                out = fmaf(fmaf(-a.fl[CT.row[i].l], ss, st), __ldg(a.x + off), tscale * tr);
-                if (MODE == OP_RESIDUAL) {
-                    float b = 0.0f;
-                    if (a.bvec) b = __ldg(a.bvec + off);
-                    else if (CT.plane0 + i < a.n_q) b = __ldg(a.q + off);
-                    out = b - out;
-                    rrun = fmaf(out, out, rrun);
-                }
-            }
-            a.y[off] = out;
+        const float st = 0.25f * (__ldg(a.st + z0 * R2 + y0 * R + c) + __ldg(a.st + z0 * R2 + y1 * R + c) +
+                                  __ldg(a.st + z1 * R2 + y0 * R + c) + __ldg(a.st + z1 * R2 + y1 * R + c));
+        const float ss = 0.25f * (__ldg(a.ss + z0 * R2 + y0 * R + c) + __ldg(a.ss + z0 * R2 + y1 * R + c) +
+                                  __ldg(a.ss + z1 * R2 + y0 * R + c) + __ldg(a.ss + z1 * R2 + y1 * R + c));
+        out = fmaf(fmaf(-a.fl[l], ss, st), __ldg(a.x + off), a.tsign * a.inv_h * tr);
+        if (MODE == OP_RESIDUAL) {
+            float b = 0.0f;
+            if (a.bvec) b = __ldg(a.bvec + off);
+            else if (CT.plane0 + i < a.n_q) b = __ldg(a.q + off);
+            out = b - out;
+            rrun = fmaf(out, out, rrun);
         }
     }
+    a.y[off] = out;
 }
 
-// Class C's planes at x = R when p_x = 0 (no unknown there): write 0.
-template <int N, int C>
-__device__ __forceinline__ void face_zero(const Args& a, size_t rowoff) {
+template <int N, int C, int MODE>
+__device__ __forceinline__ void face_class_items(const Args& a, int64_t t0, int64_t stride, float& rrun) {
     constexpr ClassTab CT = TabN<N>::value.cls[C];
-#pragma unroll
-    for (int i = 0; i < MAXC; ++i)
-        if (i < CT.n) a.y[size_t(CT.plane0 + i) * a.plane_stride + rowoff + uint32_t(a.R)] = 0.0f;
+    if (CT.n == 0) return;
+    const int R = a.R;
+    const int64_t rows = int64_t(R + 1) * (R + 1);
+    // consecutive threads take consecutive rows of the same plane (warp-uniform plane)
+    for (int64_t u = t0; u < rows * CT.n; u += stride) {
+        const int i = int(u / rows);
+        const int64_t row = u % rows;
+        face_out<N, C, MODE>(a, int(row % (R + 1)), int(row / (R + 1)), i, rrun);
+    }
 }
 
 // Slots right of the tiles: x in [x_lo, pitch_x) of every (y, z) row, and the
-// plane tails.  Only x = R can hold unknowns (face classes, p_x = 1); every
-// other slot is written 0.  blockIdx.y = parity class c (0..7): thread t owns
-// row (y, z) = (t % (R+1), t / (R+1)) of class c's planes; blockIdx.y = 8
-// clears the plane tails.
+// plane tails.  Only x = R can hold unknowns (face classes, p_x = 1).
+// blockIdx.y = 0 writes 0 to every other such slot and to the plane tails,
+// one slot per thread; blockIdx.y = 1..4 computes the x = R outputs of face
+// class 1, 3, 5, 7, one (row, plane) per thread.
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
     if (a.live && !*a.live) return;  // uniform over the grid
@@ -491,42 +499,35 @@ __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
     const uint32_t ps = a.plane_stride, py = a.pitch_y;
     const uint32_t px = uint32_t(a.pitch_x);
     const int64_t rows = int64_t(R + 1) * (R + 1);
+    const int w = a.pitch_x - x_lo;
     const uint32_t box = py * uint32_t(R + 1);
     const uint32_t tail = ps - box;
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     float rrun = 0.0f;
-    if (c == 8) {
-        for (int64_t u = t; u < int64_t(tail) * K; u += int64_t(gridDim.x) * blockDim.x)
-            a.y[size_t(u / tail) * ps + box + uint32_t(u % tail)] = 0.0f;
-    } else if (t < rows) {
-        const int y = int(t % (R + 1)), z = int(t / (R + 1));
-        const size_t rowoff = size_t(uint32_t(z) * py) + uint32_t(y) * px;
-        int p0 = 0, n = 0;
-        switch (c) {
-            case 0: p0 = T.cls[0].plane0; n = T.cls[0].n; break;
-            case 1: p0 = T.cls[1].plane0; n = T.cls[1].n; break;
-            case 2: p0 = T.cls[2].plane0; n = T.cls[2].n; break;
-            case 3: p0 = T.cls[3].plane0; n = T.cls[3].n; break;
-            case 4: p0 = T.cls[4].plane0; n = T.cls[4].n; break;
-            case 5: p0 = T.cls[5].plane0; n = T.cls[5].n; break;
-            case 6: p0 = T.cls[6].plane0; n = T.cls[6].n; break;
-            default: p0 = T.cls[7].plane0; n = T.cls[7].n; break;
-        }
-        for (int p = p0; p < p0 + n; ++p)
-            for (int x = x_lo; x < a.pitch_x; ++x)
-                if (x != R) a.y[size_t(p) * ps + rowoff + uint32_t(x)] = 0.0f;
-        if (x_lo <= R) {
-            switch (c) {
-                case 1: face_class<N, 1, MODE>(a, y, z, rowoff, rrun); break;
-                case 3: face_class<N, 3, MODE>(a, y, z, rowoff, rrun); break;
-                case 5: face_class<N, 5, MODE>(a, y, z, rowoff, rrun); break;
-                case 7: face_class<N, 7, MODE>(a, y, z, rowoff, rrun); break;
-                case 0: face_zero<N, 0>(a, rowoff); break;
-                case 2: face_zero<N, 2>(a, rowoff); break;
-                case 4: face_zero<N, 4>(a, rowoff); break;
-                default: face_zero<N, 6>(a, rowoff); break;
+    if (blockIdx.y == 0) {
+        const int64_t nz = w > 0 ? int64_t(K) * rows * w : 0;
+        for (int64_t u = t0; u < nz + int64_t(K) * tail; u += stride) {
+            if (u < nz) {
+                const int xo = int(u % w);
+                const int64_t q = u / w;
+                const int64_t row = q % rows;
+                const int p = int(q / rows);
+                const int x = x_lo + xo;
+                if (x == R && (a.pcls[p] & 1)) continue;  // a face unknown: computed below
+                const int y = int(row % (R + 1)), z = int(row / (R + 1));
+                a.y[size_t(p) * ps + size_t(uint32_t(z) * py) + uint32_t(y) * px + uint32_t(x)] = 0.0f;
+            } else {
+                const int64_t v = u - nz;
+                a.y[size_t(v / tail) * ps + box + uint32_t(v % tail)] = 0.0f;
             }
+        }
+    } else if (x_lo <= R) {
+        switch (blockIdx.y) {
+            case 1: face_class_items<N, 1, MODE>(a, t0, stride, rrun); break;
+            case 2: face_class_items<N, 3, MODE>(a, t0, stride, rrun); break;
+            case 3: face_class_items<N, 5, MODE>(a, t0, stride, rrun); break;
+            default: face_class_items<N, 7, MODE>(a, t0, stride, rrun); break;
         }
     }
     if (MODE == OP_RESIDUAL && a.partials != nullptr) {
@@ -581,10 +582,15 @@ constexpr int kTY = 4;
 
 int face_grid_x(const pn_handle* h) {
     const int64_t rows = int64_t(h->R + 1) * (h->R + 1);
-    return int((rows + 255) / 256);
+    const int64_t w = std::max<int64_t>(0, h->pitch_x - std::min<int64_t>(h->pitch_x,
+                                                                          int64_t((h->R + tiled::TX - 1) / tiled::TX) *
+                                                                              tiled::TX));
+    const int64_t tail = h->plane_stride - h->pitch_y * (h->R + 1);
+    const int64_t items = std::max(int64_t(h->K) * (rows * w + tail), int64_t(tiled::MAXC) * rows);
+    return int(std::max<int64_t>(1, std::min<int64_t>(4 * pn_sm_count(), (items + 255) / 256)));
 }
 
-int face_blocks(const pn_handle* h) { return face_grid_x(h) * 9; }
+int face_blocks(const pn_handle* h) { return face_grid_x(h) * 5; }
 
 template <int N, int MODE>
 cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& p, cudaStream_t s) {
@@ -601,7 +607,7 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
     // columns right of the tiles and plane tails
     tiled::Args af = a;
     if (af.partials) af.partials += p.grid.x * p.grid.y * p.grid.z;
-    tiled::k_face_x<N, MODE><<<dim3(face_grid_x(h), 9), 256, 0, s>>>(af, p.x_end);
+    tiled::k_face_x<N, MODE><<<dim3(face_grid_x(h), 5), 256, 0, s>>>(af, p.x_end);
     return cudaGetLastError();
 }
 

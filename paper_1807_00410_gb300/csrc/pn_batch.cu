@@ -35,7 +35,6 @@ namespace {
 
 constexpr int BM_MAX = 16;         // restart length limit (projections + |w|^2 in one pass)
 constexpr int NV1 = BM_MAX + 1;    // values per vector chunk partial (slot BM_MAX: |w|^2)
-constexpr int kRun = 8;            // float4 products summed in FP32 before each FP64 add
 
 struct BInst {
     // operator (from the handle)
@@ -193,69 +192,65 @@ __global__ void __launch_bounds__(256) kb_op(const BInst* __restrict__ I, const 
     ph_op<T, MODE>(I, st, ch, nch, cho, X, Y, Bv, gate, partials, blockIdx.x, gridDim.x);
 }
 
-// Sums NV1 per-thread values over the block into out[0..NV1) (nv projections
-// in slots 0..nv-1, the self-dot in slot BM_MAX).
-__device__ __forceinline__ void block_sum_nv(const double (&acc)[NV1], int nv, double* out) {
-    __shared__ double red[NV1][256];
-#pragma unroll
-    for (int j = 0; j < NV1; ++j) red[j][threadIdx.x] = acc[j];
-    __syncthreads();
+// Sums NV1 per-thread FP32 values over the block into out[0..NV1) (nv
+// projections in slots 0..nv-1, the self-dot in slot BM_MAX): each warp adds
+// its 32 values in FP32, the 8 warp sums are added in FP64.
+__device__ __forceinline__ void block_sum_nv(const float (&part)[NV1], int nv, double* out) {
+    __shared__ double red[NV1][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = warp; v <= nv; v += 8) {
-        const int j = v < nv ? v : BM_MAX;
-        double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t += red[j][lane + 32 * q];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) out[j] = t;
+    for (int v = 0; v < NV1; ++v) {
+        if (v < nv || v == BM_MAX) {
+            float t = part[v];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) red[v][warp] = double(t);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NV1 && (int(threadIdx.x) < nv || threadIdx.x == BM_MAX)) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[threadIdx.x][q];
+        out[threadIdx.x] = t;
     }
     __syncthreads();
 }
 
 // partials[c][v] = chunk c's share of V_v . w (v <= j) and w . w (slot BM_MAX),
-// w = V_{j+1}, for live instances.
+// w = V_{j+1}, for live instances (products summed per thread in FP32).
 __device__ __forceinline__ void ph_mdot(const BInst* __restrict__ I, const BState* st,
-                                               const VecChunk* __restrict__ ch, int nch, int64_t chv, int j,
-                                               double* partials, int cta, int ncta) {
+                                        const VecChunk* __restrict__ ch, int nch, int64_t chv, int j,
+                                        double* partials, int cta, int ncta) {
     const int nv = j + 1;
     for (int c = cta; c < nch; c += ncta) {
         const VecChunk k = ch[c];
-        double acc[NV1];
+        float part[NV1];
 #pragma unroll
-        for (int v = 0; v < NV1; ++v) acc[v] = 0.0;
+        for (int v = 0; v < NV1; ++v) part[v] = 0.0f;
         if (st[k.inst].live) {
             const BInst& in = I[k.inst];
             const int64_t n4 = in.n / 4;
             const float4* V = reinterpret_cast<const float4*>(in.V);
             const float4* w = V + int64_t(nv) * n4;
             const int64_t i0 = k.e0 / 4, i1 = min(i0 + chv / 4, n4);
-            int64_t i = i0 + threadIdx.x;
-            while (i < i1) {
-                float part[NV1];
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const float4 wi = w[i];
 #pragma unroll
-                for (int v = 0; v < NV1; ++v) part[v] = 0.0f;
-                for (int r = 0; r < kRun && i < i1; ++r, i += blockDim.x) {
-                    const float4 wi = w[i];
-#pragma unroll
-                    for (int v = 0; v < BM_MAX; ++v) {
-                        if (v < nv) {
-                            const float4 q = V[int64_t(v) * n4 + i];
-                            part[v] = fmaf(q.w, wi.w, fmaf(q.z, wi.z, fmaf(q.y, wi.y, fmaf(q.x, wi.x, part[v]))));
-                        }
+                for (int v = 0; v < BM_MAX; ++v) {
+                    if (v < nv) {
+                        const float4 q = V[int64_t(v) * n4 + i];
+                        part[v] = fmaf(q.w, wi.w, fmaf(q.z, wi.z, fmaf(q.y, wi.y, fmaf(q.x, wi.x, part[v]))));
                     }
-                    part[BM_MAX] = fmaf(wi.w, wi.w, fmaf(wi.z, wi.z, fmaf(wi.y, wi.y, fmaf(wi.x, wi.x, part[BM_MAX]))));
                 }
-#pragma unroll
-                for (int v = 0; v < NV1; ++v) acc[v] += double(part[v]);
+                part[BM_MAX] = fmaf(wi.w, wi.w, fmaf(wi.z, wi.z, fmaf(wi.y, wi.y, fmaf(wi.x, wi.x, part[BM_MAX]))));
             }
         }
-        block_sum_nv(acc, nv, partials + int64_t(c) * NV1);
+        block_sum_nv(part, nv, partials + int64_t(c) * NV1);
     }
 }
 
 __global__ void __launch_bounds__(256) kb_mdot(const BInst* __restrict__ I, const BState* st,
                                                const VecChunk* __restrict__ ch, int nch, int64_t chv, int j,
-                                               double* partials)  {
+                                               double* partials) {
     ph_mdot(I, st, ch, nch, chv, j, partials, blockIdx.x, gridDim.x);
 }
 

@@ -393,9 +393,37 @@ __global__ void k_gm_init(double* g, int m, double* S) {
     S[S_RES] = beta;
 }
 
-// Solve the k x k upper-triangular system H y = g (FP64, one thread).
+// Solve the k x k upper-triangular system H y = g in FP64 (k <= 200).  One
+// block: the threads copy the triangle and g into shared memory when it fits
+// (k <= 64), then thread 0 substitutes from there (a one-thread solve
+// straight from global memory waits on a dependent load chain).
 __global__ void k_gm_backsolve(const double* H, int ldh, const double* g, double* y, int k) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    constexpr int KS = 64;
+    __shared__ double hs[KS * (KS + 1) / 2];
+    __shared__ double gs[KS];
+    __shared__ double ys[KS];
+    if (k <= KS) {
+        // column c of the triangle (rows 0..c) at hs[c (c + 1) / 2 + row]
+        for (int e = threadIdx.x; e < k * (k + 1) / 2; e += blockDim.x) {
+            int c = int((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+            while (c * (c + 1) / 2 > e) --c;
+            while ((c + 1) * (c + 2) / 2 <= e) ++c;
+            const int row = e - c * (c + 1) / 2;
+            hs[e] = H[int64_t(c) * ldh + row];
+        }
+        for (int i = threadIdx.x; i < k; i += blockDim.x) gs[i] = g[i];
+        __syncthreads();
+        if (threadIdx.x != 0) return;
+        for (int i = k - 1; i >= 0; --i) {
+            double t = gs[i];
+            for (int c = i + 1; c < k; ++c) t -= hs[c * (c + 1) / 2 + i] * ys[c];
+            const double d = hs[i * (i + 1) / 2 + i];
+            ys[i] = d != 0.0 ? t / d : 0.0;
+        }
+        for (int i = 0; i < k; ++i) y[i] = ys[i];
+        return;
+    }
+    if (threadIdx.x != 0) return;
     for (int i = k - 1; i >= 0; --i) {
         double t = g[i];
         for (int c = i + 1; c < k; ++c) t -= H[int64_t(c) * ldh + i] * y[c];
@@ -842,7 +870,7 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
             }
         }
         c.pb();
-        k_gm_backsolve<<<1, 32, 0, c.s>>>(H, ldh, g, y, j);
+        k_gm_backsolve<<<1, 128, 0, c.s>>>(H, ldh, g, y, j);
         k_update16<<<nb, 256, 0, c.s>>>(n8, (float4*)x, (const uint4*)V16, vs8, j, y, inv_sigma);
         c.launched("gmres16: update", 2);
         c.pe(PN_PROF_MAXPY, double(h->n_active) * (8.0 + 2.0 * j));
@@ -1028,7 +1056,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
         }
         // x += V y
         c.pb();
-        k_gm_backsolve<<<1, 32, 0, c.s>>>(H, ldh, g, y, j);
+        k_gm_backsolve<<<1, 128, 0, c.s>>>(H, ldh, g, y, j);
         c.launched("gmres: backsolve");
         c.pe(PN_PROF_SCALAR, 0.0);
         const T* basis = net ? Zb : V;  // x += Z y (flexible) or V y
