@@ -490,8 +490,14 @@ __device__ __forceinline__ void face_class_items(const Args& a, int64_t t0, int6
 // blockIdx.y = 0 writes 0 to every other such slot and to the plane tails,
 // one slot per thread; blockIdx.y = 1..4 computes the x = R outputs of face
 // class 1, 3, 5, 7, one (row, plane) per thread.
+// Block ranges of the face kernel's tasks in one 1D grid: [b[0], b[1]) writes
+// the zeros, [b[k], b[k+1]) computes face class 2k - 1 (k = 1..4).
+struct FaceRanges {
+    int b[6];
+};
+
 template <int N, int MODE>
-__global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
+__global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr) {
     if (a.live && !*a.live) return;  // uniform over the grid
     constexpr Tab T = TabN<N>::value;
     constexpr int K = T.K;
@@ -502,10 +508,12 @@ __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
     const int w = a.pitch_x - x_lo;
     const uint32_t box = py * uint32_t(R + 1);
     const uint32_t tail = ps - box;
-    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int task = 0;
+    while (task < 4 && int(blockIdx.x) >= fr.b[task + 1]) ++task;
+    const int64_t t0 = int64_t(int(blockIdx.x) - fr.b[task]) * blockDim.x + threadIdx.x;
+    const int64_t stride = int64_t(fr.b[task + 1] - fr.b[task]) * blockDim.x;
     float rrun = 0.0f;
-    if (blockIdx.y == 0) {
+    if (task == 0) {
         const int64_t nz = w > 0 ? int64_t(K) * rows * w : 0;
         for (int64_t u = t0; u < nz + int64_t(K) * tail; u += stride) {
             if (u < nz) {
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
             }
         }
     } else if (x_lo <= R) {
-        switch (blockIdx.y) {
+        switch (task) {
             case 1: face_class_items<N, 1, MODE>(a, t0, stride, rrun); break;
             case 2: face_class_items<N, 3, MODE>(a, t0, stride, rrun); break;
             case 3: face_class_items<N, 5, MODE>(a, t0, stride, rrun); break;
@@ -539,7 +547,7 @@ __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo) {
         if (threadIdx.x == 0) {
             double tsum = 0.0;
             for (int i = 0; i < 8; ++i) tsum += red[i];
-            a.partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = tsum;
+            a.partials[blockIdx.x] = tsum;
         }
     }
 }
@@ -580,17 +588,30 @@ TiledPlan plan_for(const pn_handle* h) {
 
 constexpr int kTY = 4;
 
-int face_grid_x(const pn_handle* h) {
+// Block ranges of the face kernel: enough blocks for each task (one item per
+// thread), capped at 4 per SM for the zeros (grid-stride beyond).
+tiled::FaceRanges face_ranges(const pn_handle* h) {
     const int64_t rows = int64_t(h->R + 1) * (h->R + 1);
-    const int64_t w = std::max<int64_t>(0, h->pitch_x - std::min<int64_t>(h->pitch_x,
-                                                                          int64_t((h->R + tiled::TX - 1) / tiled::TX) *
-                                                                              tiled::TX));
+    const int64_t x_lo = std::min<int64_t>(h->pitch_x, int64_t((h->R + tiled::TX - 1) / tiled::TX) * tiled::TX);
+    const int64_t w = h->pitch_x - x_lo;
     const int64_t tail = h->plane_stride - h->pitch_y * (h->R + 1);
-    const int64_t items = std::max(int64_t(h->K) * (rows * w + tail), int64_t(tiled::MAXC) * rows);
-    return int(std::max<int64_t>(1, std::min<int64_t>(4 * pn_sm_count(), (items + 255) / 256)));
+    auto blocks = [](int64_t items, int64_t cap) {
+        return int(std::max<int64_t>(1, std::min<int64_t>(cap, (items + 255) / 256)));
+    };
+    int ncls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = 0; p < h->K; ++p) ++ncls[h->plane_class[p]];
+    tiled::FaceRanges fr{};
+    fr.b[0] = 0;
+    fr.b[1] = blocks(int64_t(h->K) * (rows * w + tail), 4 * int64_t(pn_sm_count()));
+    for (int k = 1; k <= 4; ++k) {
+        const int c = 2 * k - 1;
+        const int nb = (x_lo <= h->R && ncls[c] > 0) ? blocks(rows * ncls[c], 4 * int64_t(pn_sm_count())) : 0;
+        fr.b[k + 1] = fr.b[k] + nb;
+    }
+    return fr;
 }
 
-int face_blocks(const pn_handle* h) { return face_grid_x(h) * 5; }
+int face_blocks(const pn_handle* h) { return face_ranges(h).b[5]; }
 
 template <int N, int MODE>
 cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& p, cudaStream_t s) {
@@ -607,7 +628,8 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
     // columns right of the tiles and plane tails
     tiled::Args af = a;
     if (af.partials) af.partials += p.grid.x * p.grid.y * p.grid.z;
-    tiled::k_face_x<N, MODE><<<dim3(face_grid_x(h), 5), 256, 0, s>>>(af, p.x_end);
+    const tiled::FaceRanges fr = face_ranges(h);
+    tiled::k_face_x<N, MODE><<<fr.b[5], 256, 0, s>>>(af, p.x_end, fr);
     return cudaGetLastError();
 }
 
