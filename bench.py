@@ -41,11 +41,12 @@ L2_FLUSH_BYTES = 512 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel class and
 # workload; None until a capture of the current kernel exists.
 # DRAM traffic of the dominant kernel from one ncu capture of the current
-# kernel (profiles/k_mdot_givens_f32_p5_64_ir_solve.md): dram bytes read +
-# written over the algorithmic bytes of the same launch.  Launches differ in
-# the number of basis vectors, so the ratio is applied to this run's average
-# algorithmic bytes per launch.  Set to {} when the kernel changes.
-NCU_TRAFFIC = {("mdot", "p5_64", "f32"): 1.083}
+# kernel (profiles/k_mdot_givens_f32_p5_64_ir_solve.md,
+# profiles/k_maxpy16_p5_64_ir_solve.md): dram bytes read + written over the
+# algorithmic bytes of the same launches.  Launches differ in the number of
+# basis vectors, so the mean ratio is applied to this run's average
+# algorithmic bytes per launch.  An entry is removed when its kernel changes.
+NCU_TRAFFIC = {("mdot", "p5_64", "f32"): 1.083, ("maxpy", "p5_64", "f16"): 0.911}
 
 
 def parse():
@@ -76,6 +77,11 @@ def parse():
     ap.add_argument("--batch-seed", type=int, default=0)
     ap.add_argument("--batch-rmin", type=int, default=24)
     ap.add_argument("--batch-rmax", type=int, default=96)
+    ap.add_argument("--large-solve", action="store_true",
+                    help="the P7 256^3 cloud (1.08 G unknowns) solved by FP16-basis refinement, capped at "
+                         "--large-iters inner iterations: time per iteration and the residual reached")
+    ap.add_argument("--large-iters", type=int, default=600)
+    ap.add_argument("--large-sigma-min", type=float, default=0.1)
     ap.add_argument("--apply-n", type=int, default=7)
     ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
@@ -664,8 +670,45 @@ def run_batched(args):
         s.close()
 
 
+def run_large_solve(args):
+    """Full-size solve on the P7 256^3 thresholded-fBm cloud (albedo 0.99,
+    g 0.6, sigma_t_min --large-sigma-min, seeded point source): IR with FP32
+    GMRES(15), FP16-stored basis, capped at --large-iters inner iterations;
+    CUDA events around the solve."""
+    import torch
+
+    import pn_inputs
+    from paper_1807_00410_gb300 import System
+    torch.cuda.set_device(0)
+    hbm_peak, peak_src = peaks()
+    p = pn_inputs.cloud_point(7, 256, 0, sigma_t_min=args.large_sigma_min)
+    sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=args.large_sigma_min)
+    tiling = sysm.tune_apply()
+    u = sysm.zeros(torch.float64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = sysm.solve(u, solver="ir", tol=1e-6, restart=15, ortho="cgs1", basis="f16", max_iter=args.large_iters,
+                    raise_on_error=False)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    dof = sysm.layout.n_active
+    print(json.dumps({"mode": "large-solve", "workload": f"P7 256^3 thresholded-fBm cloud, sigma_t_min "
+                      f"{args.large_sigma_min}, albedo 0.99, g 0.6, point source; FP32 GMRES(15), FP16 basis, "
+                      "FP64 IR", "dof": dof, "ms": ms, "iterations": st["iterations"],
+                      "outer_iterations": st["outer_iterations"], "rel_residual": st["rel_residual"],
+                      "status": st["status"], "ms_per_iteration": ms / max(1, st["iterations"]),
+                      "gdof_iterations_per_s": dof * st["iterations"] / (ms * 1e-3) / 1e9,
+                      "apply_ctas_per_sm": tiling["ctas_per_sm"]}), flush=True)
+    sysm.close()
+
+
 def main():
     args = parse()
+    if args.large_solve:
+        run_large_solve(args)
+        return
     if args.batched:
         run_batched(args)
         return

@@ -714,36 +714,64 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
 }
 
 // w' = (w - sum_{i < nv} add[i] V16_i / sigma) * S[S_SCALE];
-// V16_out = fp16(sigma w'), vcur = w'.
-__global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* w, const uint4* V16, int64_t vstride8,
-                                                 int nv, const double* add, float inv_sigma, float sigma,
-                                                 const double* S, uint4* V16_out, float4* vcur) {
+// V16_out = fp16(sigma w'), vcur = w'.  Each thread loads two 8-element groups
+// before combining either (launched with 8 CTAs per SM).  V16_out is basis
+// vector nv, which no thread reads here (the restrict qualifiers say so).
+__global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* __restrict__ w,
+                                                 const uint4* __restrict__ V16, int64_t vstride8, int nv,
+                                                 const double* add, float inv_sigma, float sigma, const double* S,
+                                                 uint4* __restrict__ V16_out, float4* __restrict__ vcur) {
     constexpr int NV = PN_MAX_MDOT;
     float cj[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
     const float sc = float(S[S_SCALE]);
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += int64_t(gridDim.x) * blockDim.x) {
-        const float4 wa = w[2 * i], wb = w[2 * i + 1];
-        float acc[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += 2 * stride) {
+        const int64_t i2 = i + stride;
+        const bool two = i2 < n8;
+        float acc[2][8];
+        {
+            const float4 a = w[2 * i], b = w[2 * i + 1];
+            const float4 c = two ? w[2 * i2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 d = two ? w[2 * i2 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float t0[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const float t1[8] = {c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[0][k] = t0[k];
+                acc[1][k] = t1[k];
+            }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             if (v < nv) {
-                float q[8];
-                h8_to_f(V16[v * vstride8 + i], q);
+                const uint4 u0 = V16[v * vstride8 + i];
+                const uint4 u1 = two ? V16[v * vstride8 + i2] : make_uint4(0u, 0u, 0u, 0u);
+                float q0[8], q1[8];
+                h8_to_f(u0, q0);
+                h8_to_f(u1, q1);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = fmaf(cj[v], q[k], acc[k]);
+                for (int k = 0; k < 8; ++k) {
+                    acc[0][k] = fmaf(cj[v], q0[k], acc[0][k]);
+                    acc[1][k] = fmaf(cj[v], q1[k], acc[1][k]);
+                }
             }
         }
-        float hs[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            acc[k] *= sc;
-            hs[k] = acc[k] * sigma;
+        for (int g = 0; g < 2; ++g) {
+            if (g == 1 && !two) break;
+            const int64_t ii = g == 0 ? i : i2;
+            float hs[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[g][k] *= sc;
+                hs[k] = acc[g][k] * sigma;
+            }
+            V16_out[ii] = f_to_h8(hs);
+            vcur[2 * ii] = make_float4(acc[g][0], acc[g][1], acc[g][2], acc[g][3]);
+            vcur[2 * ii + 1] = make_float4(acc[g][4], acc[g][5], acc[g][6], acc[g][7]);
         }
-        V16_out[i] = f_to_h8(hs);
-        vcur[2 * i] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        vcur[2 * i + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
     }
 }
 
@@ -764,27 +792,51 @@ __global__ void __launch_bounds__(256) k_first16(int64_t n8, const float4* r, fl
     }
 }
 
-// x += sum_{i < nv} y_i V16_i / sigma.
-__global__ void __launch_bounds__(256) k_update16(int64_t n8, float4* x, const uint4* V16, int64_t vstride8, int nv,
-                                                  const double* y, float inv_sigma) {
+// x += sum_{i < nv} y_i V16_i / sigma (two 8-element groups loaded per iteration).
+__global__ void __launch_bounds__(256) k_update16(int64_t n8, float4* __restrict__ x, const uint4* __restrict__ V16,
+                                                  int64_t vstride8, int nv, const double* y, float inv_sigma) {
     constexpr int NV = PN_MAX_MDOT;
     float yj[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) yj[v] = v < nv ? float(y[v]) * inv_sigma : 0.0f;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += int64_t(gridDim.x) * blockDim.x) {
-        const float4 a = x[2 * i], b = x[2 * i + 1];
-        float acc[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += 2 * stride) {
+        const int64_t i2 = i + stride;
+        const bool two = i2 < n8;
+        float acc[2][8];
+        {
+            const float4 a = x[2 * i], b = x[2 * i + 1];
+            const float4 c = two ? x[2 * i2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 d = two ? x[2 * i2 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float t0[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const float t1[8] = {c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[0][k] = t0[k];
+                acc[1][k] = t1[k];
+            }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             if (v < nv) {
-                float q[8];
-                h8_to_f(V16[v * vstride8 + i], q);
+                const uint4 u0 = V16[v * vstride8 + i];
+                const uint4 u1 = two ? V16[v * vstride8 + i2] : make_uint4(0u, 0u, 0u, 0u);
+                float q0[8], q1[8];
+                h8_to_f(u0, q0);
+                h8_to_f(u1, q1);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = fmaf(yj[v], q[k], acc[k]);
+                for (int k = 0; k < 8; ++k) {
+                    acc[0][k] = fmaf(yj[v], q0[k], acc[0][k]);
+                    acc[1][k] = fmaf(yj[v], q1[k], acc[1][k]);
+                }
             }
         }
-        x[2 * i] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        x[2 * i + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        x[2 * i] = make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+        x[2 * i + 1] = make_float4(acc[0][4], acc[0][5], acc[0][6], acc[0][7]);
+        if (two) {
+            x[2 * i2] = make_float4(acc[1][0], acc[1][1], acc[1][2], acc[1][3]);
+            x[2 * i2 + 1] = make_float4(acc[1][4], acc[1][5], acc[1][6], acc[1][7]);
+        }
     }
 }
 
@@ -795,7 +847,7 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
     pn_handle* h = c.h;
     const int64_t n = h->n_elems;  // a multiple of 32
     const int64_t n8 = n / 8;
-    const int nb = nb_vec();
+    const int nb = 8 * pn_sm_count();  // the FP16-basis streaming kernels: 8 CTAs per SM
     double* S = h->d_scalars;
     const float sigma = float(std::sqrt(double(h->n_active)));
     const float inv_sigma = 1.0f / sigma;

@@ -2,26 +2,29 @@
 the paper's solver; the paper has no network).
 
 The preconditioner is M(v) = s net(features(v / s)) + P v with s the RMS of
-v over the unknowns and P = diag(1 / (D + 1/h)) (pn_cnn_output).  FGMRES
-applies M to Krylov vectors, so the network is trained on the residual loss
+v over the unknowns and P = diag(1 / (D + 1/h)) (pn_cnn_output).  Three
+training modes, every step in the library's kernels (pn_cnn_forward,
+pn_cnn_backward, pn_cnn_adam_step, pn_cnn_train_step, pn_apply, pn_apply_t):
 
-    L(r) = |A M(r) - r|^2 / |r|^2
-
-over vectors r that look like those: the sources themselves (point sources
-and collimated-beam single-scatter sources), residuals Q - A x_k of partial
-GMRES solves (k iterations), normalised Krylov powers A^j Q, and random
-combinations of these for the same medium.  Its gradient with respect to the
-network output is s gather(2 A^T (A M(r) - r)) / |r|^2, computed with the
-library's own operator and transpose (pn_apply, pn_apply_t, pn_cnn_targets
-as the gather); forward, backward and Adam run in the library's kernels
-(pn_cnn_forward, pn_cnn_backward, pn_cnn_adam_step).
+* hard (default): supervised pairs (r_k, e_k) where r_k is the residual that
+  plain GMRES(15) leaves after k = 0, 1, 3, 6, 10, 20 restart cycles from zero
+  and e_k = x* - x_k its exact error (x* solved to 1e-8): the components a
+  restarted Krylov method converges slowly on, with targets (e - P r) / s;
+* residual: the loss |A M(r) - r|^2 / |r|^2 over residual pools (sources,
+  partial-solve residuals, Krylov powers A^j Q, random combinations, and
+  optionally the residuals FGMRES with the current network leaves), its
+  gradient s gather(2 A^T (A M(r) - r)) / |r|^2 through the library's
+  operator and transpose;
+* supervised: exact solutions of solved sources and their combinations.
 
 Media are seeded value-noise fBm extinction fields with albedo and g drawn
 per medium.  The discrete P_N system in cell units depends only on
 sigma_t h, albedo and g, so media for a grid of R cells are drawn with
 sigma_t in [lo, hi] * R / 64 to match the optical thickness per cell of the
 64^3 workload; the network (fully convolutional, fed log(sigma_t h)) is
-trained on small grids and applied to 64^3 ones.
+trained on small grids and applied to 64^3 ones.  `compare` times flexible
+GMRES with the network against plain GMRES, both inside FP64 refinement, on
+held-out media.
 
 Usage:
     python -m paper_1807_00410_gb300.learned train --out weights.npy

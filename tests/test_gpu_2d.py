@@ -123,3 +123,18 @@ def test_2d_handle_refuses_3d_only_calls():
         gpu.solve(gpu.zeros(torch.float64), solver="ir_fgmres", precond=net)
     net.close()
     gpu.close()
+
+
+def test_2d_fp16_basis_refinement_meets_oracle():
+    """The FP16-stored Krylov basis on a 2D handle (the generic FP32 operator)."""
+    from paper_1807_00410_gb300 import System
+    N, R = 5, 40
+    st, al, g, q = _medium(R, 9)
+    lay, A, b = pn2d.assemble_2d(N, R, st, al, g, q)
+    gpu = System(N, R, st, al, g, q, dims=2)
+    u = gpu.zeros(torch.float64)
+    s = gpu.solve(u, solver="ir", tol=1e-8, restart=15, ortho="cgs1", basis="f16")
+    assert s["rel_residual"] <= 1e-8
+    uh = lay.join(gpu.to_planes(u))
+    assert np.linalg.norm(b - A @ uh) / np.linalg.norm(b) <= 1.0001e-8
+    gpu.close()
