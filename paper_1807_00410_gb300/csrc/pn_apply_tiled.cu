@@ -155,7 +155,7 @@ template <int N, int TY, int C, int MODE>
 __device__ __forceinline__ void compute_class(const Args& a, const float* buf, int tx, int ty, bool store_ok,
                                               bool active, size_t outoff, const float (&own)[MAXC],
                                               const float (&zp)[MAXC], const float (&zm)[MAXC], float st, float ss,
-                                              float& rrun) {
+                                              const float (&rhs)[MAXC], float& rrun) {
     constexpr Tab T = TabN<N>::value;
     constexpr ClassTab CT = T.cls[C];
     constexpr int bx = C & 1, by = (C >> 1) & 1;
@@ -198,13 +198,18 @@ __device__ __forceinline__ void compute_class(const Args& a, const float* buf, i
             const float d = fmaf(-a.fl[CT.row[i].l], ss, st);
             float out = fmaf(d, own[i], tscale * tr);
             if (MODE == OP_RESIDUAL) {
-                // right-hand side, read only at active slots (inside the plane box)
-                float b = 0.0f;
-                if (active) {
-                    if (a.bvec) b = __ldg(a.bvec + size_t(CT.plane0) * ps + outoff + uint32_t(i) * ps);
-                    else if (CT.plane0 + i < a.n_q) b = __ldg(a.q + size_t(CT.plane0) * ps + outoff + uint32_t(i) * ps);
+                if (N <= 6) {
+                    out = rhs[i] - out;  // loaded at the start of the step
+                } else {
+                    // P7 has no registers to spare for the early loads: read here
+                    float b = 0.0f;
+                    if (active) {
+                        if (a.bvec) b = __ldg(a.bvec + size_t(CT.plane0) * ps + outoff + uint32_t(i) * ps);
+                        else if (CT.plane0 + i < a.n_q)
+                            b = __ldg(a.q + size_t(CT.plane0) * ps + outoff + uint32_t(i) * ps);
+                    }
+                    out = b - out;
                 }
-                out = b - out;
             }
             out = active ? out : 0.0f;
             if (MODE == OP_RESIDUAL) rrun = fmaf(out, out, rrun);
@@ -220,6 +225,22 @@ __device__ __forceinline__ float xy_mean(const float* g, int tx, int ty, int bx,
     const int gx1 = tx + 1, gy1 = ty + 1;
     const int gx0 = bx ? tx : gx1, gy0 = by ? ty : gy1;
     return 0.25f * (g[gy0 * G::GX + gx0] + g[gy0 * G::GX + gx1] + g[gy1 * G::GX + gx0] + g[gy1 * G::GX + gx1]);
+}
+
+// Right-hand side of one class at slot s of this thread's column (residual
+// mode): the full vector bvec, or Q (planes beyond n_q are 0); read only at
+// active slots.  Issued at the start of a z-step so that the step's staging,
+// barrier and arithmetic hide the load latency.
+template <int N, int C>
+__device__ __forceinline__ void load_rhs(const Args& a, bool act, uint32_t col, int s, float (&r)[MAXC]) {
+    constexpr ClassTab CT = TabN<N>::value.cls[C];
+    const uint32_t ps = a.plane_stride;
+    const float* base = a.bvec ? a.bvec : a.q;
+    const int nq = a.bvec ? 64 : a.n_q;
+    const size_t off = size_t(CT.plane0) * ps + size_t(uint32_t(s) * a.pitch_y) + col;
+#pragma unroll
+    for (int i = 0; i < MAXC; ++i)
+        if (i < CT.n) r[i] = (act && CT.plane0 + i < nq) ? __ldg(base + off + uint32_t(i) * ps) : 0.0f;
 }
 
 template <int N, int TY, int GRP, int MODE>
@@ -318,6 +339,11 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
     for (int s = za; s < zb; ++s) {
         float* b = buf + (s & 1) * K * G::SLICE;
         float* g = sg + (s & 1) * 2 * G::GSL;
+        float rhs0[MAXC], rhs1[MAXC];
+        if (MODE == OP_RESIDUAL && N <= 6) {
+            load_rhs<N, C0>(a, colact0 && s < R, col, s, rhs0);
+            load_rhs<N, C1>(a, colact1, col, s, rhs1);
+        }
         // stage slice s: own values, halo, sigma
         const int sidx = (ty + 1) * G::SX + (tx + 1);
 #pragma unroll
@@ -342,10 +368,10 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
         const size_t outoff = size_t(uint32_t(s) * py) + col;
         // even class (bz = 0): z-neighbours are the odd class at s+1 (plus) and s (minus)
         compute_class<N, TY, C0, MODE>(a, b, tx, ty, store_ok, colact0 && s < R, outoff, v0c, v1n, v1c, mt, ms,
-                                       rrun);
+                                       rhs0, rrun);
         // odd class (bz = 1): z-neighbours are the even class at s (plus) and s-1 (minus)
         compute_class<N, TY, C1, MODE>(a, b, tx, ty, store_ok, colact1, outoff, v1c, v0c, v0p,
-                                       0.5f * (mt + mt_prev), 0.5f * (ms + ms_prev), rrun);
+                                       0.5f * (mt + mt_prev), 0.5f * (ms + ms_prev), rhs1, rrun);
         if (MODE == OP_RESIDUAL && ++rcnt == 4) {
             racc += double(rrun);
             rrun = 0.0f;
