@@ -103,6 +103,11 @@ void free_all(pn_handle* h) {
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     h->prof_ev.clear();
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
 }
 
 }  // namespace
@@ -338,6 +343,15 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
             e = cudaMemcpy(h->d_terms, h->terms.data(), h->terms.size() * sizeof(pn::Term), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             rc = pn_cuda_fail(nullptr, e, "pn_create: uploading tables");
+            goto fail;
+        }
+    }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            rc = pn_cuda_fail(nullptr, e, "pn_create: side stream");
             goto fail;
         }
     }

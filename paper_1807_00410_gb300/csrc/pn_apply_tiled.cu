@@ -648,15 +648,27 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
         if (e != cudaSuccess) return e;
         configured[N] = true;
     }
+    // columns right of the tiles and plane tails: disjoint outputs and partial
+    // slots, same inputs; on the handle's side stream, concurrently
+    cudaStream_t fs = h->side ? h->side : s;
+    cudaError_t e = cudaSuccess;
+    if (fs != s) {
+        e = cudaEventRecord(h->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, h->ev_fork, 0);
+        if (e != cudaSuccess) return e;
+    }
     kern<<<p.grid, p.block, p.smem, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // columns right of the tiles and plane tails
     tiled::Args af = a;
     if (af.partials) af.partials += p.grid.x * p.grid.y * p.grid.z;
     const tiled::FaceRanges fr = face_ranges(h);
-    tiled::k_face_x<N, MODE><<<fr.b[5], 256, 0, s>>>(af, p.x_end, fr);
-    return cudaGetLastError();
+    tiled::k_face_x<N, MODE><<<fr.b[5], 256, 0, fs>>>(af, p.x_end, fr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || fs == s) return e;
+    e = cudaEventRecord(h->ev_join, fs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
+    return e;
 }
 
 template <int MODE>

@@ -53,6 +53,10 @@ struct pn_handle {
     int N = 0, K = 0, R = 0;
     int dims = 3;        // 3: R^3 cells; 2: the z-independent reduction on R^2 cells
     int tile_ctas_per_sm = 4;  // z-chunking target of the tiled FP32 operator (pn_tune_apply)
+    // the face-column kernel of the tiled operator runs on a side stream,
+    // concurrently with the tiled kernel (fork / join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t nz_box = 0;  // z-slices of a plane box: R + 1 (3D) or 1 (2D)
     double h = 0.0;
     double g = 0.0;  // Henyey-Greenstein mean cosine
