@@ -42,11 +42,12 @@ L2_FLUSH_BYTES = 512 << 20
 # workload; None until a capture of the current kernel exists.
 # DRAM traffic of the dominant kernel from one ncu capture of the current
 # kernel (profiles/k_mdot_givens_f32_p5_64_ir_solve.md,
-# profiles/k_maxpy16_p5_64_ir_solve.md): dram bytes read + written over the
+# profiles/k_maxpy16_p5_64_ir_solve.md, profiles/k_mdot16_givens_p5_64_ir_solve.md):
+# dram bytes read + written over the
 # algorithmic bytes of the same launches.  Launches differ in the number of
 # basis vectors, so the mean ratio is applied to this run's average
 # algorithmic bytes per launch.  An entry is removed when its kernel changes.
-NCU_TRAFFIC = {("mdot", "p5_64", "f32"): 1.083, ("maxpy", "p5_64", "f16"): 0.911}
+NCU_TRAFFIC = {("mdot", "p5_64", "f32"): 1.083, ("maxpy", "p5_64", "f16"): 0.911, ("mdot", "p5_64", "f16"): 1.077}
 
 
 def parse():
