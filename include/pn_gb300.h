@@ -43,7 +43,8 @@
  * (class = p_x + 2 p_y + 4 p_z); planes are grouped by class.  Element
  * (z, y, x) of plane p is at
  *     p * plane_stride + z * pitch_y + y * pitch_x + x
- * and is an unknown ("active") iff x < R + p_x, y < R + p_y, z < R + p_z.
+ * and is an unknown ("active") iff x < R + p_x, y < R + p_y, z < R + p_z
+ * (PN_BC_PERIODIC_TEST: iff x, y, z < R).
  * Every other slot is padding: kernels never read it and write it as 0.
  * Query the numbers with pn_get_layout().  Element type: float (PN_F32) or
  * double (PN_F64); base pointers must be 16-byte aligned.
@@ -53,7 +54,8 @@
  * work vectors belong to the handle and are freed by pn_destroy.
  * Streams: every call is ordered on the caller's cudaStream_t (NULL = the
  * legacy default stream).  Calls that return a host scalar synchronise that
- * stream.  A handle must not be used from two host threads at once.
+ * stream.  A handle must not be used from two host threads at once (it owns
+ * a side stream and events that the FP32 operator forks to and joins from).
  * Errors: every call returns PN_OK (0) or a negative PN_ERR_* code and never
  * aborts; pn_last_error() gives a message for the handle's last failure.
  */
@@ -81,6 +83,10 @@ extern "C" {
 #define PN_F64 1
 
 #define PN_BC_VACUUM 0           /* Dirichlet: outside references dropped */
+#define PN_BC_PERIODIC_TEST 1    /* every axis wraps; R slots per axis for every coefficient (a test
+                                    mode for exact closed forms; 3D only; the generic operator
+                                    kernel serves it, FP32 included; unstagger and the learned
+                                    preconditioner refuse it) */
 
 #define PN_Q_CENTRE_00      0    /* Q: R^3 field of Q^{0,0} at voxel centres */
 #define PN_Q_CENTRE_MOMENTS 1    /* Q: K x R^3 centre moments, k-major */
@@ -119,7 +125,7 @@ typedef struct {
  * Create a handle for the P_N system of order N (1..7) on R^3 cells.
  * Copies and preprocesses the medium (clamp, sigma_s, Q in padded layout) into
  * device buffers owned by the handle.  Synchronises `stream` before returning.
- * boundary must be PN_BC_VACUUM.  On failure *out is NULL and the message is
+ * boundary is PN_BC_VACUUM or PN_BC_PERIODIC_TEST.  On failure *out is NULL and the message is
  * available from pn_last_error(NULL).
  */
 int pn_create(pn_handle** out, int N, int R, const pn_medium* medium, int boundary, void* stream);

@@ -73,7 +73,8 @@ int dev_alloc(pn_handle* h, T** p, size_t count, const char* what) {
 // Writes one padded plane from a voxel-centre field: every active slot gets
 // the mean of its adjacent in-domain centres, every other slot 0.
 __global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int64_t pitch_x,
-                             int64_t pitch_y, int64_t nzb, int64_t plane_stride, double* out_d, float* out_f) {
+                             int64_t pitch_y, int64_t nzb, int64_t plane_stride, int periodic, double* out_d,
+                             float* out_f) {
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < plane_stride;
          s += int64_t(gridDim.x) * blockDim.x) {
         const int x = int(s % pitch_x);
@@ -81,10 +82,20 @@ __global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int
         const int y = int(t % (R + 1));
         const int z = int(t / (R + 1));
         double v = 0.0;
-        if (s < pitch_y * nzb && x < R + px && y < R + py && z < R + pz) {
-            const int x0 = px ? max(x - 1, 0) : x, x1 = px ? min(x, R - 1) : x;
-            const int y0 = py ? max(y - 1, 0) : y, y1 = py ? min(y, R - 1) : y;
-            const int z0 = pz ? max(z - 1, 0) : z, z1 = pz ? min(z, R - 1) : z;
+        const int ext = periodic ? 0 : 1;
+        if (s < pitch_y * nzb && x < R + ext * px && y < R + ext * py && z < R + ext * pz) {
+            // in-domain centres adjacent to the slot (periodic: face i between centres i - 1 mod R and i)
+            int x0 = px ? max(x - 1, 0) : x, x1 = px ? min(x, R - 1) : x;
+            int y0 = py ? max(y - 1, 0) : y, y1 = py ? min(y, R - 1) : y;
+            int z0 = pz ? max(z - 1, 0) : z, z1 = pz ? min(z, R - 1) : z;
+            if (periodic) {
+                x0 = px ? (x + R - 1) % R : x;
+                y0 = py ? (y + R - 1) % R : y;
+                z0 = pz ? (z + R - 1) % R : z;
+                x1 = x;
+                y1 = y;
+                z1 = z;
+            }
             const int64_t R2 = int64_t(R) * R;
             v = 0.125 * (F[z0 * R2 + y0 * R + x0] + F[z0 * R2 + y0 * R + x1] + F[z0 * R2 + y1 * R + x0] +
                          F[z0 * R2 + y1 * R + x1] + F[z1 * R2 + y0 * R + x0] + F[z1 * R2 + y0 * R + x1] +
@@ -206,7 +217,10 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
                                                       : "pn_create_2d: R must be in [2, 16384]");
     if (!m || !m->sigma_t) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: medium or sigma_t is NULL");
     if (m->dtype != PN_F32 && m->dtype != PN_F64) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: bad medium dtype");
-    if (boundary != PN_BC_VACUUM) return pn_fail(nullptr, PN_ERR_UNSUPPORTED, "pn_create: only PN_BC_VACUUM is built");
+    if (boundary != PN_BC_VACUUM && boundary != PN_BC_PERIODIC_TEST)
+        return pn_fail(nullptr, PN_ERR_ARG, "pn_create: boundary must be PN_BC_VACUUM or PN_BC_PERIODIC_TEST");
+    if (boundary == PN_BC_PERIODIC_TEST && dims != 3)
+        return pn_fail(nullptr, PN_ERR_UNSUPPORTED, "pn_create_2d: the periodic test mode is 3D only");
     if (m->Q && m->q_mode != PN_Q_CENTRE_00 && m->q_mode != PN_Q_CENTRE_MOMENTS)
         return pn_fail(nullptr, PN_ERR_ARG, "pn_create: bad q_mode");
     if (!(std::fabs(m->g) < 1.0)) return pn_fail(nullptr, PN_ERR_ARG, "pn_create: |g| must be < 1");
@@ -218,6 +232,7 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
     cudaGetDevice(&h->device);
     h->N = N;
     h->dims = dims;
+    h->periodic = boundary == PN_BC_PERIODIC_TEST ? 1 : 0;
     h->R = R;
     h->h = 1.0 / R;
     h->g = m->g;
@@ -289,7 +304,8 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
             }
         P.t1 = int(h->terms.size());
         h->planes[q] = P;
-        h->n_active += int64_t(R + P.px) * (R + P.py) * (dims == 3 ? R + P.pz : 1);
+        const int ext = h->periodic ? 0 : 1;
+        h->n_active += int64_t(R + ext * P.px) * (R + ext * P.py) * (dims == 3 ? R + ext * P.pz : 1);
     }
 
     int rc = PN_OK;
@@ -392,7 +408,8 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
             }
             const pn::Plane& P = h->planes[q];
             k_fill_plane<<<8 * pn_sm_count(), 256, 0, s>>>(tmp, R, P.px, P.py, P.pz, h->pitch_x, h->pitch_y,
-                                                         h->nz_box, h->plane_stride, h->d_q_d + q * h->plane_stride,
+                                                         h->nz_box, h->plane_stride, h->periodic,
+                                                         h->d_q_d + q * h->plane_stride,
                                                          h->d_q_f + q * h->plane_stride);
             e = cudaStreamSynchronize(s);
             if (e == cudaSuccess) e = cudaGetLastError();

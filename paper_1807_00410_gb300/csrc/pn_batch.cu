@@ -40,7 +40,7 @@ struct BInst {
     // operator (from the handle)
     int R, K, n_q, nzb;
     int generic;     // 1: the Arnoldi-step operator runs in the generic batched launch
-    int pad_;
+    int periodic;    // the handle's periodic test mode
     int64_t pitch_x, pitch_y, plane_stride, n;
     const pn::Plane* planes;
     const pn::Term* terms;
@@ -144,6 +144,7 @@ __device__ __forceinline__ void ph_op(const BInst* __restrict__ I, const BState*
             a.terms = in.terms;
             a.R = in.R;
             a.nzb = in.nzb;
+            a.periodic = in.periodic;
             a.pitch_x = in.pitch_x;
             a.pitch_y = in.pitch_y;
             a.plane_stride = in.plane_stride;
@@ -160,7 +161,8 @@ __device__ __forceinline__ void ph_op(const BInst* __restrict__ I, const BState*
                 const int64_t t = s / in.pitch_x;
                 const int y = int(t % (R + 1));
                 const int z = int(t / (R + 1));
-                const bool active = s < box && x < R + P.px && y < R + P.py && z < R + P.pz;
+                const int ext = in.periodic ? 0 : 1;
+                const bool active = s < box && x < R + ext * P.px && y < R + ext * P.py && z < R + ext * P.pz;
                 T out = T(0);
                 if (active) {
                     out = pn::op_point<T, MODE>(a, k.plane, P, x, y, z, s);
@@ -290,7 +292,7 @@ __device__ __forceinline__ void ph_givens(const BInst* __restrict__ I, BState* s
     }
     // one Gram-Schmidt pass: |w - V h|^2 = |w|^2 - |h|^2 for orthonormal V
     double nrm2 = w2 - hh;
-    if (!(nrm2 > 1e-14 * w2)) nrm2 = 1e-14 * w2;
+    if (!(nrm2 > 1e-12 * w2)) nrm2 = 0.0;  // breakdown: the Krylov space is invariant
     const double hn = sqrt(fmax(nrm2, 0.0));
     col[j + 1] = hn;
     S.scale = hn > 0.0 ? 1.0 / hn : 0.0;
@@ -1010,7 +1012,7 @@ int pn_batch_create(pn_batch** out, pn_handle* const* handles, int count, int re
         in.K = h->K;
         in.n_q = h->n_q_planes;
         in.generic = pn::tiled_serves(h) ? 0 : 1;
-        in.pad_ = 0;
+        in.periodic = h->periodic;
         if (in.generic) ++b->n_generic;
         else ++b->n_tiled;
         in.nzb = int(h->nz_box);

@@ -52,6 +52,7 @@ int pn_sm_count();
 struct pn_handle {
     int N = 0, K = 0, R = 0;
     int dims = 3;        // 3: R^3 cells; 2: the z-independent reduction on R^2 cells
+    int periodic = 0;    // PN_BC_PERIODIC_TEST: every axis wraps, R slots per axis for every class
     int tile_ctas_per_sm = 4;  // z-chunking target of the tiled FP32 operator (pn_tune_apply)
     // the face-column kernel of the tiled operator runs on a side stream,
     // concurrently with the tiled kernel (fork / join events)

@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(256) k_op_naive(OpArgs<T> a) {
         const int64_t t = s / a.pitch_x;
         const int y = int(t % ny);
         const int z = int(t / ny);
-        const bool active = s < box && x < R + P.px && y < R + P.py && z < R + P.pz;
+        const int ext = a.periodic ? 0 : 1;  // periodic: R slots per axis for every class
+        const bool active = s < box && x < R + ext * P.px && y < R + ext * P.py && z < R + ext * P.pz;
         T out = T(0);
         if (active) {
             out = op_point<T, MODE>(a, p, P, x, y, z, s);
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256) k_op_slab(OpArgs<T> a, int x_lo) {
         const int z = int(u / (R + 1));
         const int64_t s = int64_t(z) * a.pitch_y + int64_t(y) * a.pitch_x + x;
         T out = T(0);
-        if (x < R + P.px && y < R + P.py && z < R + P.pz) {
+        if (!a.periodic && x < R + P.px && y < R + P.py && z < R + P.pz) {  // the slab path is never periodic
             out = op_point<T, MODE>(a, p, P, x, y, z, s);
             if (MODE == OP_RESIDUAL) racc += double(out) * double(out);
         }
@@ -124,7 +125,7 @@ static int slab_grid_x(const pn_handle* h) {
 static bool use_tiled(const pn_handle* h, int dtype) {
     // the tiled kernel (3D only) forms addresses with 32-bit element offsets
     // of up to 16 planes: it needs plane_stride * 16 < 2^32 (R <= 1000 or so)
-    return dtype == PN_F32 && h->dims == 3 && h->plane_stride * 16 < (int64_t(1) << 32);
+    return dtype == PN_F32 && h->dims == 3 && !h->periodic && h->plane_stride * 16 < (int64_t(1) << 32);
 }
 
 bool tiled_serves(const pn_handle* h) { return use_tiled(h, PN_F32); }
@@ -141,7 +142,7 @@ static cudaError_t op_t(const pn_handle* h, int mode, const T* x, T* y, const T*
     a.x = x; a.y = y; a.q = q; a.n_q = h->n_q_planes; a.bvec = bvec;
     a.st = st; a.ss = ss;
     a.planes = h->d_planes; a.terms = h->d_terms;
-    a.R = h->R; a.nzb = int(h->nz_box);
+    a.R = h->R; a.nzb = int(h->nz_box); a.periodic = h->periodic;
     a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
     a.partials = partials;
     dim3 grid(naive_grid_x(h), h->K);

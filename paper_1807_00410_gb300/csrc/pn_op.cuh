@@ -25,6 +25,7 @@ struct OpArgs {
     const Term* terms;
     int R;
     int nzb;           // z-slices of a plane box (R + 1; 1 for the 2D reduction)
+    int periodic;      // 1: every axis wraps, R slots per axis for every class (test mode)
     int64_t pitch_x, pitch_y, plane_stride;
     double* partials;  // residual: per-block sums of r^2
 };
@@ -52,6 +53,17 @@ __device__ __forceinline__ T centre_mean(const T* F, int R, int x, int y, int z,
     return s * T(0.125);
 }
 
+// The same with every axis wrapping (periodic test mode): face i lies
+// between centres i - 1 (mod R) and i.
+template <typename T>
+__device__ __forceinline__ T centre_mean_periodic(const T* F, int R, int x, int y, int z, int px, int py, int pz) {
+    const int x0 = px ? (x + R - 1) % R : x, y0 = py ? (y + R - 1) % R : y, z0 = pz ? (z + R - 1) % R : z;
+    const int64_t R2 = int64_t(R) * R;
+    T s = F[z0 * R2 + y0 * R + x0] + F[z0 * R2 + y0 * R + x] + F[z0 * R2 + y * R + x0] + F[z0 * R2 + y * R + x] +
+          F[z * R2 + y0 * R + x0] + F[z * R2 + y0 * R + x] + F[z * R2 + y * R + x0] + F[z * R2 + y * R + x];
+    return s * T(0.125);
+}
+
 // One output of the operator at slot (x, y, z) of plane p (active slot).  The
 // 2D reduction has no z terms, every plane has pz = 0 and z = 0, and its
 // centre fields are R^2: the same code serves it.
@@ -59,8 +71,10 @@ template <typename T, int MODE>
 __device__ __forceinline__ T op_point(const OpArgs<T>& a, int p, const Plane& P, int x, int y, int z, int64_t s) {
     const int R = a.R;
     const int64_t pbase = int64_t(p) * a.plane_stride;
-    const T diag = centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
-                   plane_fl<T>(P) * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
+    const T diag = a.periodic ? centre_mean_periodic(a.st, R, x, y, z, P.px, P.py, P.pz) -
+                                    plane_fl<T>(P) * centre_mean_periodic(a.ss, R, x, y, z, P.px, P.py, P.pz)
+                              : centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
+                                    plane_fl<T>(P) * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
     T acc = diag * a.x[pbase + s];
     T tr = T(0);
     for (int ti = P.t0; ti < P.t1; ++ti) {
@@ -72,9 +86,16 @@ __device__ __forceinline__ T op_point(const OpArgs<T>& a, int p, const Plane& P,
         else { i = z; b = P.pz; stride = a.pitch_y; }
         const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
         // plus neighbour at slot i + 1 - b (exists iff < R + 1 - b),
-        // minus neighbour at slot i - b (exists iff >= 0)
-        const T vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
-        const T vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
+        // minus neighbour at slot i - b (exists iff >= 0); periodic: both wrap mod R
+        T vp, vm;
+        if (a.periodic) {
+            const int ip = (i + 1 - b) % R, im = (i - b + R) % R;
+            vp = a.x[qb + (ip - i) * stride];
+            vm = a.x[qb + (im - i) * stride];
+        } else {
+            vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
+            vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
+        }
         tr += term_coef<T>(tm) * (vp - vm);
     }
     acc = (MODE == OP_APPLY_T) ? acc - tr : acc + tr;

@@ -180,7 +180,8 @@ extern "C" {
 
 int pn_cnn_features(pn_handle* h, const float* v, double scale, float* out, void* stream) {
     if (!h || !v || !out) return PN_ERR_ARG;
-    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_features: 3D handles only");
+    if (h->dims != 3 || h->periodic)
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_features: 3D vacuum-boundary handles only");
     const int64_t V = int64_t(h->R) * h->R * h->R;
     FeatArgs fa{v, nullptr, scale, h->d_st_f, h->d_ss_f, float(h->g), h->R, h->K, h->pitch_x, h->pitch_y,
                 h->plane_stride, out};
@@ -191,7 +192,8 @@ int pn_cnn_features(pn_handle* h, const float* v, double scale, float* out, void
 
 int pn_cnn_targets(pn_handle* h, const float* e, const float* r, double scale, float* out, void* stream) {
     if (!h || !e || !out) return PN_ERR_ARG;
-    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_targets: 3D handles only");
+    if (h->dims != 3 || h->periodic)
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_targets: 3D vacuum-boundary handles only");
     const int64_t V = int64_t(h->R) * h->R * h->R;
     k_targets<<<grid_for(V * h->K), 256, 0, (cudaStream_t)stream>>>(e, r, float(scale), h->d_planes, h->d_st_f,
                                                                       h->d_ss_f, h->R, h->K, h->pitch_x, h->pitch_y,
@@ -202,7 +204,8 @@ int pn_cnn_targets(pn_handle* h, const float* e, const float* r, double scale, f
 
 int pn_cnn_output(pn_handle* h, const float* net_out, double scale, const float* v, float* z, void* stream) {
     if (!h || !z) return PN_ERR_ARG;
-    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_output: 3D handles only");
+    if (h->dims != 3 || h->periodic)
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_output: 3D vacuum-boundary handles only");
     ScatterArgs sa{net_out, nullptr, scale, v, z, h->d_planes, h->d_st_f, h->d_ss_f, h->R, h->K, h->pitch_x,
                    h->pitch_y, h->plane_stride};
     k_scatter<<<grid_for(h->n_elems), 256, 0, (cudaStream_t)stream>>>(sa);
@@ -212,7 +215,8 @@ int pn_cnn_output(pn_handle* h, const float* net_out, double scale, const float*
 
 int pn_cnn_precondition(pn_handle* h, struct pn_cnn* net, const float* v, float* z, void* stream) {
     if (!h || !net || !v || !z) return PN_ERR_ARG;
-    if (h->dims != 3) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_precondition: 3D handles only");
+    if (h->dims != 3 || h->periodic)
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_precondition: 3D vacuum-boundary handles only");
     if (h->R % 8) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_cnn_precondition: R must be a multiple of 8");
     const int64_t V = int64_t(h->R) * h->R * h->R;
     float* scratch = nullptr;

@@ -264,11 +264,17 @@ __device__ __forceinline__ void givens_core(double* H, int ldh, const double* ad
     double* col = H + int64_t(j) * ldh;
     double nrm2 = nrm2_in;
     if (pythagoras) {
-        // single Gram-Schmidt pass: ||w - V h||^2 = ||w||^2 - ||h||^2 for orthonormal V
+        // single Gram-Schmidt pass: ||w - V h||^2 = ||w||^2 - ||h||^2 for orthonormal V.
+        // A remainder at rounding level is a breakdown (w lies in the span of V:
+        // the Krylov space is invariant and the least-squares solution exact):
+        // h_{j+1,j} = 0, the next basis vector 0, the residual estimate 0.
         double hh = 0.0;
         for (int i = 0; i <= j; ++i) hh += col[i] * col[i];
         nrm2 = nrm2 - hh;
-        if (!(nrm2 > 1e-14 * nrm2_in)) nrm2 = 1e-14 * nrm2_in;
+        // (rounding level: about 1e-14 of |w|^2 for FP32 vectors (pythagoras = 1),
+        // 1e-30 for FP64 (2), 1e-6 for a basis stored in FP16 (3))
+        const double tiny = pythagoras == 2 ? 1e-26 : (pythagoras == 3 ? 1e-5 : 1e-12);
+        if (!(nrm2 > tiny * nrm2_in)) nrm2 = 0.0;
     } else {
         for (int i = 0; i <= j; ++i) col[i] += add[i];
     }
@@ -708,7 +714,7 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
             col[i] = hi;
         }
         S[S_NRM2] = tot[NV];
-        givens_core(H, ldh, add, cs, sn, g, j, S, 1, tot[NV]);
+        givens_core(H, ldh, add, cs, sn, g, j, S, 3, tot[NV]);
         *ticket = 0u;
     }
 }
@@ -1052,7 +1058,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
                 }
                 c.pb();
                 k_cgs1_gather<<<1, 32, 0, c.s>>>(H + int64_t(j) * ldh, add, tmp0, nv0, j, S);
-                k_givens<<<1, 32, 0, c.s>>>(H, ldh, add, cs, sn, g, j, S, 1);
+                k_givens<<<1, 32, 0, c.s>>>(H, ldh, add, cs, sn, g, j, S, sizeof(T) == 4 ? 1 : 2);
                 c.launched("gmres: givens", 2);
                 c.pe(PN_PROF_SCALAR, 0.0);
                 for (int i0 = 0; i0 <= j; i0 += PN_MAX_MDOT) {
@@ -1210,8 +1216,8 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
         return pn_fail(h, PN_ERR_ARG, "pn_solve: unknown solver");
     if (o.solver == PN_SOLVER_IR_FGMRES && !o.precond)
         return pn_fail(h, PN_ERR_ARG, "pn_solve: PN_SOLVER_IR_FGMRES needs opts->precond");
-    if (o.solver == PN_SOLVER_IR_FGMRES && h->dims != 3)
-        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the learned preconditioner is 3D only");
+    if (o.solver == PN_SOLVER_IR_FGMRES && (h->dims != 3 || h->periodic))
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the learned preconditioner is 3D, vacuum boundary only");
     if (o.solver == PN_SOLVER_IR_FGMRES && h->R % 8)
         return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the learned preconditioner needs R % 8 == 0");
     if (o.solver < PN_SOLVER_IR_GMRES && o.precision != PN_F32 && o.precision != PN_F64)

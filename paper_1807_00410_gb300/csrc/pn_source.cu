@@ -160,6 +160,7 @@ extern "C" int pn_single_scatter_beam(int N, int R, const void* sigma_t, const v
 extern "C" int pn_unstagger(pn_handle* h, const void* x, void* out, int dtype, void* stream) {
     if (!h) return PN_ERR_ARG;
     if (!x || !out || (dtype != PN_F32 && dtype != PN_F64)) return pn_fail(h, PN_ERR_ARG, "pn_unstagger: bad argument");
+    if (h->periodic) return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_unstagger: not in the periodic test mode");
     const int nzc = h->dims == 3 ? h->R : 1;
     const int64_t V = int64_t(h->R) * h->R * nzc;
     const int blocks = int(std::min<int64_t>((V * h->K + 255) / 256, 8 * int64_t(pn_sm_count()) * 8));

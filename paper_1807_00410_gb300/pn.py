@@ -29,6 +29,7 @@ PN_ERR_TOO_LARGE = -9
 PN_NOALLOC_MAX_ELEMS = 1 << 31
 PN_F32, PN_F64 = 0, 1
 PN_BC_VACUUM = 0
+PN_BC_PERIODIC_TEST = 1
 PN_Q_CENTRE_00, PN_Q_CENTRE_MOMENTS = 0, 1
 SOLVERS = {"cgls": 0, "gmres": 1, "ir": 2, "ir_fgmres": 3}
 
@@ -165,6 +166,7 @@ class Layout:
     plane_k: list
     plane_class: list
     dims: int = 3   # 2: the z-independent reduction (one z-slice per plane, l + m even)
+    periodic: bool = False  # periodic test mode: R slots per axis for every class
 
     def plane_of_k(self, k: int) -> int:
         return self.plane_k.index(k)
@@ -177,8 +179,9 @@ class Layout:
     def active_shape(self, p: int):
         c = self.plane_class[p]
         R = self.R
-        nz = R + ((c >> 2) & 1) if self.dims == 3 else 1
-        return (nz, R + ((c >> 1) & 1), R + (c & 1))  # (z, y, x)
+        e = 0 if self.periodic else 1
+        nz = R + e * ((c >> 2) & 1) if self.dims == 3 else 1
+        return (nz, R + e * ((c >> 1) & 1), R + e * (c & 1))  # (z, y, x)
 
     def coefficient_index(self, p: int) -> int:
         """Position of plane p's coefficient in the handle's coefficient list
@@ -269,13 +272,15 @@ class System:
     array of centre moments.  numpy inputs are passed as host arrays (the
     library copies them); torch CUDA tensors are passed as device pointers.
 
+    periodic=True builds the periodic test mode (every axis wraps; the exact
+    closed forms of a homogeneous medium hold in it).
     dims=2 builds the z-independent 2D reduction (pn_create_2d): fields are
     (R, R) arrays [y][x], K = (N+1)(N+2)/2 coefficients with l + m even, and
     moment sources are (K, R, R) in increasing k.
     """
 
     def __init__(self, N: int, R: int, sigma_t, albedo, g: float, Q=None, sigma_t_min: float = 0.0,
-                 stream=None, dims: int = 3):
+                 stream=None, dims: int = 3, periodic: bool = False):
         if dims not in (2, 3):
             raise ValueError("dims must be 2 or 3")
         self._lib = load_library()
@@ -337,14 +342,16 @@ class System:
         if tuple(np.shape(sigma_t)) != cells:
             raise ValueError(f"sigma_t must have shape {cells}")
         create = self._lib.pn_create if dims == 3 else self._lib.pn_create_2d
-        rc = create(ctypes.byref(self._h), int(N), int(R), ctypes.byref(m), PN_BC_VACUUM,
+        rc = create(ctypes.byref(self._h), int(N), int(R), ctypes.byref(m),
+                    PN_BC_PERIODIC_TEST if periodic else PN_BC_VACUUM,
                     _stream_ptr(stream) if (st_dev or stream is not None) else ctypes.c_void_p(0))
         if rc != PN_OK:
             raise PnError(rc, self._lib.pn_last_error(None).decode())
         lay = _Layout()
         self._check(self._lib.pn_get_layout(self._h, ctypes.byref(lay)))
         self.layout = Layout(lay.N, lay.K, lay.R, lay.pitch_x, lay.pitch_y, lay.plane_stride, lay.n_elems,
-                             lay.n_active, list(lay.plane_k)[:lay.K], list(lay.plane_class)[:lay.K], dims)
+                             lay.n_active, list(lay.plane_k)[:lay.K], list(lay.plane_class)[:lay.K], dims,
+                             bool(periodic))
         self.N, self.R, self.K, self.dims = N, R, K, dims
 
     # -- plumbing -------------------------------------------------------------

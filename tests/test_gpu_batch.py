@@ -216,3 +216,20 @@ def test_grid_barrier_completes_and_its_bounded_wait_runs_out():
     torch.cuda.synchronize()
     assert bool(torch.isfinite(y).all())
     s.close()
+
+
+def test_batched_exact_eigenvector_breakdown():
+    """A homogeneous periodic instance whose first Krylov vector is an exact
+    eigenvector (happy breakdown) beside an ordinary one: both converge."""
+    from paper_1807_00410_gb300 import Batch, System
+    R = 8
+    s0 = System(3, R, np.full((R, R, R), 3.0), 0.8, 0.4, np.full((R, R, R), 2.5), periodic=True)
+    s1, d1 = _instance(3, 10, 3, 71)
+    batch = Batch([s0, s1], restart=10)
+    us = [s0.zeros(torch.float64), s1.zeros(torch.float64)]
+    st = batch.solve(us, tol=1e-10)
+    assert all(x["status"] == 0 for x in st)
+    np.testing.assert_allclose(s0.to_planes(us[0])[0], 2.5 / (3.0 * 0.2), rtol=1e-9)
+    batch.close()
+    s0.close()
+    s1.close()

@@ -379,6 +379,57 @@ def test_fp16_basis_rejected_outside_refinement():
     gpu.close()
 
 
+@pytest.mark.parametrize("N,R", [(1, 6), (3, 7), (5, 5)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_periodic_apply_transpose_residual_match_oracle(N, R, dtype):
+    """The periodic test mode (every axis wraps, R slots per axis for every
+    class) against the oracle's periodic assembly."""
+    from paper_1807_00410_gb300 import System
+    rng = np.random.default_rng(100 + 10 * N + R)
+    st = rng.uniform(0.5, 20.0, (R, R, R))
+    al = rng.uniform(0.2, 0.95, (R, R, R))
+    q = rng.uniform(0.0, 1.0, (R, R, R))
+    med = opn.Medium(st, al, 0.35, q)
+    S = opn.assemble(N, R, med, periodic=True)
+    gpu = System(N, R, st, al, 0.35, q, periodic=True)
+    assert gpu.layout.n_active == S.layout.n
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    parts = [rng.uniform(-1, 1, sh) for sh in S.layout.shapes]
+    x = gpu.from_planes(parts, dtype=tdt)
+    xu = S.layout.join(gpu.to_planes(x))
+    y = gpu.zeros(tdt)
+    tol = 1e-12 if dtype == "f64" else 3e-6
+    for op, ref in (("apply", S.A @ xu), ("apply_t", S.A.T @ xu), ("residual", S.b - S.A @ xu)):
+        getattr(gpu, op)(x, y)
+        got = S.layout.join(gpu.to_planes(y))
+        np.testing.assert_allclose(got, ref, rtol=0, atol=tol * np.abs(ref).max() * 4)
+    gpu.close()
+
+
+@pytest.mark.parametrize("N,g", [(1, 0.0), (3, 0.4), (5, 0.7)])
+def test_periodic_homogeneous_uniform_source_closed_form_on_gpu(N, g):
+    """Homogeneous medium, uniform isotropic source, periodic box: transport
+    vanishes, so L00 = Q / sigma_a everywhere and every other moment is 0
+    (the exact solution of the continuous and the discrete system)."""
+    from paper_1807_00410_gb300 import System
+    R, st, al, Q0 = 8, 3.0, 0.8, 2.5
+    gpu = System(N, R, np.full((R, R, R), st), al, g, np.full((R, R, R), Q0), periodic=True)
+    L00 = Q0 / (st * (1.0 - al))
+    # the first Krylov vector is an exact eigenvector (a breakdown in every variant)
+    for kw in ({"ortho": "cgs1"}, {"ortho": "cgs1", "basis": "f16"}, {"ortho": "cgs2"}):
+        u = gpu.zeros(torch.float64)
+        s = gpu.solve(u, solver="ir", tol=1e-12, restart=15, **kw)
+        assert s["rel_residual"] <= 1e-12
+        planes = gpu.to_planes(u)
+        np.testing.assert_allclose(planes[0], L00, rtol=1e-10)
+        for k in range(1, len(planes)):
+            assert np.abs(planes[k]).max() <= 1e-10 * L00
+    u = gpu.zeros(torch.float64)
+    s = gpu.solve(u, solver="gmres", tol=1e-12, restart=15, ortho="cgs1")
+    np.testing.assert_allclose(gpu.to_planes(u)[0], L00, rtol=1e-10)
+    gpu.close()
+
+
 # --- source building and unstaggering ---------------------------------------------
 
 @pytest.mark.parametrize("dtype,axis,sign", [("f64", 0, 1), ("f64", 2, -1), ("f32", 1, 1)])
