@@ -256,32 +256,54 @@ __global__ void __launch_bounds__(256) kb_mdot(const BInst* __restrict__ I, cons
     ph_mdot(I, st, ch, nch, chv, j, partials, blockIdx.x, gridDim.x);
 }
 
-// One warp per instance: v-th value summed over the instance's chunks (fixed order).
-__device__ __forceinline__ double warp_chunk_sum(const double* partials, int stride, int first, int count, int v) {
-    const int lane = threadIdx.x & 31;
-    double t = 0.0;
-    for (int c = lane; c < count; c += 32) t += partials[int64_t(first + c) * stride + v];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    return t;  // lane 0
+// Block-wide sums over one instance's chunk partials (256 threads, fixed
+// assignment of chunks to threads and a fixed tree: deterministic): out[v]
+// for v < nv, and out[BM_MAX] if `self`, of partials with `stride` values per
+// chunk.  Must be called by every thread of the block.
+__device__ __forceinline__ void block_chunk_sums(const double* partials, int stride, int first, int count, int nv,
+                                                 bool self, double* out) {
+    __shared__ double red[NV1][8];
+    double acc[NV1];
+#pragma unroll
+    for (int v = 0; v < NV1; ++v) acc[v] = 0.0;
+    for (int c = threadIdx.x; c < count; c += blockDim.x) {
+        const double* p = partials + int64_t(first + c) * stride;
+#pragma unroll
+        for (int v = 0; v < NV1; ++v)
+            if (v < nv || (self && v == BM_MAX)) acc[v] += p[v];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV1; ++v) {
+        if (v < nv || (self && v == BM_MAX)) {
+            double t = acc[v];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) red[v][warp] = t;
+        }
+    }
+    __syncthreads();
+    const int v = threadIdx.x;
+    if (v < NV1 && (v < nv || (self && v == BM_MAX))) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[v][q];
+        out[v] = t;
+    }
+    __syncthreads();
 }
 
-// Arnoldi bookkeeping of step j for every live instance (block = one warp per
-// instance): projections and |w|^2 from the chunk partials, Hessenberg
-// column, previous rotations, rotation j, residual estimate; freezes an
-// instance that reached its target or the end of the cycle.
+// Arnoldi bookkeeping of step j for every live instance (one block of 256
+// threads per instance): projections and |w|^2 from the chunk partials,
+// Hessenberg column, previous rotations, rotation j, residual estimate;
+// freezes an instance that reached its target or the end of the cycle.
 __device__ __forceinline__ void ph_givens(const BInst* __restrict__ I, BState* st, const int* vc_first,
                                           const int* vc_count, const double* partials, int j, int m, int inst) {
     BState& S = st[inst];
-    if (!S.live) return;
+    if (!S.live) return;  // uniform over the block
     const BInst& in = I[inst];
     __shared__ double vals[NV1];
-    for (int v = 0; v <= j; ++v) {
-        const double t = warp_chunk_sum(partials, NV1, vc_first[inst], vc_count[inst], v);
-        if ((threadIdx.x & 31) == 0) vals[v] = t;
-    }
-    const double w2 = warp_chunk_sum(partials, NV1, vc_first[inst], vc_count[inst], BM_MAX);
-    __syncwarp();
-    if ((threadIdx.x & 31) != 0) return;
+    block_chunk_sums(partials, NV1, vc_first[inst], vc_count[inst], j + 1, true, vals);
+    if (threadIdx.x != 0) return;
+    const double w2 = vals[BM_MAX];
     const int ldh = m + 1;
     double* col = in.H + int64_t(j) * ldh;
     double hh = 0.0;
@@ -364,16 +386,17 @@ __global__ void __launch_bounds__(256) kb_maxpy(const BInst* __restrict__ I, con
     ph_maxpy(I, st, ch, nch, chv, j, blockIdx.x, gridDim.x);
 }
 
-// Cycle start, one warp per running instance: beta = |r0| from the residual
-// partials, g = beta e_0, 1 / beta for the first basis vector.
+// Cycle start, one block per running instance: beta = |r0| from the
+// residual partials, g = beta e_0, 1 / beta for the first basis vector.
 __device__ __forceinline__ void ph_cycle_init(const BInst* __restrict__ I, BState* st, const int* oc_first,
                                               const int* oc_count, const double* partials, int m, int inst) {
     BState& S = st[inst];
-    if (!S.run) return;
-    const double b2 = warp_chunk_sum(partials, 1, oc_first[inst], oc_count[inst], 0);
-    if ((threadIdx.x & 31) != 0) return;
+    if (!S.run) return;  // uniform over the block
+    __shared__ double b2s[NV1];
+    block_chunk_sums(partials, 1, oc_first[inst], oc_count[inst], 1, false, b2s);
+    if (threadIdx.x != 0) return;
     const BInst& in = I[inst];
-    const double beta = sqrt(fmax(b2, 0.0));
+    const double beta = sqrt(fmax(b2s[0], 0.0));
     for (int i = 0; i <= m; ++i) in.g[i] = 0.0;
     in.g[0] = beta;
     S.res = beta;
@@ -476,9 +499,10 @@ __global__ void __launch_bounds__(256) kb_update(const BInst* __restrict__ I, co
 __global__ void kb_outer_reduce(BState* st, const int* oc_first, const int* oc_count, const double* partials) {
     const int inst = blockIdx.x;
     BState& S = st[inst];
-    if (S.done) return;
-    const double t = warp_chunk_sum(partials, 1, oc_first[inst], oc_count[inst], 0);
-    if (threadIdx.x == 0) S.rr = t;
+    if (S.done) return;  // uniform over the block
+    __shared__ double t[NV1];
+    block_chunk_sums(partials, 1, oc_first[inst], oc_count[inst], 1, false, t);
+    if (threadIdx.x == 0) S.rr = t[0];
 }
 
 // r32 = r64 / |r|, d32 = 0 for running instances (|r| = sqrt(rr)).
@@ -596,9 +620,8 @@ __global__ void __launch_bounds__(256, 2) kb_cycle_persistent(CycleArgs a) {
                                   (float* const*)a.ptrs, (const float* const*)(a.ptrs + a.p_r32), G_RUN, a.part_op,
                                   cta, ncta);
     if (!grid_sync(a.bar, nb, a.limit)) return;
-    if (threadIdx.x < 32)
-        for (int inst = cta; inst < a.n; inst += ncta)
-            ph_cycle_init(a.I, a.st, a.oc_first, a.oc_count, a.part_op, a.m, inst);
+    for (int inst = cta; inst < a.n; inst += ncta)
+        ph_cycle_init(a.I, a.st, a.oc_first, a.oc_count, a.part_op, a.m, inst);
     if (!grid_sync(a.bar, nb, a.limit)) return;
     ph_scale0(a.I, a.st, a.vc, a.nvc, a.chv, cta, ncta);
     if (!grid_sync(a.bar, nb, a.limit)) return;
@@ -609,9 +632,8 @@ __global__ void __launch_bounds__(256, 2) kb_cycle_persistent(CycleArgs a) {
         if (!grid_sync(a.bar, nb, a.limit)) return;
         ph_mdot(a.I, a.st, a.vc, a.nvc, a.chv, j, a.part_vec, cta, ncta);
         if (!grid_sync(a.bar, nb, a.limit)) return;
-        if (threadIdx.x < 32)
-            for (int inst = cta; inst < a.n; inst += ncta)
-                ph_givens(a.I, a.st, a.vc_first, a.vc_count, a.part_vec, j, a.m, inst);
+        for (int inst = cta; inst < a.n; inst += ncta)
+            ph_givens(a.I, a.st, a.vc_first, a.vc_count, a.part_vec, j, a.m, inst);
         if (!grid_sync(a.bar, nb, a.limit)) return;
         ph_maxpy(a.I, a.st, a.vc, a.nvc, a.chv, j, cta, ncta);
         if (!grid_sync(a.bar, nb, a.limit)) return;
@@ -779,7 +801,7 @@ void launch_op32(pn_batch* b, size_t px, size_t py, size_t pb, int gate, bool re
 // every tiled-capable instance as its own launch on one of the side streams
 // (independent graph branches that run concurrently), gated by the
 // instance's live flag, and one generic launch for the others.
-void launch_step_apply(pn_batch* b, int j, const int* const* live) {
+void launch_step_apply(pn_batch* b, int j, const int* const* live, const std::vector<char>* running = nullptr) {
     if (!b->use_tiled || b->n_tiled == 0) {
         launch_op32(b, size_t(P_V0 + j) * b->n, size_t(P_V0 + j + 1) * b->n, 0, G_LIVE, false);
         return;
@@ -789,7 +811,7 @@ void launch_step_apply(pn_batch* b, int j, const int* const* live) {
     int q = 0;
     for (int i = 0; i < b->n; ++i) {
         const BInst& in = b->inst[i];
-        if (in.generic) continue;
+        if (in.generic || (running && !(*running)[i])) continue;
         pn::launch_tiled_gated(b->hs[i], pn::OP_APPLY, in.V + size_t(j) * in.n, in.V + size_t(j + 1) * in.n, nullptr,
                                nullptr, live[i], b->side[q++ % pn_batch::NSIDE]);
     }
@@ -807,7 +829,7 @@ std::vector<const int*> live_flags(const pn_batch* b) {
     return f;
 }
 
-void launch_cycle(pn_batch* b) {
+void launch_cycle(pn_batch* b, const std::vector<char>* running = nullptr) {
     const int gv = grid_of(b, b->vc.size(), b->vec_mult);
     const int nch = int(b->vc.size());
     const int* oc_first = b->d_counts;
@@ -816,13 +838,13 @@ void launch_cycle(pn_batch* b) {
     const int* vc_count = b->d_counts + 3 * b->n;
     // V_0 = r32 - A d32, beta, V_0 /= beta
     launch_op32(b, p_d32(b), P_V0, p_r32(b), G_RUN, true);
-    kb_cycle_init<<<b->n, 32, 0, b->s>>>(b->d_inst, b->d_state, oc_first, oc_count, b->d_part_op, b->m);
+    kb_cycle_init<<<b->n, 256, 0, b->s>>>(b->d_inst, b->d_state, oc_first, oc_count, b->d_part_op, b->m);
     kb_scale0<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv);
     const std::vector<const int*> live = live_flags(b);
     for (int j = 0; j < b->m; ++j) {
-        launch_step_apply(b, j, live.data());
+        launch_step_apply(b, j, live.data(), running);
         kb_mdot<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, j, b->d_part_vec);
-        kb_givens<<<b->n, 32, 0, b->s>>>(b->d_inst, b->d_state, vc_first, vc_count, b->d_part_vec, j, b->m);
+        kb_givens<<<b->n, 256, 0, b->s>>>(b->d_inst, b->d_state, vc_first, vc_count, b->d_part_vec, j, b->m);
         kb_maxpy<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, j);
     }
     kb_backsolve<<<(b->n + 63) / 64, 64, 0, b->s>>>(b->d_inst, b->d_state, b->n, b->m);
@@ -1177,6 +1199,9 @@ int pn_batch_tune(pn_batch* b, void* stream) {
         const int nch = int(b->vc.size());
         float best = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
+            // the Givens kernel freezes instances (the basis is arbitrary
+            // here): every repetition starts with every instance live
+            if (what == 0 && write_state(b) != PN_OK) return -1.0f;
             cudaEventRecord(e0, b->s);
             if (what == 1) {
                 launch_op32(b, size_t(P_V0) * b->n, size_t(P_V0 + 1) * b->n, 0, G_LIVE, false);
@@ -1187,12 +1212,24 @@ int pn_batch_tune(pn_batch* b, void* stream) {
                 b->use_tiled = keep;
             } else {
                 kb_mdot<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, jmid, b->d_part_vec);
-                kb_maxpy<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, jmid);
+                kb_givens<<<b->n, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_counts + 2 * b->n,
+                                                  b->d_counts + 3 * b->n, b->d_part_vec, jmid, b->m);
             }
             cudaEventRecord(e1, b->s);
             if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
+            if (what == 0) {
+                // the multi-axpy as a second segment, every instance live again
+                if (write_state(b) != PN_OK) return -1.0f;
+                cudaEventRecord(e0, b->s);
+                kb_maxpy<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, jmid);
+                cudaEventRecord(e1, b->s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+                float ms2 = 0.0f;
+                cudaEventElapsedTime(&ms2, e0, e1);
+                ms += ms2;
+            }
             if (rep > 0) best = std::min(best, ms);  // the first run warms up
         }
         return best;
@@ -1333,7 +1370,7 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
         kb_op<double, pn::OP_RESIDUAL><<<grid, 256, 0, b->s>>>(
             b->d_inst, b->d_state, b->d_opc, int(b->opc.size()), b->cho, (const double* const*)(b->d_ptrs + p_x(b)),
             (double* const*)(b->d_ptrs + p_r64(b)), nullptr, G_NOT_DONE, b->d_part_op);
-        kb_outer_reduce<<<n, 32, 0, b->s>>>(b->d_state, oc_first, oc_count, b->d_part_op);
+        kb_outer_reduce<<<n, 256, 0, b->s>>>(b->d_state, oc_first, oc_count, b->d_part_op);
         launches += 2;
         if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "pn_batch_solve: residual");
         if ((rc = read_state(b)) != PN_OK) return rc;
@@ -1366,7 +1403,18 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
         ++launches;
         // inner GMRES cycles (graph replays) until every running instance met its target
         for (;;) {
-            if (b->mode == PN_BATCH_GRAPH) {
+            int n_run = 0;
+            for (int i = 0; i < n; ++i) n_run += b->h_state[i].run ? 1 : 0;
+            if (b->mode == PN_BATCH_GRAPH && 4 * n_run <= n && b->use_tiled && b->n_tiled > 0) {
+                // few instances left: launch this cycle directly, with tiled
+                // operator launches for the running instances only (the
+                // captured graph would launch every instance's, gated)
+                std::vector<char> running(n);
+                for (int i = 0; i < n; ++i) running[i] = b->h_state[i].run ? 1 : 0;
+                launch_cycle(b, &running);
+                if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "pn_batch_solve: cycle");
+                launches += 4 * int64_t(b->m) + 5;
+            } else if (b->mode == PN_BATCH_GRAPH) {
                 if ((e = cudaGraphLaunch(b->cycle, b->s)) != cudaSuccess) return bcuda(b, e, "pn_batch_solve: cycle");
                 launches += 4 * int64_t(b->m) + 5;
             } else {

@@ -366,6 +366,23 @@ def test_apply_tiling_plans_give_identical_outputs_and_tuner_picks_one():
     gpu.close()
 
 
+@pytest.mark.parametrize("N,R,basis", [(7, 8, "f16"), (7, 7, "f32"), (3, 2, "f16"), (1, 2, "f32")])
+def test_ir_solves_at_p7_and_at_the_smallest_grid(N, R, basis):
+    """P7 (the tiled kernel's largest classes; its residual mode loads the
+    right-hand side in place) and R = 2 (one tile, every slot on the
+    boundary) solve to the oracle's 1e-6."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(N, R, 17, 0.5, 40.0, 0.95, 0.3)
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00)
+    S = opn.assemble(N, R, med)
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, solver="ir", tol=1e-6, restart=15, ortho="cgs1", basis=basis)
+    assert st["rel_residual"] <= 1e-6
+    assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u))) <= 1.0001e-6
+    gpu.close()
+
+
 def test_fp16_basis_rejected_outside_refinement():
     from paper_1807_00410_gb300 import System
     from paper_1807_00410_gb300.pn import PnError
