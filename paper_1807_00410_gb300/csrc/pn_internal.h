@@ -118,6 +118,8 @@ enum OpMode { OP_APPLY = 0, OP_APPLY_T = 1, OP_RESIDUAL = 2 };
 cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int dtype,
                       double* partials, cudaStream_t s, const void* bvec = nullptr);
 int op_partial_count(const pn_handle* h, int dtype);
+// Kernels one launch_op makes (the tiled operator: tiled + face-column kernel).
+int op_launch_count(const pn_handle* h, int dtype);
 
 // Tiled FP32 operator (pn_apply_tiled.cu): covers x < tiled_x_end(h) of every
 // plane box; one FP64 residual partial per CTA.

@@ -130,6 +130,8 @@ static bool use_tiled(const pn_handle* h, int dtype) {
 
 bool tiled_serves(const pn_handle* h) { return use_tiled(h, PN_F32); }
 
+int op_launch_count(const pn_handle* h, int dtype) { return use_tiled(h, dtype) ? 2 : 1; }
+
 int op_partial_count(const pn_handle* h, int dtype) {
     if (use_tiled(h, dtype)) return tiled_partial_count(h);
     return naive_grid_x(h) * h->K;

@@ -542,7 +542,8 @@ int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
     double* S = h->d_scalars;
     auto residual = [&]() {
         c.pb();
-        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r, dt, h->d_partials, c.s), "cgls: residual");
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r, dt, h->d_partials, c.s), "cgls: residual",
+             pn::op_launch_count(h, dt));
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, es, false));
         c.pb();
         c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, dt), 1, S + S_RR, c.s), "cgls: reduce");
@@ -550,7 +551,7 @@ int cgls(Ctx& c, T* x, const pn_solve_opts& o, pn_solve_stats& st) {
     };
     auto op = [&](int mode, const T* in, T* out) {
         c.pb();
-        c.lk(pn::launch_op(h, mode, in, out, dt, nullptr, c.s), "cgls: operator");
+        c.lk(pn::launch_op(h, mode, in, out, dt, nullptr, c.s), "cgls: operator", pn::op_launch_count(h, dt));
         c.pe(PN_PROF_APPLY, c.ob(mode, es, false));
     };
     auto dot = [&](const T* a, double* out) {
@@ -883,7 +884,8 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
     const int64_t vs8 = n / 8;
     for (;;) {
         c.pb();
-        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, w, PN_F32, h->d_partials, c.s, bvec), "gmres16: residual");
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, w, PN_F32, h->d_partials, c.s, bvec), "gmres16: residual",
+             pn::op_launch_count(h, PN_F32));
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, 4.0, bvec != nullptr));
         c.pb();
         c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, PN_F32), 1, S + S_BETA2, c.s),
@@ -902,7 +904,8 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
         int j = 0;
         for (; j < m && total < max_iter; ++j) {
             c.pb();
-            c.lk(pn::launch_op(h, pn::OP_APPLY, vcur, w, PN_F32, nullptr, c.s), "gmres16: A v");
+            c.lk(pn::launch_op(h, pn::OP_APPLY, vcur, w, PN_F32, nullptr, c.s), "gmres16: A v",
+                 pn::op_launch_count(h, PN_F32));
             c.pe(PN_PROF_APPLY, ob);
             c.pb();
             k_mdot16_givens<<<nb_mdot(), 256, 0, c.s>>>(n8, (const uint4*)V16, vs8, j + 1, (const float4*)w,
@@ -980,7 +983,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
     for (;;) {
         // r = b - A x into V_0, beta = ||r||
         c.pb();
-        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, V, dt, h->d_partials, c.s, bvec), "gmres: residual");
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, V, dt, h->d_partials, c.s, bvec), "gmres: residual", pn::op_launch_count(h, dt));
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, es, bvec != nullptr));
         c.pb();
         c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, dt), 1, S + S_BETA2, c.s), "gmres: reduce");
@@ -1021,7 +1024,7 @@ int gmres(Ctx& c, T* x, const T* bvec, double bnorm2, double tol, int m, int max
                 av = zj;
             }
             c.pb();
-            c.lk(pn::launch_op(h, pn::OP_APPLY, av, w, dt, nullptr, c.s), "gmres: A v");
+            c.lk(pn::launch_op(h, pn::OP_APPLY, av, w, dt, nullptr, c.s), "gmres: A v", pn::op_launch_count(h, dt));
             c.pe(PN_PROF_APPLY, c.ob(pn::OP_APPLY, es, false));
             if (ortho == PN_ORTHO_CGS1 && sizeof(T) == 4 && j + 1 <= PN_MAX_MDOT) {
                 // classical Gram-Schmidt once, one fused launch for the
@@ -1154,7 +1157,7 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
     int rc = PN_OK;
     for (;;) {
         c.pb();
-        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r64, PN_F64, h->d_partials, c.s), "ir: residual");
+        c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r64, PN_F64, h->d_partials, c.s), "ir: residual", pn::op_launch_count(h, PN_F64));
         c.pe(PN_PROF_RESIDUAL, c.ob(pn::OP_RESIDUAL, 8.0, false));
         c.pb();
         c.lk(pn::launch_reduce(h->d_partials, pn::op_partial_count(h, PN_F64), 1, S + S_RR, c.s), "ir: reduce");
