@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--large-iters", type=int, default=600)
     ap.add_argument("--large-sigma-min", type=float, default=0.1)
     ap.add_argument("--apply-n", type=int, default=7)
+    ap.add_argument("--apply-kernel", choices=["auto", "tma", "register"], default="auto",
+                    help="--apply-only: main kernel of the tiled operator (auto: the autotuner's pick)")
     ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
 
@@ -280,7 +282,7 @@ def apply_scan(torch, System, pn_inputs, hbm_peak):
         gbs = bytes_alg / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs,
                      "frac_of_hbm": gbs / hbm_peak, "dof": lay.n_active, "bytes_per_apply": bytes_alg,
-                     "ctas_per_sm": tiling["ctas_per_sm"]}
+                     "ctas_per_sm": tiling["ctas_per_sm"], "kernel": tiling["kernel"]}
         sysm.close()
         del x, ys
         torch.cuda.empty_cache()
@@ -478,7 +480,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f16-basis+f32+f64" if args.basis == "f16" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart, "ortho": args.ortho,
-                       "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"],
+                       "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"],
                        "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
                        "replicas": "one independent problem per GPU (seed = rank)"},
             "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
@@ -513,6 +515,8 @@ def run_apply_only(args):
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
     lay = sysm.layout
     tiling = sysm.tune_apply()
+    if args.apply_kernel != "auto":
+        sysm.set_apply_kernel(args.apply_kernel)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand(lay.n_elems, dtype=torch.float32, device="cuda", generator=g)
     ys = [torch.empty_like(x) for _ in range(2)]
@@ -532,7 +536,8 @@ def run_apply_only(args):
     print(json.dumps({"mode": "apply-only", "workload": f"P{p.N} {p.R}^3 cloud FP32 apply", "ms": ms,
                       "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac": gbs / hbm_peak,
                       "peak": hbm_peak, "peak_source": peak_src, "dof": lay.n_active,
-                      "bytes_per_apply": bytes_alg, "ctas_per_sm": tiling["ctas_per_sm"], "steps": args.steps,
+                      "bytes_per_apply": bytes_alg, "ctas_per_sm": tiling["ctas_per_sm"],
+                      "kernel": sysm.apply_kernel, "steps": args.steps,
                       "warmup": args.warmup}), flush=True)
     sysm.close()
 

@@ -214,6 +214,12 @@ typedef struct {
                             restart <= 16): about 40 % fewer bytes per Arnoldi
                             step; the stored basis rounds at ~5e-4 relative, so
                             inner_tol should stay >= 1e-3 */
+    int augment;         /* PN_SOLVER_IR_GMRES with PN_BASIS_F16: k in [0, 4] corrections
+                            of earlier restart cycles (x_i - x_{i-1}, newest first)
+                            appended to each cycle's m Krylov directions (LGMRES(m, k));
+                            kept across restarts and refinement steps; restart + k
+                            <= 16; 0 (default): plain restarted GMRES.  pn_batch_solve
+                            ignores it */
 } pn_solve_opts;
 
 #define PN_ORTHO_CGS2 0
@@ -448,6 +454,30 @@ int pn_batch_get_op_path(const pn_batch* batch, int* tiled);
  */
 int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms);
 int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm);
+
+/*
+ * Main kernel of the tiled FP32 operator (3D handles with the vacuum
+ * boundary), both over 32 x 4 column tiles marching in z:
+ *   PN_APPLY_KERNEL_TMA (default): each parity class's input planes are
+ *     staged in shared memory by TMA tensor copies (one 4D box per class and
+ *     z-slice; inactive slots arrive as 0), and the four thread groups of a
+ *     CTA compute equal shares of the rows.  Its mbarrier waits are bounded
+ *     (about 2 s); one that runs out makes the next pn_solve return
+ *     PN_ERR_TIMEOUT.
+ *   PN_APPLY_KERNEL_REGISTER: each thread loads its columns' values of two
+ *     z-adjacent classes into registers and stages them in shared memory.
+ * Both give bitwise-identical outputs (the residual norm's partial sums of
+ * r^2 are formed over other sets of outputs, so it agrees to their FP32
+ * rounding).  pn_tune_apply times both (with every z
+ * chunking) and keeps the fastest.  pn_set_apply_kernel returns
+ * PN_ERR_UNSUPPORTED if the TMA kernel cannot serve the handle (no driver
+ * entry point for tensor maps); handles the tiled operator does not serve
+ * ignore the setting.  pn_get_apply_kernel reports the kernel that runs.
+ */
+#define PN_APPLY_KERNEL_REGISTER 0
+#define PN_APPLY_KERNEL_TMA      1
+int pn_set_apply_kernel(pn_handle* h, int kernel);
+int pn_get_apply_kernel(const pn_handle* h, int* kernel);
 
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */

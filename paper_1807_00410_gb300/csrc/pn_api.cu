@@ -200,6 +200,7 @@ void pn_default_solve_opts(pn_solve_opts* o) {
     o->ortho = PN_ORTHO_CGS2;
     o->precond = nullptr;
     o->basis = PN_BASIS_F32;
+    o->augment = 0;
 }
 
 }  // extern "C"
@@ -380,6 +381,13 @@ int create_impl(pn_handle** out, int N, int R, const pn_medium* m, int boundary,
                                                                pn::op_partial_count(h, PN_F64))))),
                      "partials"));
     PN_TRY(dev_alloc(nullptr, &h->d_scalars, size_t(PN_NSCALARS), "scalars"));
+    {
+        const cudaError_t e = cudaMemset(h->d_scalars, 0, size_t(PN_NSCALARS) * sizeof(double));
+        if (e != cudaSuccess) {
+            rc = pn_cuda_fail(nullptr, e, "pn_create: scalars");
+            goto fail;
+        }
+    }
     if (cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
         h->h_pinned = nullptr;
         rc = pn_fail(nullptr, PN_ERR_ALLOC, "pn_create: pinned host allocation failed");
@@ -461,6 +469,7 @@ int pn_destroy(pn_handle* h) {
     cudaGetDevice(&dev);
     if (dev != h->device) cudaSetDevice(h->device);
     free_all(h);
+    pn::tma_cache_free(h);
     if (dev != h->device) cudaSetDevice(dev);
     delete h;
     return PN_OK;
@@ -548,6 +557,23 @@ int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm) {
     return PN_OK;
 }
 
+int pn_set_apply_kernel(pn_handle* h, int kernel) {
+    if (!h) return PN_ERR_ARG;
+    if (kernel != PN_APPLY_KERNEL_REGISTER && kernel != PN_APPLY_KERNEL_TMA)
+        return pn_fail(h, PN_ERR_ARG, "pn_set_apply_kernel: bad kernel");
+    if (kernel == PN_APPLY_KERNEL_TMA && pn::tiled_serves(h) && !pn::tma_serves(h))
+        return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_set_apply_kernel: the TMA kernel does not serve this handle");
+    h->tile_kernel = kernel;
+    return PN_OK;
+}
+
+int pn_get_apply_kernel(const pn_handle* h, int* kernel) {
+    if (!h || !kernel) return PN_ERR_ARG;
+    *kernel = (h->tile_kernel == PN_APPLY_KERNEL_TMA && pn::tma_serves(h)) ? PN_APPLY_KERNEL_TMA
+                                                                             : PN_APPLY_KERNEL_REGISTER;
+    return PN_OK;
+}
+
 int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms) {
     if (!h) return PN_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -564,11 +590,14 @@ int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms)
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int cands[] = {1, 2, 4, 8};
-    int best = h->tile_ctas_per_sm;
+    int best = h->tile_ctas_per_sm, best_k = h->tile_kernel;
     float best_t = 1e30f;
-    for (int c : cands) {
+    const int nk = pn::tma_serves(h) ? 2 : 1;
+    for (int ci = 0; ci < 4 * nk; ++ci) {
+        const int c = cands[ci % 4];
         if (e != cudaSuccess) break;
         h->tile_ctas_per_sm = c;
+        h->tile_kernel = nk == 2 ? ci / 4 : PN_APPLY_KERNEL_REGISTER;
         float tsum = 0.0f;
         for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
             e = cudaEventRecord(e0, s);
@@ -582,9 +611,11 @@ int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms)
         if (e == cudaSuccess && tsum / 5.0f < best_t) {
             best_t = tsum / 5.0f;
             best = c;
+            best_k = h->tile_kernel;
         }
     }
     h->tile_ctas_per_sm = best;
+    h->tile_kernel = best_k;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(x);

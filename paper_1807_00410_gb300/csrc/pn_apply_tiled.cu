@@ -31,96 +31,10 @@
 #include <cmath>
 #include <cstdint>
 
-#include "pn_couplings.h"
-#include "pn_internal.h"
+#include "pn_tiled.cuh"
 
 namespace pn {
 namespace tiled {
-
-constexpr int TX = 32;
-constexpr int NG = 4;          // thread groups: (bx, by) in {0,1}^2
-constexpr int MAXT = 10;       // max transport terms per row per axis
-constexpr int MAXC = 10;       // max coefficients per class (N <= 7)
-
-struct ClassRow {
-    int k, l;
-    int nt[3];
-    int j[3][MAXT];     // index of the input within the neighbour class along that axis
-    float c[3][MAXT];   // A_d (dimensionless; 1/h applied per output)
-};
-struct ClassTab {
-    int n;
-    int plane0;
-    ClassRow row[MAXC];
-};
-struct Tab {
-    int K;
-    int maxc;
-    ClassTab cls[8];
-};
-
-constexpr Tab make_tab(int N) {
-    Tab t{};
-    t.K = (N + 1) * (N + 1);
-    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int cls_of_k[64] = {};
-    int j_of_k[64] = {};
-    for (int l = 0; l <= N; ++l)
-        for (int m = -l; m <= l; ++m) {
-            const int k = l * l + l + m;
-            const int c = cpl::parity_class(l, m);
-            cls_of_k[k] = c;
-            j_of_k[k] = cnt[c]++;
-        }
-    int base = 0;
-    for (int c = 0; c < 8; ++c) {
-        t.cls[c].n = cnt[c];
-        t.cls[c].plane0 = base;
-        base += cnt[c];
-        if (cnt[c] > t.maxc) t.maxc = cnt[c];
-    }
-    for (int l = 0; l <= N; ++l)
-        for (int m = -l; m <= l; ++m) {
-            const int k = l * l + l + m;
-            ClassRow& r = t.cls[cls_of_k[k]].row[j_of_k[k]];
-            r.k = k;
-            r.l = l;
-            const cpl::RowTerms rt = cpl::row_terms(N, l, m);
-            for (int i = 0; i < rt.n; ++i) {
-                const int a = rt.t[i].axis;
-                const int kp = rt.t[i].lp * rt.t[i].lp + rt.t[i].lp + rt.t[i].mp;
-                r.j[a][r.nt[a]] = j_of_k[kp];
-                r.c[a][r.nt[a]] = float(rt.t[i].coef);
-                r.nt[a]++;
-            }
-        }
-    return t;
-}
-
-template <int N>
-struct TabN {
-    static constexpr Tab value = make_tab(N);
-};
-
-struct Args {
-    const float* x;
-    float* y;
-    const float* q;      // source planes (n_q of them) or null
-    const float* bvec;   // full right-hand side vector or null
-    int n_q;
-    const float* st;     // clamped sigma_t, R^3 voxel centres
-    const float* ss;     // sigma_s, R^3
-    int R;
-    int pitch_x;
-    uint32_t pitch_y, plane_stride;  // element strides (the launcher checks they fit)
-    int zc;              // slices per CTA (z chunk)
-    float inv_h;         // R
-    float tsign;         // +1: A, -1: A^T
-    float fl[8];         // g^l
-    unsigned char pcls[64];  // parity class of plane p
-    double* partials;    // residual: per-CTA FP64 sums of r^2
-    const int* live;     // null, or a device flag: the launch does nothing while it is 0
-};
 
 // Load n values of one class at slot z of this thread's column; inactive
 // slots read 0.  `base` points at the class's first plane, z = 0, this column;
@@ -225,22 +139,6 @@ __device__ __forceinline__ float xy_mean(const float* g, int tx, int ty, int bx,
     const int gx1 = tx + 1, gy1 = ty + 1;
     const int gx0 = bx ? tx : gx1, gy0 = by ? ty : gy1;
     return 0.25f * (g[gy0 * G::GX + gx0] + g[gy0 * G::GX + gx1] + g[gy1 * G::GX + gx0] + g[gy1 * G::GX + gx1]);
-}
-
-// Right-hand side of one class at slot s of this thread's column (residual
-// mode): the full vector bvec, or Q (planes beyond n_q are 0); read only at
-// active slots.  Issued at the start of a z-step so that the step's staging,
-// barrier and arithmetic hide the load latency.
-template <int N, int C>
-__device__ __forceinline__ void load_rhs(const Args& a, bool act, uint32_t col, int s, float (&r)[MAXC]) {
-    constexpr ClassTab CT = TabN<N>::value.cls[C];
-    const uint32_t ps = a.plane_stride;
-    const float* base = a.bvec ? a.bvec : a.q;
-    const int nq = a.bvec ? 64 : a.n_q;
-    const size_t off = size_t(CT.plane0) * ps + size_t(uint32_t(s) * a.pitch_y) + col;
-#pragma unroll
-    for (int i = 0; i < MAXC; ++i)
-        if (i < CT.n) r[i] = (act && CT.plane0 + i < nq) ? __ldg(base + off + uint32_t(i) * ps) : 0.0f;
 }
 
 template <int N, int TY, int GRP, int MODE>
@@ -657,8 +555,12 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
         if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, h->ev_fork, 0);
         if (e != cudaSuccess) return e;
     }
-    kern<<<p.grid, p.block, p.smem, s>>>(a);
-    e = cudaGetLastError();
+    if (h->tile_kernel == PN_APPLY_KERNEL_TMA && tma_serves(h)) {
+        e = launch_tma_main(h, MODE, a, p.grid, s);
+    } else {
+        kern<<<p.grid, p.block, p.smem, s>>>(a);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     tiled::Args af = a;
     if (af.partials) af.partials += p.grid.x * p.grid.y * p.grid.z;
@@ -728,6 +630,7 @@ cudaError_t launch_tiled_gated(const pn_handle* h, int mode, const float* x, flo
     for (int q = 0; q < 64; ++q) a.pcls[q] = q < h->K ? (unsigned char)h->plane_class[q] : 0;
     a.partials = partials;
     a.live = live;
+    a.err = reinterpret_cast<unsigned int*>(h->d_scalars + PN_S_FAULT);
     if (mode == OP_RESIDUAL) return launch_mode<OP_RESIDUAL>(h, a, p, s);
     return launch_mode<OP_APPLY>(h, a, p, s);
 }

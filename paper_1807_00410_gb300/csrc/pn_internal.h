@@ -54,6 +54,8 @@ struct pn_handle {
     int dims = 3;        // 3: R^3 cells; 2: the z-independent reduction on R^2 cells
     int periodic = 0;    // PN_BC_PERIODIC_TEST: every axis wraps, R slots per axis for every class
     int tile_ctas_per_sm = 4;  // z-chunking target of the tiled FP32 operator (pn_tune_apply)
+    int tile_kernel = PN_APPLY_KERNEL_TMA;  // main kernel of the tiled operator (pn_set_apply_kernel)
+    void* tma_cache = nullptr;  // tensor maps of recent input vectors (pn_apply_tma.cu)
     // the face-column kernel of the tiled operator runs on a side stream,
     // concurrently with the tiled kernel (fork / join events)
     cudaStream_t side = nullptr;
@@ -106,6 +108,9 @@ struct pn_handle {
 
 #define PN_MAX_MDOT 16
 #define PN_NSCALARS 1024
+// d_scalars[PN_S_FAULT] (as unsigned int): set by a kernel whose bounded wait
+// ran out (the TMA-staged operator); pn_solve reports it as PN_ERR_TIMEOUT
+#define PN_S_FAULT 1000
 
 // Kernel launchers (pn_kernels.cu).  All return cudaError_t of the launch.
 namespace pn {
@@ -131,6 +136,10 @@ cudaError_t launch_tiled_gated(const pn_handle* h, int mode, const float* x, flo
                                double* partials, const int* live, cudaStream_t s);
 // Whether the tiled FP32 operator serves this handle.
 bool tiled_serves(const pn_handle* h);
+// Whether its TMA-staged main kernel can (pn_apply_tma.cu); the handle's cache
+// of tensor maps is freed by tma_cache_free.
+bool tma_serves(const pn_handle* h);
+void tma_cache_free(pn_handle* h);
 int tiled_partial_count(const pn_handle* h);
 int tiled_partial_bound(const pn_handle* h);  // over every z-chunking pn_tune_apply may choose
 int tiled_x_end(const pn_handle* h);

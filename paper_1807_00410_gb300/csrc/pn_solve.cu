@@ -847,10 +847,67 @@ __global__ void __launch_bounds__(256) k_update16(int64_t n8, float4* __restrict
     }
 }
 
+// Error approximations appended to each restart cycle (LGMRES: the cycle's
+// search space is the m Krylov vectors plus the corrections x_i - x_{i-1} of
+// the last k cycles, which carry the directions restarting loses).
+#define PN_MAX_AUG 4
+struct Aug {
+    float* z = nullptr;  // ring of k + 1 FP32 vectors (n elements each)
+    int k = 0;           // corrections appended per cycle
+    int count = 0;       // stored so far (at most k)
+    int newest = -1;     // ring slot of the latest
+};
+struct AugIn {
+    const float4* z[PN_MAX_AUG];
+};
+
+// c = sum_{i < nv} y_i V16_i / sigma + sum_{a < na} y_{nv + a} Z_a;
+// x += c; cout = c (the cycle's correction, the next error approximation).
+__global__ void __launch_bounds__(256) k_update16_aug(int64_t n8, float4* __restrict__ x,
+                                                      const uint4* __restrict__ V16, int64_t vstride8, int nv,
+                                                      const double* y, float inv_sigma, AugIn za, int na,
+                                                      float4* __restrict__ cout) {
+    constexpr int NV = PN_MAX_MDOT;
+    float yj[NV], ya[PN_MAX_AUG];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) yj[v] = v < nv ? float(y[v]) * inv_sigma : 0.0f;
+#pragma unroll
+    for (int q = 0; q < PN_MAX_AUG; ++q) ya[q] = q < na ? float(y[nv + q]) : 0.0f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += int64_t(gridDim.x) * blockDim.x) {
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nv) {
+                float q[8];
+                h8_to_f(V16[v * vstride8 + i], q);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = fmaf(yj[v], q[k], acc[k]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PN_MAX_AUG; ++q) {
+            if (q < na) {
+                const float4 a = za.z[q][2 * i], b = za.z[q][2 * i + 1];
+                const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = fmaf(ya[q], f[k], acc[k]);
+            }
+        }
+        const float4 xa = x[2 * i], xb = x[2 * i + 1];
+        x[2 * i] = make_float4(xa.x + acc[0], xa.y + acc[1], xa.z + acc[2], xa.w + acc[3]);
+        x[2 * i + 1] = make_float4(xb.x + acc[4], xb.y + acc[5], xb.z + acc[6], xb.w + acc[7]);
+        cout[2 * i] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        cout[2 * i + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+}
+
 // Restarted GMRES(m), CGS1, FP32 arithmetic with the basis in FP16 (m <= 16).
-// Same contract as gmres<float>.
+// Same contract as gmres<float>.  With aug (k > 0) each cycle that has stored
+// corrections appends up to k of them (newest first) after its m Krylov
+// steps, as the flexible Arnoldi process allows (A Z = V H for the cycle's
+// search directions Z), with m + k <= 16.
 int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, int m, int max_iter, int check_every,
-              int* iters, double* rel_out) {
+              int* iters, double* rel_out, Aug* aug = nullptr) {
     pn_handle* h = c.h;
     const int64_t n = h->n_elems;  // a multiple of 32
     const int64_t n8 = n / 8;
@@ -858,22 +915,24 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
     double* S = h->d_scalars;
     const float sigma = float(std::sqrt(double(h->n_active)));
     const float inv_sigma = 1.0f / sigma;
-    const size_t v16bytes = size_t(m + 1) * n * sizeof(__half);
+    const int ka = aug ? aug->k : 0;
+    const int ms = m + ka;  // Hessenberg columns
+    const size_t v16bytes = size_t(ms + 1) * n * sizeof(__half);
     const size_t fbytes = 2 * size_t(n) * sizeof(float);  // w and vcur
     const size_t vbytes = ((v16bytes + 255) / 256) * 256 + fbytes;
-    const int ldh = m + 1;
-    const size_t dcount = size_t(ldh) * m + 4 * size_t(m + 1) + 16 * size_t(m + 1);
+    const int ldh = ms + 1;
+    const size_t dcount = size_t(ldh) * ms + 4 * size_t(ms + 1) + 16 * size_t(ms + 1);
     int rc = ensure_work(h, vbytes + dcount * sizeof(double) + 256);
     if (rc != PN_OK) return rc;
     __half* V16 = (__half*)h->d_work;
     float* w = (float*)((char*)h->d_work + ((v16bytes + 255) / 256) * 256);
     float* vcur = w + n;
     double* H = (double*)((char*)h->d_work + ((vbytes + 255) / 256) * 256);
-    double* cs = H + size_t(ldh) * m;
-    double* sn = cs + (m + 1);
-    double* g = sn + (m + 1);
-    double* y = g + (m + 1);
-    double* add = y + (m + 1);
+    double* cs = H + size_t(ldh) * ms;
+    double* sn = cs + (ms + 1);
+    double* g = sn + (ms + 1);
+    double* y = g + (ms + 1);
+    double* add = y + (ms + 1);
     c.ok(cudaMemsetAsync(S + S_TICKET, 0, sizeof(double), c.s), "gmres16: ticket");
     const double bnorm = std::sqrt(bnorm2);
     const double target = tol * (bnorm > 0.0 ? bnorm : 1.0);
@@ -897,14 +956,20 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
         if (!std::isfinite(res)) return pn_fail(h, PN_ERR_NONFINITE, "gmres16: non-finite residual");
         if (res <= target || total >= max_iter) break;
         c.pb();
-        k_gm_init<<<1, 32, 0, c.s>>>(g, m, S);
+        k_gm_init<<<1, 32, 0, c.s>>>(g, ms, S);
         k_first16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, sigma, S, (uint4*)V16, (float4*)vcur);
         c.launched("gmres16: init", 2);
         c.pe(PN_PROF_VECTOR, double(h->n_active) * (4.0 + 2.0 + 4.0));
+        const int na = aug ? std::min(aug->count, ka) : 0;  // corrections appended to this cycle
+        const int s = m + na;
+        auto zaug = [&](int q) {  // q-th newest stored correction
+            return aug->z + size_t((aug->newest - q + 2 * (ka + 1)) % (ka + 1)) * size_t(n);
+        };
         int j = 0;
-        for (; j < m && total < max_iter; ++j) {
+        for (; j < s && total < max_iter; ++j) {
             c.pb();
-            c.lk(pn::launch_op(h, pn::OP_APPLY, vcur, w, PN_F32, nullptr, c.s), "gmres16: A v",
+            const float* zin = j < m ? vcur : zaug(j - m);
+            c.lk(pn::launch_op(h, pn::OP_APPLY, zin, w, PN_F32, nullptr, c.s), "gmres16: A v",
                  pn::op_launch_count(h, PN_F32));
             c.pe(PN_PROF_APPLY, ob);
             c.pb();
@@ -920,7 +985,7 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
             c.launched("gmres16: maxpy");
             c.pe(PN_PROF_MAXPY, double(h->n_active) * (4.0 + 2.0 * (j + 1) + 2.0 + 4.0));
             ++total;
-            if ((j + 1) % every == 0 || j + 1 == m || total >= max_iter) {
+            if ((j + 1) % every == 0 || j + 1 == s || total >= max_iter) {
                 double r1 = 0.0;
                 if (!c.read(S_RES, 1, &r1)) return c.rc;
                 if (!std::isfinite(r1)) return pn_fail(h, PN_ERR_NONFINITE, "gmres16: non-finite Hessenberg");
@@ -932,9 +997,23 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
         }
         c.pb();
         k_gm_backsolve<<<1, 128, 0, c.s>>>(H, ldh, g, y, j);
-        k_update16<<<nb, 256, 0, c.s>>>(n8, (float4*)x, (const uint4*)V16, vs8, j, y, inv_sigma);
-        c.launched("gmres16: update", 2);
-        c.pe(PN_PROF_MAXPY, double(h->n_active) * (8.0 + 2.0 * j));
+        if (aug && j > 0) {
+            // x += V y + Z y_aug; the correction becomes the newest stored one
+            const int nk = std::min(j, m), nz = j - nk;
+            AugIn za{};
+            for (int q = 0; q < nz; ++q) za.z[q] = (const float4*)zaug(q);
+            const int slot = (aug->newest + 1) % (ka + 1);  // the oldest: not among the nz <= k read here
+            k_update16_aug<<<nb, 256, 0, c.s>>>(n8, (float4*)x, (const uint4*)V16, vs8, nk, y, inv_sigma, za, nz,
+                                                (float4*)(aug->z + size_t(slot) * size_t(n)));
+            aug->newest = slot;
+            aug->count = std::min(aug->count + 1, ka);
+            c.launched("gmres16: update", 2);
+            c.pe(PN_PROF_MAXPY, double(h->n_active) * (12.0 + 2.0 * nk + 4.0 * nz));
+        } else {
+            k_update16<<<nb, 256, 0, c.s>>>(n8, (float4*)x, (const uint4*)V16, vs8, j, y, inv_sigma);
+            c.launched("gmres16: update", 2);
+            c.pe(PN_PROF_MAXPY, double(h->n_active) * (8.0 + 2.0 * j));
+        }
         if (c.rc != PN_OK) return c.rc;
     }
     *iters += total;
@@ -1155,6 +1234,19 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
     int outer = 0, inner = 0;
     double rel = 0.0;
     int rc = PN_OK;
+    // LGMRES corrections (FP16-basis inner solver): kept across restarts and
+    // refinement steps (the same operator throughout)
+    Aug aug;
+    if (o.augment > 0 && o.basis == PN_BASIS_F16 && !net) {
+        aug.k = o.augment;
+        if (cudaMalloc(&aug.z, size_t(aug.k + 1) * n * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(r64);
+            cudaFree(r32);
+            cudaFree(d32);
+            return pn_fail(h, PN_ERR_ALLOC, "ir: cannot allocate the augmentation vectors");
+        }
+    }
     for (;;) {
         c.pb();
         c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r64, PN_F64, h->d_partials, c.s), "ir: residual", pn::op_launch_count(h, PN_F64));
@@ -1182,7 +1274,8 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
         double itol = o.inner_tol;
         if (rel > 0.0 && o.tol / rel > itol) itol = std::min(0.5, o.tol / rel);
         if (o.basis == PN_BASIS_F16 && !net)
-            rc = gmres_f16(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel);
+            rc = gmres_f16(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner, &inner_rel,
+                           aug.k > 0 ? &aug : nullptr);
         else
             rc = gmres<float>(c, d32, r32, 1.0, itol, o.restart, o.max_iter - inner, o.check_every, &inner,
                               &inner_rel, o.ortho, net, &st.precond_applications, &fell_back);
@@ -1198,6 +1291,7 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
     cudaFree(r64);
     cudaFree(r32);
     cudaFree(d32);
+    if (aug.z) cudaFree(aug.z);
     st.iterations = inner;
     st.outer_iterations = outer;
     st.rel_residual = rel;
@@ -1231,6 +1325,10 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
     if (o.basis != PN_BASIS_F32 && o.basis != PN_BASIS_F16) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad basis");
     if (o.basis == PN_BASIS_F16 && (o.solver != PN_SOLVER_IR_GMRES || o.restart > PN_MAX_MDOT))
         return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the FP16 basis needs PN_SOLVER_IR_GMRES and restart <= 16");
+    if (o.augment < 0 || o.augment > PN_MAX_AUG) return pn_fail(h, PN_ERR_ARG, "pn_solve: augment must be in [0, 4]");
+    if (o.augment > 0 && (o.basis != PN_BASIS_F16 || o.restart + o.augment > PN_MAX_MDOT))
+        return pn_fail(h, PN_ERR_UNSUPPORTED,
+                       "pn_solve: augment needs the FP16 basis (PN_SOLVER_IR_GMRES) and restart + augment <= 16");
     pn_solve_stats st{};
     Ctx c{h, (cudaStream_t)stream};
     pn_prof_reset(h, o.profile != 0);
@@ -1256,6 +1354,15 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
     }
     if (cudaStreamSynchronize(c.s) == cudaSuccess) pn_prof_drain(h);
     h->prof_on = false;
+    {
+        // a bounded wait of the TMA-staged operator that ran out
+        unsigned int fault = 0;
+        if (cudaMemcpy(&fault, h->d_scalars + PN_S_FAULT, sizeof(fault), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            fault != 0) {
+            cudaMemset(h->d_scalars + PN_S_FAULT, 0, sizeof(double));
+            rc = pn_fail(h, PN_ERR_TIMEOUT, "pn_solve: a wait of the TMA-staged operator ran out");
+        }
+    }
     const auto t1 = std::chrono::steady_clock::now();
     st.seconds = std::chrono::duration<double>(t1 - t0).count();
     st.status = rc;

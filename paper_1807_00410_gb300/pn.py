@@ -49,7 +49,8 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_cnn_targets", "pn_cnn_output", "pn_cnn_precondition", "pn_batch_create", "pn_batch_destroy",
            "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
-           "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path"]
+           "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
+           "pn_get_apply_kernel"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -75,7 +76,8 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
-                ("ortho", ctypes.c_int), ("precond", ctypes.c_void_p), ("basis", ctypes.c_int)]
+                ("ortho", ctypes.c_int), ("precond", ctypes.c_void_p), ("basis", ctypes.c_int),
+                ("augment", ctypes.c_int)]
 
 
 class _SolveStats(ctypes.Structure):
@@ -139,6 +141,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_batch_tune": (i, [vp, vp]),
         "pn_tune_apply": (i, [vp, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "pn_set_apply_tiling": (i, [vp, i]),
+        "pn_set_apply_kernel": (i, [vp, i]),
+        "pn_get_apply_kernel": (i, [vp, ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
         "pn_batch_set_mode": (i, [vp, i, ctypes.c_longlong]),
@@ -432,8 +436,9 @@ class System:
     def solve(self, u, solver: str = "cgls", tol: float = 1e-6, max_iter: int = 100000, restart: int = 60,
               inner_tol: float = 1e-2, max_outer: int = 50, check_every: int = 10, stream=None,
               raise_on_error: bool = True, profile: bool = False, ortho: str = "cgs2", precond=None,
-              basis: str = "f32") -> dict:
-        """Solve A u = Q in place (u is the initial guess).  Returns the stats."""
+              basis: str = "f32", augment: int = 0) -> dict:
+        """Solve A u = Q in place (u is the initial guess).  Returns the stats.
+        augment: LGMRES corrections appended per restart cycle (FP16 basis)."""
         up, dt = self._vec(u)
         o = _SolveOpts()
         self._lib.pn_default_solve_opts(ctypes.byref(o))
@@ -448,6 +453,7 @@ class System:
         o.profile = 1 if profile else 0
         o.ortho = {"cgs2": 0, "cgs1": 1}[ortho]
         o.basis = {"f32": 0, "f16": 1}[basis]
+        o.augment = int(augment)
         st = _SolveStats()
         rc = self._lib.pn_solve(self._h, up, ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
         stats = {"status": rc, "iterations": st.iterations, "outer_iterations": st.outer_iterations,
@@ -468,13 +474,26 @@ class System:
         return out
 
     def tune_apply(self, stream=None) -> dict:
-        """The operator autotuner (pn_tune_apply): keeps the fastest z-chunking."""
+        """The operator autotuner (pn_tune_apply): keeps the fastest main kernel
+        and z-chunking."""
         c, ms = ctypes.c_int(), ctypes.c_double()
         self._check(self._lib.pn_tune_apply(self._h, _stream_ptr(stream), ctypes.byref(c), ctypes.byref(ms)))
-        return {"ctas_per_sm": c.value, "ms": ms.value}
+        return {"ctas_per_sm": c.value, "ms": ms.value, "kernel": self.apply_kernel}
 
     def set_apply_tiling(self, ctas_per_sm: int):
         self._check(self._lib.pn_set_apply_tiling(self._h, int(ctas_per_sm)))
+
+    APPLY_KERNELS = {"register": 0, "tma": 1}
+
+    def set_apply_kernel(self, kernel: str):
+        """Main kernel of the tiled FP32 operator: "tma" or "register"."""
+        self._check(self._lib.pn_set_apply_kernel(self._h, self.APPLY_KERNELS[kernel]))
+
+    @property
+    def apply_kernel(self) -> str:
+        k = ctypes.c_int()
+        self._check(self._lib.pn_get_apply_kernel(self._h, ctypes.byref(k)))
+        return {v: n for n, v in self.APPLY_KERNELS.items()}[k.value]
 
     def cnn_features(self, v, scale: float = 1.0, stream=None):
         """Network input features of a padded FP32 vector: (R, R, R, K + 3)."""

@@ -359,10 +359,47 @@ def test_apply_tiling_plans_give_identical_outputs_and_tuner_picks_one():
         gpu.residual(x, r)
         assert torch.equal(y, ref_y) and torch.equal(r, ref_r)
     t = gpu.tune_apply()
-    assert t["ctas_per_sm"] in (1, 2, 4, 8) and t["ms"] > 0
+    assert t["ctas_per_sm"] in (1, 2, 4, 8) and t["ms"] > 0 and t["kernel"] in ("tma", "register")
     y = gpu.zeros(torch.float32)
     gpu.apply(x, y)
     assert torch.equal(y, ref_y)
+    gpu.close()
+
+
+@pytest.mark.parametrize("N,R", [(0, 5), (1, 2), (1, 33), (2, 9), (3, 17), (4, 12), (5, 29), (6, 6), (7, 11),
+                                 (3, 64), (7, 35)])
+def test_tma_and_register_operator_kernels_agree_bitwise(N, R):
+    """The TMA-staged and the register-staged tiled kernels compute every output
+    with the same operands in the same order: apply, transpose and residual
+    vectors are bitwise equal, for every z-chunking (chunks of one slice up to
+    the whole column), with NaN in every padding slot of the input; the
+    residual norm agrees to the rounding of its FP32 partial sums."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(N, R, 17 + N, 0.5, 40.0, 0.95, 0.3)
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    lay_o = opn.Layout(N, R)
+    rng = np.random.Generator(np.random.PCG64(N * 1000 + R))
+    x = gpu.from_planes([rng.uniform(-1, 1, sh) for sh in lay_o.shapes], dtype=torch.float32)
+    pad = gpu.from_planes([np.ones(sh) for sh in lay_o.shapes], dtype=torch.float32) == 0
+    x[pad] = float("nan")
+    out = {}
+    for kern in ("register", "tma"):
+        gpu.set_apply_kernel(kern)
+        assert gpu.apply_kernel == kern
+        for c in (1, 4, 16):
+            gpu.set_apply_tiling(c)
+            y, yt, r = gpu.zeros(torch.float32), gpu.zeros(torch.float32), gpu.zeros(torch.float32)
+            gpu.apply(x, y)
+            gpu.apply_t(x, yt)
+            rel = gpu.residual(x, r)
+            assert torch.isfinite(y).all() and torch.isfinite(r).all()
+            out[(kern, c)] = (y, yt, r, rel)
+    ref = out[("register", 4)]
+    for key, (y, yt, r, rel) in out.items():
+        assert torch.equal(y, ref[0]) and torch.equal(yt, ref[1]) and torch.equal(r, ref[2]), key
+        # ||r|| adds each thread's FP32 partial sums of r^2 (over other rows in
+        # the two kernels) in FP64: equal to FP32 rounding of those sums
+        assert abs(rel - ref[3]) <= 1e-6 * ref[3], key
     gpu.close()
 
 

@@ -67,5 +67,6 @@ def test_struct_sizes_match_header():
     from paper_1807_00410_gb300 import pn
     assert ctypes.sizeof(pn._Medium) == 64
     assert ctypes.sizeof(pn._Layout) == 5 * 8 + 16 + 2 * 64 * 4
-    assert ctypes.sizeof(pn._SolveOpts) == 64  # 4+4+8+4+4+8+4+4+4+4 = 48, an 8-byte pointer, an int + padding
+    assert ctypes.sizeof(pn._SolveOpts) == 64  # 4+4+8+4+4+8+4+4+4+4 = 48, an 8-byte pointer, two ints
+    assert pn._SolveOpts.augment.offset == 60
     assert ctypes.sizeof(pn._SolveStats) == 48
