@@ -83,6 +83,9 @@ def parse():
                          "--large-iters inner iterations: time per iteration and the residual reached")
     ap.add_argument("--large-iters", type=int, default=600)
     ap.add_argument("--large-sigma-min", type=float, default=0.1)
+    ap.add_argument("--seed", type=int, default=0, help="medium seed offset (the medium of rank r is seed + r)")
+    ap.add_argument("--augment", type=int, default=0,
+                    help="LGMRES: corrections of earlier restart cycles appended to each cycle (FP16 basis)")
     ap.add_argument("--apply-n", type=int, default=7)
     ap.add_argument("--apply-kernel", choices=["auto", "tma", "register"], default="auto",
                     help="--apply-only: main kernel of the tiled operator (auto: the autotuner's pick)")
@@ -349,14 +352,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     hbm_peak, peak_src = peaks()
-    p = pn_inputs.p5_64_fbm(rank)
+    p = pn_inputs.p5_64_fbm(rank + args.seed)
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
     lay = sysm.layout
     tiling = sysm.tune_apply()  # the operator's z-chunking, picked by timing (setup, untimed)
     u = sysm.zeros(torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     opts = dict(solver="ir", tol=1e-6, restart=args.restart, inner_tol=args.inner_tol, max_iter=30000,
-                check_every=5, ortho=args.ortho, basis=args.basis)
+                check_every=5, ortho=args.ortho, basis=args.basis,
+                augment=args.augment if args.basis == "f16" else 0)
     for _ in range(args.warmup):
         u.zero_()
         sysm.solve(u, **opts)
@@ -391,7 +395,7 @@ def run_ours(args):
                     agg[key] += v[key]
     # the same solves with the other basis element type, for comparison
     alt = "f32" if args.basis == "f16" else "f16"
-    alt_opts = dict(opts, basis=alt)
+    alt_opts = dict(opts, basis=alt, augment=0)  # augmentation needs the FP16 basis
     alt_ms, alt_st = [], None
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -479,10 +483,11 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f16-basis+f32+f64" if args.basis == "f16" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart, "ortho": args.ortho,
+            "config": {"workload": WORKLOAD, "dof": lay.n_active, "restart": args.restart,
+                       "augment": opts["augment"], "ortho": args.ortho,
                        "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"],
                        "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
-                       "replicas": "one independent problem per GPU (seed = rank)"},
+                       "replicas": f"one independent problem per GPU (medium seed = {args.seed} + rank)"},
             "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
                       "rel_residual": stats[-1]["rel_residual"], "wall_s": wall},
             "roofline": roofline,

@@ -214,7 +214,7 @@ typedef struct {
                             restart <= 16): about 40 % fewer bytes per Arnoldi
                             step; the stored basis rounds at ~5e-4 relative, so
                             inner_tol should stay >= 1e-3 */
-    int augment;         /* PN_SOLVER_IR_GMRES with PN_BASIS_F16: k in [0, 4] corrections
+    int augment;         /* PN_SOLVER_IR_GMRES with PN_BASIS_F16: k in [0, 8] corrections
                             of earlier restart cycles (x_i - x_{i-1}, newest first)
                             appended to each cycle's m Krylov directions (LGMRES(m, k));
                             kept across restarts and refinement steps; restart + k

@@ -28,6 +28,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <dlfcn.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -379,14 +381,21 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// The driver's tensor-map encoder: through the runtime's entry-point query,
+// else from the driver library itself (some profiler shims do not forward the
+// query); null if neither has it (the register-staged kernel then runs).
 EncodeTiled encode_fn() {
     static const EncodeTiled fn = []() -> EncodeTiled {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && p)
+            return reinterpret_cast<EncodeTiled>(p);
+        cudaGetLastError();
+        void* lib = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
+        if (!lib) return nullptr;
+        p = dlsym(lib, "cuTensorMapEncodeTiled");
         return reinterpret_cast<EncodeTiled>(p);
     }();
     return fn;

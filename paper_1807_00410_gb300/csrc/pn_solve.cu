@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(256) k_update16(int64_t n8, float4* __restrict
 // Error approximations appended to each restart cycle (LGMRES: the cycle's
 // search space is the m Krylov vectors plus the corrections x_i - x_{i-1} of
 // the last k cycles, which carry the directions restarting loses).
-#define PN_MAX_AUG 4
+#define PN_MAX_AUG 8
 struct Aug {
     float* z = nullptr;  // ring of k + 1 FP32 vectors (n elements each)
     int k = 0;           // corrections appended per cycle
@@ -1325,7 +1325,7 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
     if (o.basis != PN_BASIS_F32 && o.basis != PN_BASIS_F16) return pn_fail(h, PN_ERR_ARG, "pn_solve: bad basis");
     if (o.basis == PN_BASIS_F16 && (o.solver != PN_SOLVER_IR_GMRES || o.restart > PN_MAX_MDOT))
         return pn_fail(h, PN_ERR_UNSUPPORTED, "pn_solve: the FP16 basis needs PN_SOLVER_IR_GMRES and restart <= 16");
-    if (o.augment < 0 || o.augment > PN_MAX_AUG) return pn_fail(h, PN_ERR_ARG, "pn_solve: augment must be in [0, 4]");
+    if (o.augment < 0 || o.augment > PN_MAX_AUG) return pn_fail(h, PN_ERR_ARG, "pn_solve: augment must be in [0, 8]");
     if (o.augment > 0 && (o.basis != PN_BASIS_F16 || o.restart + o.augment > PN_MAX_MDOT))
         return pn_fail(h, PN_ERR_UNSUPPORTED,
                        "pn_solve: augment needs the FP16 basis (PN_SOLVER_IR_GMRES) and restart + augment <= 16");

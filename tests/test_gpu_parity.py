@@ -337,6 +337,44 @@ def test_ir_with_fp16_basis_meets_oracle_residual(N, R, restart):
     gpu.close()
 
 
+@pytest.mark.parametrize("N,R,restart,augment", [(5, 12, 13, 2), (1, 20, 12, 4), (3, 12, 8, 1), (7, 8, 14, 2),
+                                                  (3, 33, 13, 3)])
+def test_ir_lgmres_meets_oracle_residual(N, R, restart, augment):
+    """LGMRES(m, k): each restart cycle of the FP16-basis inner GMRES appends the
+    corrections of up to k earlier cycles (kept across refinement steps) to its
+    m Krylov directions.  The solution meets the oracle residual <= 1e-6, and
+    (where the oracle's sparse LU is quick) L^{0,0} within 1e-5 of the direct
+    solution; the iteration count stays within the plain GMRES(m + k) solve's
+    plus a margin."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(N, R, 21, 0.5, 40.0, 0.95, 0.3)
+    S = opn.assemble(N, R, opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00))
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    ua = gpu.zeros(torch.float64)
+    sta = gpu.solve(ua, solver="ir", tol=1e-6, restart=restart, ortho="cgs1", basis="f16", augment=augment)
+    up = gpu.zeros(torch.float64)
+    stp = gpu.solve(up, solver="ir", tol=1e-6, restart=restart + augment, ortho="cgs1", basis="f16")
+    assert sta["rel_residual"] <= 1e-6
+    uo = S.layout.join(gpu.to_planes(ua))
+    assert opn.relative_residual(S.A, S.b, uo) <= 1.0001e-6
+    if S.A.shape[0] <= 70000:
+        ref = S.layout.split(opn.solve_direct(S))[0]
+        assert np.linalg.norm(S.layout.split(uo)[0] - ref) / np.linalg.norm(ref) <= 1e-5
+    assert sta["iterations"] <= 1.5 * stp["iterations"] + 2 * (restart + augment)
+    gpu.close()
+
+
+def test_lgmres_option_limits():
+    from paper_1807_00410_gb300 import PnError, System
+    p = pn_inputs.fbm_point(3, 8, 2, 0.5, 40.0, 0.95, 0.3)
+    gpu = System(3, 8, p.sigma_t, p.albedo, p.g, p.Q00)
+    for kw in ({"basis": "f32", "augment": 2}, {"basis": "f16", "restart": 15, "augment": 2},
+               {"basis": "f16", "restart": 8, "augment": 9}, {"basis": "f16", "restart": 8, "augment": -1}):
+        with pytest.raises(PnError):
+            gpu.solve(gpu.zeros(torch.float64), solver="ir", **{"restart": 10, **kw})
+    gpu.close()
+
+
 def test_apply_tiling_plans_give_identical_outputs_and_tuner_picks_one():
     """Every z-chunking of the tiled FP32 operator computes each output with the
     same operands in the same order: apply and residual vectors are bitwise
