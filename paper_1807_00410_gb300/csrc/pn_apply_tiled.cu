@@ -295,7 +295,8 @@ template <int N, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
     if (a.live && !*a.live) return;  // uniform over the grid
     extern __shared__ float smem[];
-    const int tx = threadIdx.x, ty = threadIdx.y, grp = threadIdx.z;
+    // warp w runs group w % 4 (one group's code per scheduler; see pn_apply_tma.cu)
+    const int tx = threadIdx.x, grp = threadIdx.y, ty = threadIdx.z;
     const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
     const int za = blockIdx.z * a.zc;
     const int zb = min(za + a.zc, a.R + 1);
@@ -503,7 +504,7 @@ TiledPlan plan_for(const pn_handle* h) {
     const int zc = (R + 1 + nzc - 1) / nzc;
     nzc = (R + 1 + zc - 1) / zc;
     p.grid = dim3(nxt, nyt, nzc);
-    p.block = dim3(tiled::TX, TY, tiled::NG);
+    p.block = dim3(tiled::TX, tiled::NG, TY);
     p.zc = zc;
     p.smem = (size_t(2) * h->K * G::SLICE + 4 * G::GSL) * sizeof(float);
     p.x_end = std::min<int>(int(h->pitch_x), nxt * tiled::TX);

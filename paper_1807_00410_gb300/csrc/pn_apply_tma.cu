@@ -344,7 +344,10 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
     float* sg = ring + L.floats;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sg + 4 * GSL);
     const uint32_t bar_s = smem_u32(bars);
-    const int tx = threadIdx.x, ty = threadIdx.y, grp = threadIdx.z;
+    // warp w runs group w % 4: each of the SM's four schedulers (warps are
+    // spread over them by warp index) executes one group's code, so its
+    // instruction cache holds one of the four specialised bodies
+    const int tx = threadIdx.x, grp = threadIdx.y, ty = threadIdx.z;
     const int tid = tx + TX * (ty + TY * grp);
     const int za = blockIdx.z * a.zc;
     const int zb = min(za + a.zc, a.R + 1);
@@ -473,7 +476,7 @@ cudaError_t launch_n(const Maps& m, const Args& a, dim3 grid, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    kern<<<grid, dim3(TX, TY, NG), bytes, s>>>(m, a);
+    kern<<<grid, dim3(TX, NG, TY), bytes, s>>>(m, a);
     return cudaGetLastError();
 }
 

@@ -259,6 +259,22 @@ void launch_maxpy<double>(int nb, cudaStream_t s, int64_t n, double* w, const do
 //   S[S_NRM2] = ||w||^2 after orthogonalisation.
 // Applies the previous rotations, forms rotation j, updates g and writes
 // |g[j+1]| to S[S_RES] and 1/||w|| to S[S_SCALE].
+// sum_{b = lane, lane + 32, ...} p[b] in that order (the order of a plain
+// loop), with eight loads issued before their adds: the last block's
+// reduction is a chain of L2 reads otherwise.
+__device__ __forceinline__ double lane_sum_partials(const double* p, int nb, int lane) {
+    double t = 0.0;
+    for (int b0 = lane; b0 < nb; b0 += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = b0 + 32 * u < nb ? __ldcg(p + b0 + 32 * u) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (b0 + 32 * u < nb) t += v[u];
+    }
+    return t;
+}
+
 __device__ __forceinline__ void givens_core(double* H, int ldh, const double* add, double* cs, double* sn,
                                             double* g, int j, double* S, int pythagoras, double nrm2_in) {
     double* col = H + int64_t(j) * ldh;
@@ -361,8 +377,7 @@ __global__ void __launch_bounds__(256) k_mdot_givens_f32(int64_t n4, const float
     __threadfence();
     for (int v = warp; v <= NV; v += 8) {
         if (v < nv || v == NV) {
-            double t = 0.0;
-            for (int b = lane; b < nb; b += 32) t += __ldcg(partials + int64_t(v) * nb + b);
+            double t = lane_sum_partials(partials + int64_t(v) * nb, nb, lane);
             for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
             if (lane == 0) tot[v] = t;
         }
@@ -700,8 +715,7 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
     __threadfence();
     for (int v = warp; v <= NV; v += 8) {
         if (v < nv || v == NV) {
-            double t = 0.0;
-            for (int b = lane; b < nb; b += 32) t += __ldcg(partials + int64_t(v) * nb + b);
+            double t = lane_sum_partials(partials + int64_t(v) * nb, nb, lane);
             for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
             if (lane == 0) tot[v] = t;
         }
