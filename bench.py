@@ -37,17 +37,14 @@ WORKLOAD = "P5 64^3 fBm sigma_t[0.5,40] albedo 0.95 g 0.3 point source, solve to
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel class and
-# workload; None until a capture of the current kernel exists.
 # DRAM traffic of the dominant kernel from one ncu capture of the current
-# kernel (profiles/k_mdot_givens_f32_p5_64_ir_solve.md,
-# profiles/k_maxpy16_p5_64_ir_solve.md, profiles/k_mdot16_givens_p5_64_ir_solve.md):
-# dram bytes read + written over the
-# algorithmic bytes of the same launches.  Launches differ in the number of
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic
+# bytes of the same launches; profiles/k_maxpy16_p5_64_ir_solve.md), keyed by
+# kernel class, workload and basis type.  Launches differ in the number of
 # basis vectors, so the mean ratio is applied to this run's average
-# algorithmic bytes per launch.  An entry is removed when its kernel changes.
-NCU_TRAFFIC = {("mdot", "p5_64", "f32"): 1.083, ("maxpy", "p5_64", "f16"): 0.911, ("mdot", "p5_64", "f16"): 1.077}
+# algorithmic bytes per launch.  An entry is removed when its kernel changes
+# (traffic is then reported as null).
+NCU_TRAFFIC = {("maxpy", "p5_64", "f16"): 0.911}
 
 
 def parse():
@@ -88,7 +85,7 @@ def parse():
                     help="LGMRES: corrections of earlier restart cycles appended to each cycle (FP16 basis)")
     ap.add_argument("--apply-n", type=int, default=7)
     ap.add_argument("--apply-kernel", choices=["auto", "tma", "register"], default="auto",
-                    help="--apply-only: main kernel of the tiled operator (auto: the autotuner's pick)")
+                    help="main kernel of the tiled operator (auto: the autotuner's pick)")
     ap.add_argument("--apply-r", type=int, default=256)
     return ap.parse_args()
 
@@ -357,7 +354,10 @@ def run_ours(args):
     p = pn_inputs.p5_64_fbm(rank + args.seed)
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
     lay = sysm.layout
-    tiling = sysm.tune_apply()  # the operator's z-chunking, picked by timing (setup, untimed)
+    tiling = sysm.tune_apply()  # the operator's kernel and z-chunking, picked by timing (setup, untimed)
+    if args.apply_kernel != "auto":
+        sysm.set_apply_kernel(args.apply_kernel)
+        tiling["kernel"] = sysm.apply_kernel
     u = sysm.zeros(torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     opts = dict(solver="ir", tol=1e-6, restart=args.restart, inner_tol=args.inner_tol, max_iter=30000,
