@@ -39,12 +39,13 @@ L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic of the dominant kernel from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic
-# bytes of the same launches; profiles/k_maxpy16_p5_64_ir_solve.md), keyed by
+# bytes of the same launches; profiles/k_maxpy16_p5_64_ir_solve.md,
+# profiles/k_mdot16_givens_p5_64_ir_solve.md), keyed by
 # kernel class, workload and basis type.  Launches differ in the number of
 # basis vectors, so the mean ratio is applied to this run's average
 # algorithmic bytes per launch.  An entry is removed when its kernel changes
 # (traffic is then reported as null).
-NCU_TRAFFIC = {("maxpy", "p5_64", "f16"): 0.911}
+NCU_TRAFFIC = {("maxpy", "p5_64", "f16"): 0.911, ("mdot", "p5_64", "f16"): 1.077}
 
 
 def parse():
