@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="many-instance workload: batched solve of --batch-count systems vs one-by-one solves")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-restart", type=int, default=15, help="--batched: GMRES restart of both arms")
     ap.add_argument("--batch-seed", type=int, default=0)
     ap.add_argument("--batch-rmin", type=int, default=24)
     ap.add_argument("--batch-rmax", type=int, default=96)
@@ -82,6 +83,8 @@ def parse():
     ap.add_argument("--large-iters", type=int, default=600)
     ap.add_argument("--large-sigma-min", type=float, default=0.1)
     ap.add_argument("--seed", type=int, default=0, help="medium seed offset (the medium of rank r is seed + r)")
+    ap.add_argument("--no-l2-resident", action="store_true",
+                    help="do not keep the solver's FP32 step vectors resident in L2")
     ap.add_argument("--augment", type=int, default=4,
                     help="LGMRES: corrections of earlier restart cycles appended to each cycle (FP16 basis)")
     ap.add_argument("--apply-n", type=int, default=7)
@@ -356,6 +359,7 @@ def run_ours(args):
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
     lay = sysm.layout
     tiling = sysm.tune_apply()  # the operator's kernel and z-chunking, picked by timing (setup, untimed)
+    sysm.set_l2_residency(not args.no_l2_resident)
     if args.apply_kernel != "auto":
         sysm.set_apply_kernel(args.apply_kernel)
         tiling["kernel"] = sysm.apply_kernel
@@ -491,7 +495,7 @@ def run_ours(args):
                                   if opts["augment"] else
                                   f"FP64 iterative refinement around FP32 GMRES({args.restart})"),
                        "restart": args.restart,
-                       "augment": opts["augment"], "ortho": args.ortho,
+                       "augment": opts["augment"], "ortho": args.ortho, "l2_resident": not args.no_l2_resident,
                        "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"],
                        "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
                        "replicas": f"one independent problem per GPU (medium seed = {args.seed} + rank)"},
@@ -570,13 +574,15 @@ def run_threshold_sweep(args):
             sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=smin)
             u = sysm.zeros(torch.float64)
             st = sysm.solve(u, solver="ir", tol=1e-6, restart=args.restart, ortho=args.ortho, max_iter=200000,
+                            basis=args.basis, augment=args.augment if args.basis == "f16" else 0,
                             raise_on_error=False)
             rows.append({"N": N, "sigma_t_min": smin, "iterations": st["iterations"],
                          "outer": st["outer_iterations"], "seconds": st["seconds"],
                          "rel_residual": st["rel_residual"], "status": st["status"]})
             sysm.close()
     print(json.dumps({"mode": "threshold-sweep", "workload": "64^3 thresholded-fBm cloud, albedo 0.99, g 0.6, "
-                      "point source, FP32 GMRES + FP64 IR to 1e-6", "rows": rows}), flush=True)
+                      f"point source, FP32 LGMRES({args.restart}, {args.augment}) ({args.basis} basis) + FP64 IR "
+                      "to 1e-6", "rows": rows}), flush=True)
 
 
 def run_checkerboard(args):
@@ -641,7 +647,7 @@ def run_batched(args):
             Q = ppn.single_scatter_beam(b.N, st, b.albedo, b.g, axis, sign, radius, centre)
         systems.append(System(b.N, b.R, st, b.albedo, b.g, Q))
     dof = sum(s.layout.n_active for s in systems)
-    batch = Batch(systems, restart=args.restart, tune=True)
+    batch = Batch(systems, restart=args.batch_restart, tune=True)
     tiling = batch.tiling()
 
     def timed(fn):
@@ -666,7 +672,7 @@ def run_batched(args):
         out = []
         for s in systems:
             u = s.zeros(torch.float64)
-            out.append(s.solve(u, solver="ir", tol=1e-6, restart=args.restart, ortho=args.ortho, max_iter=200000,
+            out.append(s.solve(u, solver="ir", tol=1e-6, restart=args.batch_restart, ortho=args.ortho, max_iter=200000,
                                raise_on_error=False))
         return out
     seq_ms, seq_stats = timed(one_by_one)
@@ -675,7 +681,7 @@ def run_batched(args):
         "mode": "batched", "workload": f"{len(systems)} instances (pn_inputs.batch_instances, seed "
         f"{args.batch_seed}): grids {args.batch_rmin}..{args.batch_rmax} per axis, N in {{1,3,5}}, fBm sigma_t in "
         f"[0.1, 60], albedo 0.7..0.99, "
-        f"g 0..0.7, point or beam source; FP32 GMRES({args.restart}) + FP64 IR to 1e-6",
+        f"g 0..0.7, point or beam source; FP32 GMRES({args.batch_restart}) + FP64 IR to 1e-6",
         "instances": len(systems), "dof": dof, "ms": best, "ms_median": statistics.median(times),
         "solves_per_s": len(systems) / (best * 1e-3), "converged": ok,
         "iterations_max": max(its), "iterations_mean": float(np.mean(its)),

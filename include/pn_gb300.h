@@ -479,6 +479,18 @@ int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm);
 int pn_set_apply_kernel(pn_handle* h, int kernel);
 int pn_get_apply_kernel(const pn_handle* h, int* kernel);
 
+/*
+ * L2 residency of the FP16-basis GMRES (PN_BASIS_F16): while it runs, its two
+ * FP32 step vectors (A v and the newest basis vector, each written and read
+ * again within every Arnoldi step) are kept in L2 by a persisting
+ * access-policy window on the solver's stream, up to the device's persisting
+ * capacity; afterwards the window is closed, the persisting lines released and
+ * the context's persisting-lines limit restored.  pn_solve runs on a stream of
+ * its own, ordered after `stream` on entry and before it on exit.  on = 1
+ * (default) or 0.  Results do not depend on it.
+ */
+int pn_set_l2_residency(pn_handle* h, int on);
+
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */
 #define PN_PROF_RESIDUAL 1   /* residual operator launches */

@@ -119,6 +119,11 @@ void free_all(pn_handle* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     h->side = nullptr;
     h->ev_fork = h->ev_join = nullptr;
+    if (h->solve_s) cudaStreamDestroy(h->solve_s);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    h->solve_s = nullptr;
+    h->ev_in = h->ev_out = nullptr;
 }
 
 }  // namespace
@@ -554,6 +559,12 @@ int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm) {
     if (!h) return PN_ERR_ARG;
     if (ctas_per_sm < 1 || ctas_per_sm > 16) return pn_fail(h, PN_ERR_ARG, "pn_set_apply_tiling: ctas_per_sm in [1, 16]");
     h->tile_ctas_per_sm = ctas_per_sm;
+    return PN_OK;
+}
+
+int pn_set_l2_residency(pn_handle* h, int on) {
+    if (!h) return PN_ERR_ARG;
+    h->l2_resident = on ? 1 : 0;
     return PN_OK;
 }
 

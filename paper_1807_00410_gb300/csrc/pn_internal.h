@@ -60,6 +60,12 @@ struct pn_handle {
     // concurrently with the tiled kernel (fork / join events)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pn_solve runs on this stream (joined to the caller's stream by events on
+    // entry and exit), which carries the L2 access-policy window of the FP16-
+    // basis GMRES (pn_set_l2_residency)
+    cudaStream_t solve_s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int l2_resident = 1;
     int64_t nz_box = 0;  // z-slices of a plane box: R + 1 (3D) or 1 (2D)
     double h = 0.0;
     double g = 0.0;  // Henyey-Greenstein mean cosine

@@ -915,6 +915,61 @@ __global__ void __launch_bounds__(256) k_update16_aug(int64_t n8, float4* __rest
     }
 }
 
+// Keeps [base, base + bytes) resident in L2 for the launches of stream s while
+// it lives: a persisting access-policy window (at most the device's persisting
+// capacity; the hit ratio covers the rest of the window proportionally).  The
+// stream is the solver's own (the handle's solve stream).  On destruction the
+// window is closed, the persisting lines are released and the context's
+// persisting-lines limit is put back.
+struct L2Resident {
+    cudaStream_t s = nullptr;
+    bool on = false;
+    size_t old_limit = 0;
+    L2Resident(cudaStream_t st, void* base, size_t bytes, bool enable) : s(st) {
+        if (!enable || bytes == 0 || st == nullptr) return;
+        int dev = 0, maxp = 0, maxw = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess || maxp <= 0 ||
+            maxw <= 0) {
+            cudaGetLastError();
+            return;
+        }
+        const size_t win = std::min(bytes, size_t(maxw));
+        const size_t lim = std::min(win, size_t(maxp));
+        if (cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess ||
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, lim) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaStreamAttrValue v{};
+        v.accessPolicyWindow.base_ptr = base;
+        v.accessPolicyWindow.num_bytes = win;
+        v.accessPolicyWindow.hitRatio = float(double(lim) / double(win));
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        if (cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess) {
+            cudaGetLastError();
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+            return;
+        }
+        on = true;
+    }
+    ~L2Resident() {
+        if (!on) return;
+        cudaStreamAttrValue v{};
+        v.accessPolicyWindow.num_bytes = 0;
+        v.accessPolicyWindow.hitRatio = 0.0f;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+        cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &v);
+        cudaStreamSynchronize(s);
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+        cudaGetLastError();
+    }
+};
+
 // Restarted GMRES(m), CGS1, FP32 arithmetic with the basis in FP16 (m <= 16).
 // Same contract as gmres<float>.  With aug (k > 0) each cycle that has stored
 // corrections appends up to k of them (newest first) after its m Krylov
@@ -947,6 +1002,8 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
     double* g = sn + (ms + 1);
     double* y = g + (ms + 1);
     double* add = y + (ms + 1);
+    // w and vcur (adjacent): written and read again within every Arnoldi step
+    L2Resident l2(c.s, w, 2 * size_t(n) * sizeof(float), h->l2_resident != 0);
     c.ok(cudaMemsetAsync(S + S_TICKET, 0, sizeof(double), c.s), "gmres16: ticket");
     const double bnorm = std::sqrt(bnorm2);
     const double target = tol * (bnorm > 0.0 ? bnorm : 1.0);
@@ -1344,7 +1401,20 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
         return pn_fail(h, PN_ERR_UNSUPPORTED,
                        "pn_solve: augment needs the FP16 basis (PN_SOLVER_IR_GMRES) and restart + augment <= 16");
     pn_solve_stats st{};
-    Ctx c{h, (cudaStream_t)stream};
+    // the solve runs on the handle's own stream, ordered after the caller's
+    // stream on entry and before it on exit
+    cudaStream_t user = (cudaStream_t)stream;
+    if (!h->solve_s) {
+        if (cudaStreamCreateWithFlags(&h->solve_s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaError_t e = cudaGetLastError();
+            return pn_cuda_fail(h, e != cudaSuccess ? e : cudaErrorUnknown, "pn_solve: solve stream");
+        }
+    }
+    if (cudaEventRecord(h->ev_in, user) != cudaSuccess || cudaStreamWaitEvent(h->solve_s, h->ev_in, 0) != cudaSuccess)
+        return pn_cuda_fail(h, cudaGetLastError(), "pn_solve: stream join");
+    Ctx c{h, h->solve_s};
     pn_prof_reset(h, o.profile != 0);
     const auto t0 = std::chrono::steady_clock::now();
     int rc;
@@ -1368,6 +1438,10 @@ extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_sol
     }
     if (cudaStreamSynchronize(c.s) == cudaSuccess) pn_prof_drain(h);
     h->prof_on = false;
+    if (cudaEventRecord(h->ev_out, c.s) != cudaSuccess || cudaStreamWaitEvent(user, h->ev_out, 0) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        if (rc == PN_OK) rc = pn_cuda_fail(h, e, "pn_solve: stream join");
+    }
     {
         // a bounded wait of the TMA-staged operator that ran out
         unsigned int fault = 0;

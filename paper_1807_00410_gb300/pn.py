@@ -50,7 +50,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
-           "pn_get_apply_kernel"]
+           "pn_get_apply_kernel", "pn_set_l2_residency"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -143,6 +143,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_set_apply_tiling": (i, [vp, i]),
         "pn_set_apply_kernel": (i, [vp, i]),
         "pn_get_apply_kernel": (i, [vp, ctypes.POINTER(i)]),
+        "pn_set_l2_residency": (i, [vp, i]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
         "pn_batch_set_mode": (i, [vp, i, ctypes.c_longlong]),
@@ -488,6 +489,10 @@ class System:
     def set_apply_kernel(self, kernel: str):
         """Main kernel of the tiled FP32 operator: "tma" or "register"."""
         self._check(self._lib.pn_set_apply_kernel(self._h, self.APPLY_KERNELS[kernel]))
+
+    def set_l2_residency(self, on: bool):
+        """Keep the FP16-basis GMRES's two FP32 step vectors resident in L2."""
+        self._check(self._lib.pn_set_l2_residency(self._h, 1 if on else 0))
 
     @property
     def apply_kernel(self) -> str:

@@ -364,6 +364,35 @@ def test_ir_lgmres_meets_oracle_residual(N, R, restart, augment):
     gpu.close()
 
 
+def test_solve_orders_after_the_callers_stream_and_l2_residency_changes_no_bit():
+    """pn_solve runs on the handle's own stream, joined to the caller's: an
+    initial guess written on the caller's stream behind a long fill is seen
+    (a converged guess needs no iteration).  Keeping the step vectors resident
+    in L2 changes no bit of the solution."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(5, 20, 4, 0.5, 40.0, 0.95, 0.3)
+    gpu = System(5, 20, p.sigma_t, p.albedo, p.g, p.Q00)
+    opts = dict(solver="ir", tol=1e-6, restart=12, ortho="cgs1", basis="f16", augment=4)
+    u_on = gpu.zeros(torch.float64)
+    st_on = gpu.solve(u_on, **opts)
+    gpu.set_l2_residency(False)
+    u_off = gpu.zeros(torch.float64)
+    st_off = gpu.solve(u_off, **opts)
+    gpu.set_l2_residency(True)
+    assert torch.equal(u_on, u_off) and st_on["iterations"] == st_off["iterations"]
+    s = torch.cuda.Stream()
+    u = gpu.zeros(torch.float64)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        big = torch.empty(1 << 28, dtype=torch.float32, device="cuda")
+        for _ in range(4):
+            big.fill_(1.0)
+        u.copy_(u_on)
+        st = gpu.solve(u, stream=s, **opts)
+    assert st["iterations"] == 0 and st["rel_residual"] <= 1e-6
+    gpu.close()
+
+
 def test_lgmres_option_limits():
     from paper_1807_00410_gb300 import PnError, System
     p = pn_inputs.fbm_point(3, 8, 2, 0.5, 40.0, 0.95, 0.3)
