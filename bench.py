@@ -288,7 +288,8 @@ def apply_scan(torch, System, pn_inputs, hbm_peak):
         gbs = bytes_alg / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs,
                      "frac_of_hbm": gbs / hbm_peak, "dof": lay.n_active, "bytes_per_apply": bytes_alg,
-                     "ctas_per_sm": tiling["ctas_per_sm"], "kernel": tiling["kernel"]}
+                     "ctas_per_sm": tiling["ctas_per_sm"], "kernel": tiling["kernel"],
+                     "face_serial": tiling["face_serial"]}
         sysm.close()
         del x, ys
         torch.cuda.empty_cache()
@@ -497,6 +498,7 @@ def run_ours(args):
                        "restart": args.restart,
                        "augment": opts["augment"], "ortho": args.ortho, "l2_resident": not args.no_l2_resident,
                        "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"],
+                       "apply_face_serial": tiling["face_serial"],
                        "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
                        "replicas": f"one independent problem per GPU (medium seed = {args.seed} + rank)"},
             "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
@@ -553,7 +555,7 @@ def run_apply_only(args):
                       "gdof_s": lay.n_active / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac": gbs / hbm_peak,
                       "peak": hbm_peak, "peak_source": peak_src, "dof": lay.n_active,
                       "bytes_per_apply": bytes_alg, "ctas_per_sm": tiling["ctas_per_sm"],
-                      "kernel": sysm.apply_kernel, "steps": args.steps,
+                      "kernel": sysm.apply_kernel, "face_serial": sysm.apply_plan["face_serial"], "steps": args.steps,
                       "warmup": args.warmup}), flush=True)
     sysm.close()
 

@@ -446,14 +446,18 @@ int pn_batch_get_op_path(const pn_batch* batch, int* tiled);
  * Tile plan of the FP32 operator (3D handles): the z-marching tiled kernel
  * splits each (x, y) tile column into z chunks so that about ctas_per_sm CTAs
  * per SM are launched (default 4; larger values shorten the chunks).
- * pn_tune_apply times the FP32 apply for ctas_per_sm in {1, 2, 4, 8} on this
- * handle (allocates two scratch vectors; synchronises `stream`), keeps the
- * fastest and reports it and its time (either output may be NULL);
- * pn_set_apply_tiling sets it directly (1..16).  Results do not depend on the
- * plan except for the order of the residual's FP64 partial sums.
+ * pn_tune_apply times the FP32 apply for ctas_per_sm in {1, 2, 4, 8}, each main
+ * kernel (below) and both schedules of the face-column kernel (the outputs
+ * right of the tiles: concurrently on a side stream, or after the main kernel)
+ * on this handle (allocates two scratch vectors; synchronises `stream`), keeps
+ * the fastest and reports its ctas_per_sm and time (either output may be
+ * NULL); pn_get_apply_plan reports the whole plan (any output may be NULL);
+ * pn_set_apply_tiling sets ctas_per_sm directly (1..16).  Results do not
+ * depend on the plan except for the order of the residual's partial sums.
  */
 int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms);
 int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm);
+int pn_get_apply_plan(const pn_handle* h, int* ctas_per_sm, int* kernel, int* face_serial);
 
 /*
  * Main kernel of the tiled FP32 operator (3D handles with the vacuum

@@ -562,6 +562,14 @@ int pn_set_apply_tiling(pn_handle* h, int ctas_per_sm) {
     return PN_OK;
 }
 
+int pn_get_apply_plan(const pn_handle* h, int* ctas_per_sm, int* kernel, int* face_serial) {
+    if (!h) return PN_ERR_ARG;
+    if (ctas_per_sm) *ctas_per_sm = h->tile_ctas_per_sm;
+    if (kernel) pn_get_apply_kernel(h, kernel);
+    if (face_serial) *face_serial = h->face_serial;
+    return PN_OK;
+}
+
 int pn_set_l2_residency(pn_handle* h, int on) {
     if (!h) return PN_ERR_ARG;
     h->l2_resident = on ? 1 : 0;
@@ -601,14 +609,15 @@ int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms)
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int cands[] = {1, 2, 4, 8};
-    int best = h->tile_ctas_per_sm, best_k = h->tile_kernel;
+    int best = h->tile_ctas_per_sm, best_k = h->tile_kernel, best_f = h->face_serial;
     float best_t = 1e30f;
     const int nk = pn::tma_serves(h) ? 2 : 1;
-    for (int ci = 0; ci < 4 * nk; ++ci) {
+    for (int ci = 0; ci < 8 * nk; ++ci) {
         const int c = cands[ci % 4];
         if (e != cudaSuccess) break;
         h->tile_ctas_per_sm = c;
-        h->tile_kernel = nk == 2 ? ci / 4 : PN_APPLY_KERNEL_REGISTER;
+        h->face_serial = (ci / 4) % 2;
+        h->tile_kernel = nk == 2 ? ci / 8 : PN_APPLY_KERNEL_REGISTER;
         float tsum = 0.0f;
         for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
             e = cudaEventRecord(e0, s);
@@ -623,10 +632,12 @@ int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms)
             best_t = tsum / 5.0f;
             best = c;
             best_k = h->tile_kernel;
+            best_f = h->face_serial;
         }
     }
     h->tile_ctas_per_sm = best;
     h->tile_kernel = best_k;
+    h->face_serial = best_f;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(x);

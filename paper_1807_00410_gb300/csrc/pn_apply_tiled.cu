@@ -548,8 +548,9 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
         configured[N] = true;
     }
     // columns right of the tiles and plane tails: disjoint outputs and partial
-    // slots, same inputs; on the handle's side stream, concurrently
-    cudaStream_t fs = h->side ? h->side : s;
+    // slots, same inputs; on the handle's side stream, concurrently, or after
+    // the main kernel on the same stream (h->face_serial, chosen by the tuner)
+    cudaStream_t fs = (h->side && !h->face_serial) ? h->side : s;
     cudaError_t e = cudaSuccess;
     if (fs != s) {
         e = cudaEventRecord(h->ev_fork, s);

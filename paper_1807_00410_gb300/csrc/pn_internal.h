@@ -55,6 +55,7 @@ struct pn_handle {
     int periodic = 0;    // PN_BC_PERIODIC_TEST: every axis wraps, R slots per axis for every class
     int tile_ctas_per_sm = 4;  // z-chunking target of the tiled FP32 operator (pn_tune_apply)
     int tile_kernel = PN_APPLY_KERNEL_TMA;  // main kernel of the tiled operator (pn_set_apply_kernel)
+    int face_serial = 0;  // face-column kernel after the main kernel on its stream (1) or concurrent (0)
     void* tma_cache = nullptr;  // tensor maps of recent input vectors (pn_apply_tma.cu)
     // the face-column kernel of the tiled operator runs on a side stream,
     // concurrently with the tiled kernel (fork / join events)

@@ -50,7 +50,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
-           "pn_get_apply_kernel", "pn_set_l2_residency"]
+           "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -144,6 +144,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_set_apply_kernel": (i, [vp, i]),
         "pn_get_apply_kernel": (i, [vp, ctypes.POINTER(i)]),
         "pn_set_l2_residency": (i, [vp, i]),
+        "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
         "pn_batch_set_mode": (i, [vp, i, ctypes.c_longlong]),
@@ -479,7 +480,14 @@ class System:
         and z-chunking."""
         c, ms = ctypes.c_int(), ctypes.c_double()
         self._check(self._lib.pn_tune_apply(self._h, _stream_ptr(stream), ctypes.byref(c), ctypes.byref(ms)))
-        return {"ctas_per_sm": c.value, "ms": ms.value, "kernel": self.apply_kernel}
+        return {"ctas_per_sm": c.value, "ms": ms.value, "kernel": self.apply_kernel,
+                "face_serial": self.apply_plan["face_serial"]}
+
+    @property
+    def apply_plan(self) -> dict:
+        c, k, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.pn_get_apply_plan(self._h, ctypes.byref(c), ctypes.byref(k), ctypes.byref(f)))
+        return {"ctas_per_sm": c.value, "kernel": {0: "register", 1: "tma"}[k.value], "face_serial": bool(f.value)}
 
     def set_apply_tiling(self, ctas_per_sm: int):
         self._check(self._lib.pn_set_apply_tiling(self._h, int(ctas_per_sm)))
