@@ -495,6 +495,17 @@ int pn_get_apply_kernel(const pn_handle* h, int* kernel);
  */
 int pn_set_l2_residency(pn_handle* h, int on);
 
+/*
+ * Vector kernels of the FP16-basis GMRES: bit 0 of `mask` stages the fused
+ * CGS1 step's streams (w and the basis vectors), bit 1 the multi-axpy's, in
+ * shared memory by bulk copies (TMA, 1024-element chunks, every G-th chunk
+ * to each of G blocks, three chunks in flight); a clear bit loads them
+ * directly.
+ * Default 3.  Both forms compute the same products; the multi-dot's sums are
+ * formed in another order, so results agree to rounding.
+ */
+int pn_set_stream_kernels(pn_handle* h, int mask);
+
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */
 #define PN_PROF_RESIDUAL 1   /* residual operator launches */

@@ -570,6 +570,13 @@ int pn_get_apply_plan(const pn_handle* h, int* ctas_per_sm, int* kernel, int* fa
     return PN_OK;
 }
 
+int pn_set_stream_kernels(pn_handle* h, int tma) {
+    if (!h) return PN_ERR_ARG;
+    if (tma < 0 || tma > 3) return pn_fail(h, PN_ERR_ARG, "pn_set_stream_kernels: mask in [0, 3]");
+    h->stream_tma = tma;
+    return PN_OK;
+}
+
 int pn_set_l2_residency(pn_handle* h, int on) {
     if (!h) return PN_ERR_ARG;
     h->l2_resident = on ? 1 : 0;

@@ -34,6 +34,7 @@
 #include <cstring>
 #include <vector>
 
+#include "pn_mbar.cuh"
 #include "pn_tiled.cuh"
 
 namespace pn {
@@ -94,50 +95,16 @@ struct Maps {
     CUtensorMap tm[8];  // one per parity class (unused where the class is empty)
 };
 
-// ---- PTX wrappers -------------------------------------------------------------
+// ---- PTX wrappers (mbarriers: pn_mbar.cuh) ----------------------------------
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using mbar::smem_u32;
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) { mbar::init(bar, count); }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    mbar::arrive_expect_tx(bar, bytes);
 }
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of `bar` with this parity to complete, for at most about
-// 2 s; a wait that runs out sets *err and `failed` (later waits return at once).
 __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err, bool& failed) {
-    if (mbar_try_wait(bar, parity) || failed) return;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > 2000000000ull) {
-            failed = true;
-            if (err) atomicExch(err, 1u);
-            return;
-        }
-    }
+    mbar::wait(bar, parity, err, failed);
 }
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -353,8 +320,7 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
     const int zb = min(za + a.zc, a.R + 1);
     if (tid == 0) {
         for (int i = 0; i < 2 * DEPTH; ++i) mbar_init(bar_s + uint32_t(i) * 8u, 1u);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar::fence_init();
     }
     __syncthreads();
     double racc = 0.0;

@@ -67,6 +67,7 @@ struct pn_handle {
     cudaStream_t solve_s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int l2_resident = 1;
+    int stream_tma = 3;  // FP16-basis GMRES: bulk-copy (TMA) staged multi-dot (bit 0) and multi-axpy (bit 1)
     int64_t nz_box = 0;  // z-slices of a plane box: R + 1 (3D) or 1 (2D)
     double h = 0.0;
     double g = 0.0;  // Henyey-Greenstein mean cosine

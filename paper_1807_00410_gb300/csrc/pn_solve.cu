@@ -17,6 +17,7 @@
 #include <string>
 
 #include "pn_internal.h"
+#include "pn_mbar.cuh"
 
 namespace {
 
@@ -660,34 +661,15 @@ __device__ __forceinline__ uint4 f_to_h8(const float (&f)[8]) {
 // The fused CGS1 step of the FP16-basis path: projections (V16_i . w) / sigma
 // for i < nv, |w|^2, the deterministic last-block reduction and the Givens
 // update (as k_mdot_givens_f32).  n8 = n / 8; w is FP32.
-__global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* V16, int64_t vstride8, int nv,
-                                                       const float4* w, float inv_sigma, double* partials,
-                                                       unsigned int* ticket, double* H, int ldh, double* add,
-                                                       double* cs, double* sn, double* g, int j, double* S) {
+// The end of a fused CGS1 step over a 256-thread block: block sums of the
+// per-thread FP32 partial products (warp sums in FP32, across warps in FP64)
+// into partials[v * gridDim.x + block]; the last block to finish (ticket)
+// adds them in block order (deterministic), writes the projections and the
+// Hessenberg column and runs the Givens update.
+__device__ __forceinline__ void mdot16_finish(const float (&part)[PN_MAX_MDOT + 1], int nv, float inv_sigma,
+                                              double* partials, unsigned int* ticket, double* H, int ldh,
+                                              double* add, double* cs, double* sn, double* g, int j, double* S) {
     constexpr int NV = PN_MAX_MDOT;
-    float part[NV + 1];
-#pragma unroll
-    for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += stride) {
-        const float4 wa = w[2 * i], wb = w[2 * i + 1];
-        const float wf[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            if (v < nv) {
-                float q[8];
-                h8_to_f(V16[v * vstride8 + i], q);
-                float t = part[v];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) t = fmaf(q[k], wf[k], t);
-                part[v] = t;
-            }
-        }
-        float t = part[NV];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) t = fmaf(wf[k], wf[k], t);
-        part[NV] = t;
-    }
     __shared__ double red[NV + 1][8];
     __shared__ double tot[NV + 1];
     __shared__ int last;
@@ -732,6 +714,125 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
         givens_core(H, ldh, add, cs, sn, g, j, S, 3, tot[NV]);
         *ticket = 0u;
     }
+}
+
+__global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* V16, int64_t vstride8, int nv,
+                                                       const float4* w, float inv_sigma, double* partials,
+                                                       unsigned int* ticket, double* H, int ldh, double* add,
+                                                       double* cs, double* sn, double* g, int j, double* S) {
+    constexpr int NV = PN_MAX_MDOT;
+    float part[NV + 1];
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += stride) {
+        const float4 wa = w[2 * i], wb = w[2 * i + 1];
+        const float wf[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nv) {
+                float q[8];
+                h8_to_f(V16[v * vstride8 + i], q);
+                float t = part[v];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t = fmaf(q[k], wf[k], t);
+                part[v] = t;
+            }
+        }
+        float t = part[NV];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t = fmaf(wf[k], wf[k], t);
+        part[NV] = t;
+    }
+    mdot16_finish(part, nv, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S);
+}
+
+// The same fused CGS1 step with the streams staged by bulk copies (TMA): each
+// block walks every G-th MD_CH-element chunk (G blocks); one thread copies
+// each chunk's w (FP32) and nv basis slices (FP16) into one of MD_ST shared
+// slots, MD_ST - 1 chunks ahead of the arithmetic (mbarrier per slot, bounded
+// waits that set *err).  n is a multiple of 32, so every chunk's byte counts
+// are multiples of 16 and every address 16-byte aligned.
+constexpr int MD_CH = 1024;  // elements per chunk (4 per thread)
+constexpr int MD_ST = 3;     // shared slots
+constexpr size_t md_smem_bytes() {
+    return size_t(MD_ST) * MD_CH * 4 + size_t(MD_ST) * PN_MAX_MDOT * MD_CH * 2 + MD_ST * 8 + 128;
+}
+
+__global__ void __launch_bounds__(256, 2) k_mdot16_tma(int64_t n, const __half* V16, int64_t vstride, int nv,
+                                                      const float* w, float inv_sigma, double* partials,
+                                                      unsigned int* ticket, double* H, int ldh, double* add,
+                                                      double* cs, double* sn, double* g, int j, double* S,
+                                                      unsigned int* err) {
+    constexpr int NV = PN_MAX_MDOT;
+    extern __shared__ __align__(128) unsigned char md_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(md_raw) + 127) &
+                                                           ~uintptr_t(127));
+    float* sw = reinterpret_cast<float*>(base);                                  // [MD_ST][MD_CH]
+    __half* sv = reinterpret_cast<__half*>(base + size_t(MD_ST) * MD_CH * 4);    // [MD_ST][NV][MD_CH]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + size_t(MD_ST) * MD_CH * 4 + size_t(MD_ST) * NV * MD_CH * 2);
+    const uint32_t bar_s = pn::mbar::smem_u32(bars);
+    const int tid = threadIdx.x;
+    // block b takes chunks b, b + G, b + 2G, ...: at any moment the blocks work
+    // on neighbouring chunks, so each stream is read from one region of DRAM
+    const int64_t nch = (n + MD_CH - 1) / MD_CH;
+    const int64_t G = gridDim.x;
+    const int64_t nk = nch > int64_t(blockIdx.x) ? (nch - blockIdx.x + G - 1) / G : 0;  // chunks of this block
+    if (tid == 0) {
+        for (int st = 0; st < MD_ST; ++st) pn::mbar::init(bar_s + 8u * st, 1u);
+        pn::mbar::fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t c, int st) {
+        const int64_t e0 = c * MD_CH;
+        const int64_t rem = n - e0;
+        const uint32_t cnt = uint32_t(rem < MD_CH ? rem : MD_CH);
+        const uint32_t bar = bar_s + 8u * st;
+        pn::mbar::arrive_expect_tx(bar, cnt * 4u + uint32_t(nv) * cnt * 2u);
+        pn::mbar::bulk_g2s(pn::mbar::smem_u32(sw + st * MD_CH), w + e0, cnt * 4u, bar);
+        for (int v = 0; v < nv; ++v)
+            pn::mbar::bulk_g2s(pn::mbar::smem_u32(sv + (size_t(st) * NV + v) * MD_CH), V16 + v * vstride + e0, cnt * 2u,
+                           bar);
+    };
+    if (tid == 0)
+        for (int k = 0; k < MD_ST && k < nk; ++k) issue(blockIdx.x + k * G, k);
+    float part[NV + 1];
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
+    bool failed = false;
+    for (int64_t kk = 0; kk < nk; ++kk) {
+        const int64_t c = blockIdx.x + kk * G;
+        const int k = int(kk);
+        const int st = k % MD_ST;
+        pn::mbar::wait(bar_s + 8u * st, uint32_t(k / MD_ST) & 1u, err, failed);
+        const int64_t rem = n - c * MD_CH;
+        const int64_t cnt = rem < MD_CH ? rem : MD_CH;
+        if (4 * tid < cnt) {
+            const float4 wv = reinterpret_cast<const float4*>(sw + st * MD_CH)[tid];
+            const float wf[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if (v < nv) {
+                    const uint2 hv = reinterpret_cast<const uint2*>(sv + (size_t(st) * NV + v) * MD_CH)[tid];
+                    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
+                    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
+                    float t = part[v];
+                    t = fmaf(a.x, wf[0], t);
+                    t = fmaf(a.y, wf[1], t);
+                    t = fmaf(b.x, wf[2], t);
+                    t = fmaf(b.y, wf[3], t);
+                    part[v] = t;
+                }
+            }
+            float t = part[NV];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t = fmaf(wf[q], wf[q], t);
+            part[NV] = t;
+        }
+        __syncthreads();  // slot st is free again
+        if (tid == 0 && kk + MD_ST < nk) issue(c + MD_ST * G, st);
+    }
+    mdot16_finish(part, nv, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S);
 }
 
 // w' = (w - sum_{i < nv} add[i] V16_i / sigma) * S[S_SCALE];
@@ -793,6 +894,89 @@ __global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* __res
             vcur[2 * ii] = make_float4(acc[g][0], acc[g][1], acc[g][2], acc[g][3]);
             vcur[2 * ii + 1] = make_float4(acc[g][4], acc[g][5], acc[g][6], acc[g][7]);
         }
+    }
+}
+
+// The multi-axpy of k_maxpy16 with its streams (w and the nv basis slices)
+// staged like k_mdot16_tma: bulk copies of MD_CH-element chunks (every G-th
+// chunk per block) into MD_ST shared slots; each thread
+// combines 4 elements per chunk and writes V16_out and vcur directly.
+__global__ void __launch_bounds__(256, 2) k_maxpy16_tma(int64_t n, const float* w, const __half* V16,
+                                                       int64_t vstride, int nv, const double* add, float inv_sigma,
+                                                       float sigma, const double* S, __half* __restrict__ V16_out,
+                                                       float* __restrict__ vcur, unsigned int* err) {
+    constexpr int NV = PN_MAX_MDOT;
+    extern __shared__ __align__(128) unsigned char mx_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(mx_raw) + 127) &
+                                                           ~uintptr_t(127));
+    float* sw = reinterpret_cast<float*>(base);                                  // [MD_ST][MD_CH]
+    __half* sv = reinterpret_cast<__half*>(base + size_t(MD_ST) * MD_CH * 4);    // [MD_ST][NV][MD_CH]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + size_t(MD_ST) * MD_CH * 4 + size_t(MD_ST) * NV * MD_CH * 2);
+    const uint32_t bar_s = pn::mbar::smem_u32(bars);
+    const int tid = threadIdx.x;
+    float cj[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
+    const float sc = float(S[S_SCALE]);
+    // block b takes chunks b, b + G, b + 2G, ...: at any moment the blocks work
+    // on neighbouring chunks, so each stream is read from one region of DRAM
+    const int64_t nch = (n + MD_CH - 1) / MD_CH;
+    const int64_t G = gridDim.x;
+    const int64_t nk = nch > int64_t(blockIdx.x) ? (nch - blockIdx.x + G - 1) / G : 0;  // chunks of this block
+    if (tid == 0) {
+        for (int st = 0; st < MD_ST; ++st) pn::mbar::init(bar_s + 8u * st, 1u);
+        pn::mbar::fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t c, int st) {
+        const int64_t e0 = c * MD_CH;
+        const int64_t rem = n - e0;
+        const uint32_t cnt = uint32_t(rem < MD_CH ? rem : MD_CH);
+        const uint32_t bar = bar_s + 8u * st;
+        pn::mbar::arrive_expect_tx(bar, cnt * 4u + uint32_t(nv) * cnt * 2u);
+        pn::mbar::bulk_g2s(pn::mbar::smem_u32(sw + st * MD_CH), w + e0, cnt * 4u, bar);
+        for (int v = 0; v < nv; ++v)
+            pn::mbar::bulk_g2s(pn::mbar::smem_u32(sv + (size_t(st) * NV + v) * MD_CH), V16 + v * vstride + e0,
+                               cnt * 2u, bar);
+    };
+    if (tid == 0)
+        for (int k = 0; k < MD_ST && k < nk; ++k) issue(blockIdx.x + k * G, k);
+    bool failed = false;
+    for (int64_t kk = 0; kk < nk; ++kk) {
+        const int64_t c = blockIdx.x + kk * G;
+        const int k = int(kk);
+        const int st = k % MD_ST;
+        pn::mbar::wait(bar_s + 8u * st, uint32_t(k / MD_ST) & 1u, err, failed);
+        const int64_t rem = n - c * MD_CH;
+        const int64_t cnt = rem < MD_CH ? rem : MD_CH;
+        if (4 * tid < cnt) {
+            const float4 wv = reinterpret_cast<const float4*>(sw + st * MD_CH)[tid];
+            float acc[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if (v < nv) {
+                    const uint2 hv = reinterpret_cast<const uint2*>(sv + (size_t(st) * NV + v) * MD_CH)[tid];
+                    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
+                    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
+                    acc[0] = fmaf(cj[v], a.x, acc[0]);
+                    acc[1] = fmaf(cj[v], a.y, acc[1]);
+                    acc[2] = fmaf(cj[v], b.x, acc[2]);
+                    acc[3] = fmaf(cj[v], b.y, acc[3]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] *= sc;
+            const int64_t e = c * MD_CH + 4 * tid;
+            reinterpret_cast<float4*>(vcur + e)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            __half2 h01 = __floats2half2_rn(acc[0] * sigma, acc[1] * sigma);
+            __half2 h23 = __floats2half2_rn(acc[2] * sigma, acc[3] * sigma);
+            uint2 o;
+            o.x = *reinterpret_cast<uint32_t*>(&h01);
+            o.y = *reinterpret_cast<uint32_t*>(&h23);
+            reinterpret_cast<uint2*>(V16_out + e)[0] = o;
+        }
+        __syncthreads();  // slot st is free again
+        if (tid == 0 && kk + MD_ST < nk) issue(c + MD_ST * G, st);
     }
 }
 
@@ -1044,15 +1228,41 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
                  pn::op_launch_count(h, PN_F32));
             c.pe(PN_PROF_APPLY, ob);
             c.pb();
-            k_mdot16_givens<<<nb_mdot(), 256, 0, c.s>>>(n8, (const uint4*)V16, vs8, j + 1, (const float4*)w,
-                                                        inv_sigma, h->d_partials,
-                                                        reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add,
-                                                        cs, sn, g, j, S);
+            if (h->stream_tma & 1) {
+                static bool md_configured = false;
+                if (!md_configured) {
+                    c.ok(cudaFuncSetAttribute(k_mdot16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(md_smem_bytes())),
+                         "gmres16: mdot smem");
+                    md_configured = true;
+                }
+                k_mdot16_tma<<<2 * pn_sm_count(), 256, md_smem_bytes(), c.s>>>(
+                    n, V16, n, j + 1, w, inv_sigma, h->d_partials, reinterpret_cast<unsigned int*>(S + S_TICKET), H,
+                    ldh, add, cs, sn, g, j, S, reinterpret_cast<unsigned int*>(S + PN_S_FAULT));
+            } else {
+                k_mdot16_givens<<<nb_mdot(), 256, 0, c.s>>>(n8, (const uint4*)V16, vs8, j + 1, (const float4*)w,
+                                                            inv_sigma, h->d_partials,
+                                                            reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh,
+                                                            add, cs, sn, g, j, S);
+            }
             c.launched("gmres16: mdot");
             c.pe(PN_PROF_MDOT, double(h->n_active) * (2.0 * (j + 1) + 4.0));
             c.pb();
-            k_maxpy16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, (const uint4*)V16, vs8, j + 1, add, inv_sigma, sigma,
-                                           S, (uint4*)V16 + int64_t(j + 1) * vs8, (float4*)vcur);
+            if (h->stream_tma & 2) {
+                static bool mx_configured = false;
+                if (!mx_configured) {
+                    c.ok(cudaFuncSetAttribute(k_maxpy16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(md_smem_bytes())),
+                         "gmres16: maxpy smem");
+                    mx_configured = true;
+                }
+                k_maxpy16_tma<<<2 * pn_sm_count(), 256, md_smem_bytes(), c.s>>>(
+                    n, w, V16, n, j + 1, add, inv_sigma, sigma, S, V16 + size_t(j + 1) * n, vcur,
+                    reinterpret_cast<unsigned int*>(S + PN_S_FAULT));
+            } else {
+                k_maxpy16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, (const uint4*)V16, vs8, j + 1, add, inv_sigma,
+                                               sigma, S, (uint4*)V16 + int64_t(j + 1) * vs8, (float4*)vcur);
+            }
             c.launched("gmres16: maxpy");
             c.pe(PN_PROF_MAXPY, double(h->n_active) * (4.0 + 2.0 * (j + 1) + 2.0 + 4.0));
             ++total;

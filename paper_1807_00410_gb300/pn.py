@@ -50,7 +50,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
-           "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan"]
+           "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -144,6 +144,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_set_apply_kernel": (i, [vp, i]),
         "pn_get_apply_kernel": (i, [vp, ctypes.POINTER(i)]),
         "pn_set_l2_residency": (i, [vp, i]),
+        "pn_set_stream_kernels": (i, [vp, i]),
         "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
@@ -497,6 +498,10 @@ class System:
     def set_apply_kernel(self, kernel: str):
         """Main kernel of the tiled FP32 operator: "tma" or "register"."""
         self._check(self._lib.pn_set_apply_kernel(self._h, self.APPLY_KERNELS[kernel]))
+
+    def set_stream_kernels(self, mask: int):
+        """FP16-basis GMRES: bit 0 bulk-copy (TMA) staged multi-dot, bit 1 multi-axpy."""
+        self._check(self._lib.pn_set_stream_kernels(self._h, int(mask)))
 
     def set_l2_residency(self, on: bool):
         """Keep the FP16-basis GMRES's two FP32 step vectors resident in L2."""

@@ -393,6 +393,32 @@ def test_solve_orders_after_the_callers_stream_and_l2_residency_changes_no_bit()
     gpu.close()
 
 
+def test_staged_and_direct_vector_kernels_agree():
+    """The FP16-basis GMRES's multi-dot and multi-axpy staged by bulk copies
+    (mask 3) and with direct loads (mask 0): both solutions meet the oracle
+    residual and agree to the accuracy the residual allows; masks outside
+    [0, 3] are refused."""
+    from paper_1807_00410_gb300 import PnError, System
+    N, R = 3, 24
+    p = pn_inputs.fbm_point(N, R, 8, 0.5, 40.0, 0.95, 0.3)
+    S = opn.assemble(N, R, opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00))
+    gpu = System(N, R, p.sigma_t, p.albedo, p.g, p.Q00)
+    opts = dict(solver="ir", tol=1e-6, restart=12, ortho="cgs1", basis="f16", augment=4)
+    sols = []
+    for mask in (3, 0, 1, 2):
+        gpu.set_stream_kernels(mask)
+        u = gpu.zeros(torch.float64)
+        st = gpu.solve(u, **opts)
+        uo = S.layout.join(gpu.to_planes(u))
+        assert st["rel_residual"] <= 1e-6 and opn.relative_residual(S.A, S.b, uo) <= 1.0001e-6
+        sols.append(S.layout.split(uo)[0])
+    for a in sols[1:]:
+        assert np.linalg.norm(a - sols[0]) / np.linalg.norm(sols[0]) <= 2e-5
+    with pytest.raises(PnError):
+        gpu.set_stream_kernels(4)
+    gpu.close()
+
+
 def test_lgmres_option_limits():
     from paper_1807_00410_gb300 import PnError, System
     p = pn_inputs.fbm_point(3, 8, 2, 0.5, 40.0, 0.95, 0.3)
