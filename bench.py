@@ -40,12 +40,11 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic of the dominant kernel from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic
 # bytes of the same launches; profiles/k_maxpy16_p5_64_ir_solve.md,
-# profiles/k_mdot16_givens_p5_64_ir_solve.md), keyed by
-# kernel class, workload and basis type.  Launches differ in the number of
-# basis vectors, so the mean ratio is applied to this run's average
-# algorithmic bytes per launch.  An entry is removed when its kernel changes
-# (traffic is then reported as null).
-NCU_TRAFFIC = {("maxpy", "p5_64", "f16"): 0.911, ("mdot", "p5_64", "f16"): 1.077}
+# profiles/k_mdot16_givens_p5_64_ir_solve.md), keyed by kernel and workload.
+# Launches differ in the number of basis vectors, so the mean ratio is
+# applied to this run's average algorithmic bytes per launch.  An entry is
+# removed when its kernel changes (traffic is then reported as null).
+NCU_TRAFFIC = {("k_maxpy16", "p5_64"): 0.911, ("k_mdot16_givens", "p5_64"): 1.077}
 
 
 def parse():
@@ -430,12 +429,14 @@ def run_ours(args):
     d = kinds[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
     f16 = args.basis == "f16"
-    kernel_names = {"apply": "k_apply_tiled<5,4,OP_APPLY> + k_face_x", "residual": "k_apply_tiled<*,OP_RESIDUAL>",
-                    "mdot": "k_mdot16_givens (fused CGS1 step, FP16 basis)" if f16 else
-                    "k_mdot_givens_f32 (fused CGS1 step)",
-                    "maxpy": "k_maxpy16 (FP16 basis) + k_update16" if f16 else "k_maxpy_f32<16>",
-                    "dot": "k_dot_f32", "vector": "vector updates"}
-    ratio = NCU_TRAFFIC.get((dom, "p5_64", args.basis))
+    op = "k_apply_tma" if tiling["kernel"] == "tma" else "k_apply_tiled"
+    md = ("k_mdot16_tma" if args.stream_tma & 1 else "k_mdot16_givens") if f16 else "k_mdot_givens_f32"
+    mx = ("k_maxpy16_tma" if args.stream_tma & 2 else "k_maxpy16") if f16 else "k_maxpy_f32"
+    kernels = {"apply": op, "residual": op, "mdot": md, "maxpy": mx, "dot": "k_dot_f32", "vector": "vector updates"}
+    kernel_names = {"apply": f"{op}<5, OP_APPLY> + k_face_x", "residual": f"{op}<5, OP_RESIDUAL> + k_face_x",
+                    "mdot": f"{md} (fused CGS1 step{', FP16 basis' if f16 else ''})",
+                    "maxpy": f"{mx} (multi-axpy) + update", "dot": "k_dot_f32", "vector": "vector updates"}
+    ratio = NCU_TRAFFIC.get((kernels.get(dom, dom), "p5_64"))
     traffic = ratio * d["bytes"] / d["launches"] if ratio else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "kernel": kernel_names.get(dom, dom),

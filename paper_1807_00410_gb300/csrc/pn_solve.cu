@@ -753,13 +753,13 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
 // slots, MD_ST - 1 chunks ahead of the arithmetic (mbarrier per slot, bounded
 // waits that set *err).  n is a multiple of 32, so every chunk's byte counts
 // are multiples of 16 and every address 16-byte aligned.
-constexpr int MD_CH = 1024;  // elements per chunk (4 per thread)
-constexpr int MD_ST = 3;     // shared slots
+template <int MD_CH, int MD_ST>
 constexpr size_t md_smem_bytes() {
     return size_t(MD_ST) * MD_CH * 4 + size_t(MD_ST) * PN_MAX_MDOT * MD_CH * 2 + MD_ST * 8 + 128;
 }
 
-__global__ void __launch_bounds__(256, 2) k_mdot16_tma(int64_t n, const __half* V16, int64_t vstride, int nv,
+template <int MD_CH, int MD_ST, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_mdot16_tma(int64_t n, const __half* V16, int64_t vstride, int nv,
                                                       const float* w, float inv_sigma, double* partials,
                                                       unsigned int* ticket, double* H, int ldh, double* add,
                                                       double* cs, double* sn, double* g, int j, double* S,
@@ -807,13 +807,13 @@ __global__ void __launch_bounds__(256, 2) k_mdot16_tma(int64_t n, const __half* 
         pn::mbar::wait(bar_s + 8u * st, uint32_t(k / MD_ST) & 1u, err, failed);
         const int64_t rem = n - c * MD_CH;
         const int64_t cnt = rem < MD_CH ? rem : MD_CH;
-        if (4 * tid < cnt) {
-            const float4 wv = reinterpret_cast<const float4*>(sw + st * MD_CH)[tid];
+        for (int gq = tid; 4 * gq < cnt; gq += 256) {
+            const float4 wv = reinterpret_cast<const float4*>(sw + st * MD_CH)[gq];
             const float wf[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if (v < nv) {
-                    const uint2 hv = reinterpret_cast<const uint2*>(sv + (size_t(st) * NV + v) * MD_CH)[tid];
+                    const uint2 hv = reinterpret_cast<const uint2*>(sv + (size_t(st) * NV + v) * MD_CH)[gq];
                     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
                     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
                     float t = part[v];
@@ -901,7 +901,8 @@ __global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* __res
 // staged like k_mdot16_tma: bulk copies of MD_CH-element chunks (every G-th
 // chunk per block) into MD_ST shared slots; each thread
 // combines 4 elements per chunk and writes V16_out and vcur directly.
-__global__ void __launch_bounds__(256, 2) k_maxpy16_tma(int64_t n, const float* w, const __half* V16,
+template <int MD_CH, int MD_ST, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_maxpy16_tma(int64_t n, const float* w, const __half* V16,
                                                        int64_t vstride, int nv, const double* add, float inv_sigma,
                                                        float sigma, const double* S, __half* __restrict__ V16_out,
                                                        float* __restrict__ vcur, unsigned int* err) {
@@ -949,13 +950,13 @@ __global__ void __launch_bounds__(256, 2) k_maxpy16_tma(int64_t n, const float* 
         pn::mbar::wait(bar_s + 8u * st, uint32_t(k / MD_ST) & 1u, err, failed);
         const int64_t rem = n - c * MD_CH;
         const int64_t cnt = rem < MD_CH ? rem : MD_CH;
-        if (4 * tid < cnt) {
-            const float4 wv = reinterpret_cast<const float4*>(sw + st * MD_CH)[tid];
+        for (int gq = tid; 4 * gq < cnt; gq += 256) {
+            const float4 wv = reinterpret_cast<const float4*>(sw + st * MD_CH)[gq];
             float acc[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if (v < nv) {
-                    const uint2 hv = reinterpret_cast<const uint2*>(sv + (size_t(st) * NV + v) * MD_CH)[tid];
+                    const uint2 hv = reinterpret_cast<const uint2*>(sv + (size_t(st) * NV + v) * MD_CH)[gq];
                     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
                     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
                     acc[0] = fmaf(cj[v], a.x, acc[0]);
@@ -966,7 +967,7 @@ __global__ void __launch_bounds__(256, 2) k_maxpy16_tma(int64_t n, const float* 
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[q] *= sc;
-            const int64_t e = c * MD_CH + 4 * tid;
+            const int64_t e = c * MD_CH + 4 * gq;
             reinterpret_cast<float4*>(vcur + e)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             __half2 h01 = __floats2half2_rn(acc[0] * sigma, acc[1] * sigma);
             __half2 h23 = __floats2half2_rn(acc[2] * sigma, acc[3] * sigma);
@@ -978,6 +979,53 @@ __global__ void __launch_bounds__(256, 2) k_maxpy16_tma(int64_t n, const float* 
         __syncthreads();  // slot st is free again
         if (tid == 0 && kk + MD_ST < nk) issue(c + MD_ST * G, st);
     }
+}
+
+// Launchers of the staged vector kernels: chunk size, slots and blocks per SM.
+template <int CH, int ST, int MINB>
+cudaError_t launch_md(int64_t n, const __half* V16, int nv, const float* w, float inv_sigma, double* partials,
+                      unsigned int* ticket, double* H, int ldh, double* add, double* cs, double* sn, double* g, int j,
+                      double* S, unsigned int* err, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_mdot16_tma<CH, ST, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(md_smem_bytes<CH, ST>()));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_mdot16_tma<CH, ST, MINB><<<MINB * pn_sm_count(), 256, md_smem_bytes<CH, ST>(), s>>>(
+        n, V16, n, nv, w, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S, err);
+    return cudaGetLastError();
+}
+
+template <int CH, int ST, int MINB>
+cudaError_t launch_mx(int64_t n, const float* w, const __half* V16, int nv, const double* add, float inv_sigma,
+                      float sigma, const double* S, __half* V16_out, float* vcur, unsigned int* err, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_maxpy16_tma<CH, ST, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(md_smem_bytes<CH, ST>()));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_maxpy16_tma<CH, ST, MINB><<<MINB * pn_sm_count(), 256, md_smem_bytes<CH, ST>(), s>>>(
+        n, w, V16, n, nv, add, inv_sigma, sigma, S, V16_out, vcur, err);
+    return cudaGetLastError();
+}
+
+// 1024-element chunks, two slots, three blocks per SM: the best of
+// {512, 4, 3}, {1024, 3, 2}, {1024, 2, 3}, {2048, 3, 1} (chunk elements,
+// slots, blocks per SM) on the P5 64^3 solve.
+cudaError_t launch_mdot16_tma(int64_t n, const __half* V16, int nv, const float* w, float inv_sigma,
+                              double* partials, unsigned int* ticket, double* H, int ldh, double* add, double* cs,
+                              double* sn, double* g, int j, double* S, unsigned int* err, cudaStream_t s) {
+    return launch_md<1024, 2, 3>(n, V16, nv, w, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S, err, s);
+}
+
+cudaError_t launch_maxpy16_tma(int64_t n, const float* w, const __half* V16, int nv, const double* add,
+                               float inv_sigma, float sigma, const double* S, __half* V16_out, float* vcur,
+                               unsigned int* err, cudaStream_t s) {
+    return launch_mx<1024, 2, 3>(n, w, V16, nv, add, inv_sigma, sigma, S, V16_out, vcur, err, s);
 }
 
 // First basis vector: r / beta (beta^2 = S[S_BETA2]) into V16_0 (scaled) and vcur.
@@ -1229,16 +1277,10 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
             c.pe(PN_PROF_APPLY, ob);
             c.pb();
             if (h->stream_tma & 1) {
-                static bool md_configured = false;
-                if (!md_configured) {
-                    c.ok(cudaFuncSetAttribute(k_mdot16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(md_smem_bytes())),
-                         "gmres16: mdot smem");
-                    md_configured = true;
-                }
-                k_mdot16_tma<<<2 * pn_sm_count(), 256, md_smem_bytes(), c.s>>>(
-                    n, V16, n, j + 1, w, inv_sigma, h->d_partials, reinterpret_cast<unsigned int*>(S + S_TICKET), H,
-                    ldh, add, cs, sn, g, j, S, reinterpret_cast<unsigned int*>(S + PN_S_FAULT));
+                c.ok(launch_mdot16_tma(n, V16, j + 1, w, inv_sigma, h->d_partials,
+                                       reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add, cs, sn, g, j, S,
+                                       reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s),
+                     "gmres16: mdot");
             } else {
                 k_mdot16_givens<<<nb_mdot(), 256, 0, c.s>>>(n8, (const uint4*)V16, vs8, j + 1, (const float4*)w,
                                                             inv_sigma, h->d_partials,
@@ -1249,16 +1291,9 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
             c.pe(PN_PROF_MDOT, double(h->n_active) * (2.0 * (j + 1) + 4.0));
             c.pb();
             if (h->stream_tma & 2) {
-                static bool mx_configured = false;
-                if (!mx_configured) {
-                    c.ok(cudaFuncSetAttribute(k_maxpy16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(md_smem_bytes())),
-                         "gmres16: maxpy smem");
-                    mx_configured = true;
-                }
-                k_maxpy16_tma<<<2 * pn_sm_count(), 256, md_smem_bytes(), c.s>>>(
-                    n, w, V16, n, j + 1, add, inv_sigma, sigma, S, V16 + size_t(j + 1) * n, vcur,
-                    reinterpret_cast<unsigned int*>(S + PN_S_FAULT));
+                c.ok(launch_maxpy16_tma(n, w, V16, j + 1, add, inv_sigma, sigma, S, V16 + size_t(j + 1) * n, vcur,
+                                        reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s),
+                     "gmres16: maxpy");
             } else {
                 k_maxpy16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, (const uint4*)V16, vs8, j + 1, add, inv_sigma,
                                                sigma, S, (uint4*)V16 + int64_t(j + 1) * vs8, (float4*)vcur);
