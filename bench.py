@@ -304,9 +304,10 @@ LEARNED_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "pape
 def learned_compare(torch, args, seeds=(90000, 90001)):
     """Learned vs plain: held-out P3 64^3 fBm media (sigma_t in [0.5, 80],
     albedo 0.8..0.99, g 0..0.6, point source) solved to 1e-6 by FP64
-    refinement around plain FP32 GMRES (the bench's basis) and around
-    flexible GMRES with the committed network (training: learned.py --loss
-    hard); CUDA events around each solve, best of two."""
+    refinement around the bench's plain solver (LGMRES(restart, augment) with
+    its basis) and around flexible GMRES(15) with the committed network
+    (training: learned.py --loss hard); CUDA events around each solve, best of
+    two."""
     import numpy as np
 
     from paper_1807_00410_gb300 import Net, System
@@ -329,7 +330,8 @@ def learned_compare(torch, args, seeds=(90000, 90001)):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 if mode == "plain":
-                    s = sysm.solve(u, solver="ir", tol=1e-6, restart=15, ortho="cgs1", basis=args.basis)
+                    s = sysm.solve(u, solver="ir", tol=1e-6, restart=args.restart, ortho="cgs1", basis=args.basis,
+                                   augment=args.augment if args.basis == "f16" else 0)
                 else:
                     s = sysm.solve(u, solver="ir_fgmres", tol=1e-6, restart=15, ortho="cgs1", precond=net)
                 e1.record()
@@ -343,6 +345,8 @@ def learned_compare(torch, args, seeds=(90000, 90001)):
         sysm.close()
     net.close()
     return {"workload": "P3 64^3 fBm sigma_t[0.5,80], held-out seeds, point source, to 1e-6",
+            "plain": f"LGMRES({args.restart}, {args.augment if args.basis == 'f16' else 0}), {args.basis} basis",
+            "learned": "flexible GMRES(15) with the network, FP32 basis",
             "plain_ms_mean": float(np.mean([r["plain"]["ms"] for r in rows])),
             "learned_ms_mean": float(np.mean([r["learned"]["ms"] for r in rows])), "rows": rows}
 

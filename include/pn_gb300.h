@@ -499,8 +499,9 @@ int pn_set_l2_residency(pn_handle* h, int on);
  * Vector kernels of the FP16-basis GMRES: bit 0 of `mask` stages the fused
  * CGS1 step's streams (w and the basis vectors), bit 1 the multi-axpy's, in
  * shared memory by bulk copies (TMA, 1024-element chunks, every G-th chunk
- * to each of G blocks, two slots per block, three blocks per SM); a clear bit
- * loads them directly.
+ * to each of G blocks, two slots per block, three blocks per SM) for steps
+ * with at least five basis vectors (with fewer the direct form is faster); a
+ * clear bit loads them directly.
  * Default 3.  Both forms compute the same products; the multi-dot's sums are
  * formed in another order, so results agree to rounding.
  */

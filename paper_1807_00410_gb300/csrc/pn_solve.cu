@@ -753,6 +753,7 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
 // slots, MD_ST - 1 chunks ahead of the arithmetic (mbarrier per slot, bounded
 // waits that set *err).  n is a multiple of 32, so every chunk's byte counts
 // are multiples of 16 and every address 16-byte aligned.
+constexpr int MD_MIN_NV = 5;  // fewest basis vectors the staged kernels are used for
 template <int MD_CH, int MD_ST>
 constexpr size_t md_smem_bytes() {
     return size_t(MD_ST) * MD_CH * 4 + size_t(MD_ST) * PN_MAX_MDOT * MD_CH * 2 + MD_ST * 8 + 128;
@@ -1276,7 +1277,10 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
                  pn::op_launch_count(h, PN_F32));
             c.pe(PN_PROF_APPLY, ob);
             c.pb();
-            if (h->stream_tma & 1) {
+            // staged from MD_MIN_NV basis vectors on (ncu, P5 64^3, cold: the
+            // direct kernel is faster below, e.g. 24.0 against 33.9 us at one
+            // vector; 90.8 against 77.2 us at sixteen)
+            if ((h->stream_tma & 1) && j + 1 >= MD_MIN_NV) {
                 c.ok(launch_mdot16_tma(n, V16, j + 1, w, inv_sigma, h->d_partials,
                                        reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add, cs, sn, g, j, S,
                                        reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s),
@@ -1290,7 +1294,7 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
             c.launched("gmres16: mdot");
             c.pe(PN_PROF_MDOT, double(h->n_active) * (2.0 * (j + 1) + 4.0));
             c.pb();
-            if (h->stream_tma & 2) {
+            if ((h->stream_tma & 2) && j + 1 >= MD_MIN_NV) {  // (23.3 against 30.5 us at one vector)
                 c.ok(launch_maxpy16_tma(n, w, V16, j + 1, add, inv_sigma, sigma, S, V16 + size_t(j + 1) * n, vcur,
                                         reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s),
                      "gmres16: maxpy");
