@@ -40,11 +40,15 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic of the dominant kernel from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic
 # bytes of the same launches; profiles/k_maxpy16_p5_64_ir_solve.md,
-# profiles/k_mdot16_givens_p5_64_ir_solve.md), keyed by kernel and workload.
+# profiles/k_mdot16_givens_p5_64_ir_solve.md,
+# profiles/k_mdot16_tma_k_maxpy16_tma_p5_64_ir_solve.md), keyed by kernel and
+# workload (the staged kernels run from five basis vectors on, the direct ones
+# below: the ratio of the kernel that carries most of the bytes is used).
 # Launches differ in the number of basis vectors, so the mean ratio is
 # applied to this run's average algorithmic bytes per launch.  An entry is
 # removed when its kernel changes (traffic is then reported as null).
-NCU_TRAFFIC = {("k_maxpy16", "p5_64"): 0.911, ("k_mdot16_givens", "p5_64"): 1.077}
+NCU_TRAFFIC = {("k_maxpy16", "p5_64"): 0.911, ("k_mdot16_givens", "p5_64"): 1.077,
+               ("k_mdot16_tma", "p5_64"): 1.077, ("k_maxpy16_tma", "p5_64"): 0.888}
 
 
 def parse():

@@ -393,7 +393,12 @@ __device__ __forceinline__ void face_out(const Args& a, int y, int z, int i, flo
             rrun = fmaf(out, out, rrun);
         }
     }
-    a.y[off] = out;
+    // x = R is the first of the row's last four slots (R a multiple of 32, the
+    // only case with outputs right of the tiles): the output and three zeros
+    if (a.pitch_x - R == 4)
+        *reinterpret_cast<float4*>(a.y + off) = make_float4(out, 0.0f, 0.0f, 0.0f);
+    else
+        a.y[off] = out;
 }
 
 template <int N, int C, int MODE>
@@ -438,7 +443,24 @@ __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr)
     const int64_t t0 = int64_t(int(blockIdx.x) - fr.b[task]) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(fr.b[task + 1] - fr.b[task]) * blockDim.x;
     float rrun = 0.0f;
-    if (task == 0) {
+    if (task == 0 && w == 4 && x_lo + 4 == a.pitch_x) {
+        // four slots per row, 16-byte aligned: one vector store each; the face
+        // planes' rows are written with their x = R output by tasks 1..4
+        const int64_t nz = int64_t(K) * rows;
+        for (int64_t u = t0; u < nz + int64_t(K) * tail; u += stride) {
+            if (u < nz) {
+                const int64_t row = u % rows;
+                const int p = int(u / rows);
+                if ((a.pcls[p] & 1) && x_lo <= R) continue;
+                const int y = int(row % (R + 1)), z = int(row / (R + 1));
+                *reinterpret_cast<float4*>(a.y + size_t(p) * ps + size_t(uint32_t(z) * py) + uint32_t(y) * px +
+                                           uint32_t(x_lo)) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else {
+                const int64_t v = u - nz;
+                a.y[size_t(v / tail) * ps + box + uint32_t(v % tail)] = 0.0f;
+            }
+        }
+    } else if (task == 0) {
         const int64_t nz = w > 0 ? int64_t(K) * rows * w : 0;
         for (int64_t u = t0; u < nz + int64_t(K) * tail; u += stride) {
             if (u < nz) {
@@ -527,7 +549,8 @@ tiled::FaceRanges face_ranges(const pn_handle* h) {
     for (int p = 0; p < h->K; ++p) ++ncls[h->plane_class[p]];
     tiled::FaceRanges fr{};
     fr.b[0] = 0;
-    fr.b[1] = blocks(int64_t(h->K) * (rows * w + tail), 4 * int64_t(pn_sm_count()));
+    const int64_t zero_items = w == 4 && x_lo + 4 == h->pitch_x ? rows : rows * w;  // vector stores when w = 4
+    fr.b[1] = blocks(int64_t(h->K) * (zero_items + tail), 4 * int64_t(pn_sm_count()));
     for (int k = 1; k <= 4; ++k) {
         const int c = 2 * k - 1;
         const int nb = (x_lo <= h->R && ncls[c] > 0) ? blocks(rows * ncls[c], 4 * int64_t(pn_sm_count())) : 0;
