@@ -711,9 +711,9 @@ def run_batched(args):
 
 def run_large_solve(args):
     """Full-size solve on the P7 256^3 thresholded-fBm cloud (albedo 0.99,
-    g 0.6, sigma_t_min --large-sigma-min, seeded point source): IR with FP32
-    GMRES(15), FP16-stored basis, capped at --large-iters inner iterations;
-    CUDA events around the solve."""
+    g 0.6, sigma_t_min --large-sigma-min, seeded point source): IR with the
+    bench's FP32 solver (LGMRES(--restart, --augment), FP16-stored basis),
+    capped at --large-iters inner iterations; CUDA events around the solve."""
     import torch
 
     import pn_inputs
@@ -723,23 +723,25 @@ def run_large_solve(args):
     p = pn_inputs.cloud_point(7, 256, 0, sigma_t_min=args.large_sigma_min)
     sysm = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=args.large_sigma_min)
     tiling = sysm.tune_apply()
+    sysm.set_l2_residency(not args.no_l2_resident)
+    sysm.set_stream_kernels(args.stream_tma)
     u = sysm.zeros(torch.float64)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    st = sysm.solve(u, solver="ir", tol=1e-6, restart=15, ortho="cgs1", basis="f16", max_iter=args.large_iters,
-                    raise_on_error=False)
+    st = sysm.solve(u, solver="ir", tol=1e-6, restart=args.restart, ortho="cgs1", basis="f16",
+                    augment=args.augment, max_iter=args.large_iters, raise_on_error=False)
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     dof = sysm.layout.n_active
     print(json.dumps({"mode": "large-solve", "workload": f"P7 256^3 thresholded-fBm cloud, sigma_t_min "
-                      f"{args.large_sigma_min}, albedo 0.99, g 0.6, point source; FP32 GMRES(15), FP16 basis, "
-                      "FP64 IR", "dof": dof, "ms": ms, "iterations": st["iterations"],
+                      f"{args.large_sigma_min}, albedo 0.99, g 0.6, point source; FP32 LGMRES({args.restart}, "
+                      f"{args.augment}), FP16 basis, FP64 IR", "dof": dof, "ms": ms, "iterations": st["iterations"],
                       "outer_iterations": st["outer_iterations"], "rel_residual": st["rel_residual"],
                       "status": st["status"], "ms_per_iteration": ms / max(1, st["iterations"]),
                       "gdof_iterations_per_s": dof * st["iterations"] / (ms * 1e-3) / 1e9,
-                      "apply_ctas_per_sm": tiling["ctas_per_sm"]}), flush=True)
+                      "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"]}), flush=True)
     sysm.close()
 
 

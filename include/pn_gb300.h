@@ -488,7 +488,7 @@ int pn_get_apply_kernel(const pn_handle* h, int* kernel);
  * FP32 step vectors (A v and the newest basis vector, each written and read
  * again within every Arnoldi step) are kept in L2 by a persisting
  * access-policy window on the solver's stream, up to the device's persisting
- * capacity; afterwards the window is closed, the persisting lines released and
+ * capacity, when the two fit in L2 (larger ones are left alone); afterwards the window is closed, the persisting lines released and
  * the context's persisting-lines limit restored.  pn_solve runs on a stream of
  * its own, ordered after `stream` on entry and before it on exit.  on = 1
  * (default) or 0.  Results do not depend on it.

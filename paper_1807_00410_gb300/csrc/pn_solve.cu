@@ -1149,8 +1149,9 @@ __global__ void __launch_bounds__(256) k_update16_aug(int64_t n8, float4* __rest
 }
 
 // Keeps [base, base + bytes) resident in L2 for the launches of stream s while
-// it lives: a persisting access-policy window (at most the device's persisting
-// capacity; the hit ratio covers the rest of the window proportionally).  The
+// it lives, if it fits in L2: a persisting access-policy window (at most the
+// device's persisting capacity; the hit ratio covers the rest of the window
+// proportionally).  The
 // stream is the solver's own (the handle's solve stream).  On destruction the
 // window is closed, the persisting lines are released and the context's
 // persisting-lines limit is put back.
@@ -1160,14 +1161,18 @@ struct L2Resident {
     size_t old_limit = 0;
     L2Resident(cudaStream_t st, void* base, size_t bytes, bool enable) : s(st) {
         if (!enable || bytes == 0 || st == nullptr) return;
-        int dev = 0, maxp = 0, maxw = 0;
+        int dev = 0, maxp = 0, maxw = 0, l2 = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess || maxp <= 0 ||
-            maxw <= 0) {
+            cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || maxp <= 0 || maxw <= 0) {
             cudaGetLastError();
             return;
         }
+        // only vectors that fit in L2: a window over a sliver of larger ones
+        // takes L2 from every other access (P7 256^3: 20.8 against 12.0 ms
+        // per iteration)
+        if (bytes > size_t(l2)) return;
         const size_t win = std::min(bytes, size_t(maxw));
         const size_t lim = std::min(win, size_t(maxp));
         if (cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess ||
