@@ -70,3 +70,21 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(pn._SolveOpts) == 64  # 4+4+8+4+4+8+4+4+4+4 = 48, an 8-byte pointer, two ints
     assert pn._SolveOpts.augment.offset == 60
     assert ctypes.sizeof(pn._SolveStats) == 48
+
+
+def header_defines():
+    return {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"#define\s+(PN_[A-Z0-9_]+)\s+(-?\d+)\b", open(HEADER).read())}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's codes for operator kernels, solvers, bases and errors are
+    the header's (a mismatch would select the wrong kernel or solver)."""
+    from paper_1807_00410_gb300 import pn
+    d = header_defines()
+    assert pn.System.APPLY_KERNELS == {"register": d["PN_APPLY_KERNEL_REGISTER"], "tma": d["PN_APPLY_KERNEL_TMA"]}
+    assert pn.SOLVERS["cgls"] == d["PN_SOLVER_CGLS"] and pn.SOLVERS["gmres"] == d["PN_SOLVER_GMRES"]
+    assert pn.SOLVERS["ir"] == d["PN_SOLVER_IR_GMRES"] and pn.SOLVERS["ir_fgmres"] == d["PN_SOLVER_IR_FGMRES"]
+    assert (d["PN_BASIS_F32"], d["PN_BASIS_F16"]) == (0, 1)  # the binding maps "f32"/"f16" to 0/1
+    assert (d["PN_ORTHO_CGS2"], d["PN_ORTHO_CGS1"]) == (0, 1)  # and "cgs2"/"cgs1" to 0/1
+    assert d["PN_ERR_TIMEOUT"] < 0 and d["PN_OK"] == 0
