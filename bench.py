@@ -39,9 +39,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic of the dominant kernel from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic
-# bytes of the same launches; profiles/k_maxpy16_p5_64_ir_solve.md,
-# profiles/k_mdot16_givens_p5_64_ir_solve.md,
-# profiles/k_mdot16_tma_k_maxpy16_tma_p5_64_ir_solve.md), keyed by kernel and
+# bytes of the same launches, in the committed ncu summaries), keyed by kernel and
 # workload (the staged kernels run from five basis vectors on, the direct ones
 # below: the ratio of the kernel that carries most of the bytes is used).
 # Launches differ in the number of basis vectors, so the mean ratio is
@@ -66,6 +64,8 @@ def parse():
     ap.add_argument("--no-apply-scan", action="store_true", help="skip the separate operator throughput scan")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--no-paper-cgls", action="store_true",
+                    help="skip the GPU FP64 CGLS solve (the paper's method) of the same workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the FP32 operator on the P_N cloud medium given by --apply-n / --apply-r")
@@ -187,80 +187,130 @@ def barrier(world):
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle timing (the reference arm and the cpu_baseline object)
+# CPU oracle timing (the reference arm and the cpu_baseline object): the
+# paper's solver -- CG on the normal equations without forming A^T A
+# (section "Results"; oracle.pn.cgls) -- on the oracle's explicitly assembled
+# FP64 CSR matrix (section "Runtime"), its sparse products split into row
+# blocks over all host cores.
 
-def oracle_solve_sample(seed: int, sample_iters: int, m: int):
-    """Time `sample_iters` GMRES(m) iterations of the FP64 oracle (matrix-free
-    operator, numpy) on the full workload.  Returns seconds per iteration and
-    seconds for the initial residual."""
-    import numpy as np
+def host_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
 
+
+class ThreadedCSR:
+    """y = A v and y = A^T v for a SciPy CSR matrix, the rows of A (and of
+    A^T) split into one contiguous block per thread.  SciPy's sparse products
+    release the GIL, so the blocks run on separate cores."""
+
+    def __init__(self, A, threads: int):
+        import numpy as np
+        from concurrent.futures import ThreadPoolExecutor
+        self.n = A.shape[0]
+        self.threads = threads
+        self.bounds = np.linspace(0, self.n, threads + 1).astype(np.int64)
+        AT = A.T.tocsr()
+        self.rows = [A[self.bounds[i]:self.bounds[i + 1]] for i in range(threads)]
+        self.rows_t = [AT[self.bounds[i]:self.bounds[i + 1]] for i in range(threads)]
+        self.pool = ThreadPoolExecutor(threads)
+
+    def _prod(self, blocks, v):
+        import numpy as np
+        out = np.empty(self.n)
+
+        def part(i):
+            out[self.bounds[i]:self.bounds[i + 1]] = blocks[i] @ v
+        list(self.pool.map(part, range(self.threads)))
+        return out
+
+    def matvec(self, v):
+        return self._prod(self.rows, v)
+
+    def rmatvec(self, v):
+        return self._prod(self.rows_t, v)
+
+    # the matrix interface oracle.pn.cgls uses: A @ v and A.T @ v
+    def __matmul__(self, v):
+        return self.matvec(v)
+
+    @property
+    def T(self):
+        outer = self
+
+        class _Transposed:
+            def __matmul__(self, v):
+                return outer.rmatvec(v)
+        return _Transposed()
+
+    def close(self):
+        self.pool.shutdown()
+
+
+def oracle_cgls_setup(seed: int):
+    """The oracle's CSR of the bench workload (untimed setup) and its
+    right-hand side, with a threaded product over all host cores."""
     import pn_inputs
-    from oracle import gmres as ogm
-    from oracle import grid as ogrid
     from oracle import pn as opn
     p = pn_inputs.p5_64_fbm(seed)
-    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00, p.sigma_t_min)
-    lay = ogrid.Layout(p.N, p.R)
-    b = opn.rhs(lay, med)
-    mv = lambda v: opn.apply_matrix_free(lay, med, v)  # noqa: E731
+    S = opn.assemble(p.N, p.R, opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00, p.sigma_t_min))
+    return ThreadedCSR(S.A, host_threads()), S.b
+
+
+def oracle_cgls_sample(op, b, iters: int):
+    """Seconds of the oracle's CGLS set-up (initial residual and A^T r) and
+    seconds per CGLS iteration, from one run of `iters` iterations."""
+    from oracle import pn as opn
     t0 = time.perf_counter()
-    r0 = b - mv(np.zeros_like(b))
+    opn.cgls(op, b, tol=1e-300, max_iter=0)
     t1 = time.perf_counter()
-    _ = r0
-    ogm.gmres(mv, b, tol=1e-30, m=m, max_iter=sample_iters)
+    opn.cgls(op, b, tol=1e-300, max_iter=iters)
     t2 = time.perf_counter()
-    # gmres() computes one residual before and one after the cycle
-    per_iter = max((t2 - t1) - 2 * (t1 - t0), 0.0) / sample_iters
-    return per_iter, t1 - t0
-
-
-def cpu_cores_used() -> int:
-    try:
-        from threadpoolctl import threadpool_info
-        n = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        n = 1
-    # the oracle's operator is numpy element-wise work: one thread
-    return 1 if n >= 1 else 1
+    return t1 - t0, max((t2 - t1) - (t1 - t0), 0.0) / iters
 
 
 def run_reference(args):
     rank, world, _ = dist_init(args)
     if rank != 0:
         return
-    m = REF_RESTART
-    # the oracle's method (restarted GMRES(15)) needs about this many inner
-    # iterations and refinement residuals on this workload (the count of the
-    # plain GMRES(15) solve on GB300, stated in DESIGN.md)
-    iters_est = int(os.environ.get("PN_REF_ITERS", "0")) or REF_ITERS_ESTIMATE
-    times = []
-    sample = 3
+    op, b = oracle_cgls_setup(0)
+    times, walls = [], []
+    t_setup = per_iter = 0.0
     for s in range(args.warmup + args.steps):
-        per_iter, t_res = oracle_solve_sample(0, sample, m)
-        est = per_iter * iters_est + t_res * REF_OUTER_ESTIMATE
+        w0 = time.perf_counter()
+        t_setup, per_iter = oracle_cgls_sample(op, b, REF_SAMPLE_ITERS)
+        w1 = time.perf_counter()
         if s >= args.warmup:
-            times.append(est)
+            times.append(t_setup + per_iter * REF_CGLS_ITERS)
+            walls.append(w1 - w0)
+    op.close()
     sec = statistics.mean(times)
     value = 1.0 / sec
+    sample = (f"{REF_SAMPLE_ITERS} CGLS iterations (the paper's CG on the normal equations) per step on the "
+              f"oracle's FP64 CSR of the full P5 64^3 problem, products split over {op.threads} host threads; "
+              f"solve time extrapolated to the {REF_CGLS_ITERS} iterations the same method (FP64 CGLS) needs on "
+              f"this workload on the GPU")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solve/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "solver": "oracle GMRES(m) FP64, matrix-free numpy operator",
-                   "restart": m},
-        "cpu_baseline": {"value": value, "unit": "solve/s", "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": f"{sample} GMRES({m}) iterations of the FP64 oracle per step on the full "
-                                   f"P5 64^3 problem, extrapolated to {iters_est} iterations + "
-                                   f"{REF_OUTER_ESTIMATE} residuals (the counts of plain GMRES({m}) on the GPU)"},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solver": "oracle CGLS FP64 (oracle.pn.cgls) on the assembled CSR"},
+        "extrapolated": {"seconds_per_iteration": per_iter, "setup_seconds": t_setup, "iterations": REF_CGLS_ITERS,
+                         "seconds_per_solve": sec, "ms_per_step_is": "wall time of the step's sample"},
+        "cpu_baseline": {"value": value, "unit": "solve/s", "cores": op.threads, "kind": "oracle",
+                         "cpu_count": os.cpu_count(), "sample": sample},
         "e2e": {"value": value, "unit": "solve/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-REF_RESTART = 15
-REF_ITERS_ESTIMATE = 845
-REF_OUTER_ESTIMATE = 4
+REF_SAMPLE_ITERS = 10
+CPU_SAMPLE_ITERS = 20
+# iterations FP64 CGLS needs to reach 1e-6 on the P5 64^3 workload (medium
+# seed 0), measured by the bench's own `paper_cgls` run of the library's FP64
+# CGLS on GB300 (the GPU arm reports the count it measured next to this one)
+REF_CGLS_ITERS = 0
 
 
 # ----------------------------------------------------------------------------
@@ -483,18 +533,44 @@ def run_ours(args):
     if rank == 0 and not args.no_apply_scan:
         scan = apply_scan(torch, System, pn_inputs, hbm_peak)
 
+    # the paper's own solver on the GPU: FP64 CG on the normal equations
+    # (CGLS, the library's FP64 operator) on the same medium, to the same target
+    paper = None
+    if rank == 0 and not args.no_paper_cgls:
+        cg_opts = dict(solver="cgls", tol=1e-6, max_iter=200000, check_every=50)
+        u64 = sysm.zeros(torch.float64)
+        sysm.solve(u64, **dict(cg_opts, max_iter=20), raise_on_error=False)  # workspace, untimed
+        u64.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        cst = sysm.solve(u64, **cg_opts, raise_on_error=False)
+        e1.record()
+        e1.synchronize()
+        paper = {"solver": "CGLS (CG on the normal equations, the paper's method), FP64 vectors and operator",
+                 "ms": e0.elapsed_time(e1), "iterations": cst["iterations"], "rel_residual": cst["rel_residual"],
+                 "status": cst["status"], "vs_plain_solve": e0.elapsed_time(e1) / ms_per_step}
+        del u64
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle's restarted GMRES(15), extrapolated to the iterations that
-        # method needs here (the plain GMRES(15) count on the GPU)
-        iters, outers, sample = REF_ITERS_ESTIMATE, REF_OUTER_ESTIMATE, 3
-        per_iter, t_res = oracle_solve_sample(0, sample, REF_RESTART)
-        cpu_sec = per_iter * iters + t_res * outers
-        cpu = {"value": 1.0 / cpu_sec, "unit": "solve/s", "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"{sample} GMRES({REF_RESTART}) iterations of the FP64 oracle (matrix-free numpy "
-                         f"operator) on the full P5 64^3 problem, extrapolated to the {iters} inner "
-                         f"iterations + {outers} residuals plain GMRES({REF_RESTART}) needs on this workload",
-               "seconds_per_solve": cpu_sec}
+        # the oracle's CGLS on its CSR over all host cores: a bounded sample of
+        # iterations on the full problem, extrapolated to the iterations the
+        # same method needed on the GPU in this run
+        iters = paper["iterations"] if paper and paper["status"] == 0 else None
+        op, bvec = oracle_cgls_setup(0)
+        t_setup, per_iter = oracle_cgls_sample(op, bvec, CPU_SAMPLE_ITERS)
+        op.close()
+        cpu = {"unit": "solve/s", "cores": op.threads, "cpu_count": os.cpu_count(), "kind": "oracle",
+               "method": "oracle.pn.cgls: CG on the normal equations (the paper's solver), FP64, assembled CSR, "
+                         f"sparse products split over {op.threads} threads",
+               "seconds_per_iteration": per_iter, "setup_seconds": t_setup}
+        if iters:
+            cpu_sec = t_setup + per_iter * iters
+            cpu.update({"value": 1.0 / cpu_sec, "seconds_per_solve": cpu_sec, "iterations": iters,
+                        "sample": f"{CPU_SAMPLE_ITERS} CGLS iterations on the full P5 64^3 problem, extrapolated "
+                                  f"to the {iters} iterations FP64 CGLS needed on the GPU in this run"})
+        else:
+            cpu.update({"value": None, "sample": "no GPU CGLS iteration count in this run: not extrapolated"})
 
     sysm.close()
     if rank == 0:
@@ -522,6 +598,7 @@ def run_ours(args):
                           "iterations": alt_st["iterations"], "rel_residual": alt_st["rel_residual"]},
             "apply": scan,
             "learned": learned,
+            "paper_cgls": paper,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(sum(s["launches"] for s in stats)),

@@ -255,6 +255,17 @@ void pn_default_solve_opts(pn_solve_opts* opts);
 int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_solve_stats* stats, void* stream);
 
 /*
+ * Solver workspace of the handle: *bytes (host) = device bytes the solvers
+ * hold (Krylov basis, Hessenberg scalars, refinement vectors, LGMRES ring),
+ * *allocations = device allocations made for them since pn_create.  A solve
+ * allocates only when it needs more workspace than earlier solves on the
+ * handle left (the first solve, a larger restart or augmentation); the
+ * workspace is kept until pn_destroy, so repeated solves with the same
+ * options allocate nothing.  Either output may be NULL.
+ */
+int pn_get_workspace(const pn_handle* h, int64_t* bytes, int64_t* allocations);
+
+/*
  * Single-scatter source of a collimated beam, as K = (N+1)^2 voxel-centre
  * moments (section "Rendering": the single-scattered light is folded into the
  * emission term, Q = sigma_s int p(w' -> w) L_u(w') dw', with L_u the
@@ -332,12 +343,15 @@ int pn_cnn_train_step(pn_cnn* net, const float* in, const float* target, int B, 
  * Scratch: a fixed 2 MiB __device__ array inside the library (one FP64
  * partial per 8192 elements plus a result slot), held on every device that
  * loads the library until the process exits.  The first call on a device
- * looks up the array's device address (with that device current), so make
- * that first call before any stream capture.  All calls share the array and
- * each call overwrites what it uses: calls whose kernels overlap on the GPU
- * (other streams, other host threads) race.  Synchronises `stream`.
- * Returns PN_OK, PN_ERR_ARG (NULL pointer, bad dtype, misalignment, n < 0),
- * PN_ERR_TOO_LARGE (n > PN_NOALLOC_MAX_ELEMS) or PN_ERR_CUDA.
+ * looks up the array's device address (with that device current).  Every
+ * call copies the result to the host and synchronises `stream`, so no call
+ * can be made on a stream that is being captured into a CUDA graph: such a
+ * call returns PN_ERR_ARG before any device work.  All calls share the array
+ * and each call overwrites what it uses: calls whose kernels overlap on the
+ * GPU (other streams, other host threads) race, so callers must serialise them.
+ * Returns PN_OK, PN_ERR_ARG (NULL pointer, bad dtype, misalignment, n < 0,
+ * a capturing stream), PN_ERR_TOO_LARGE (n > PN_NOALLOC_MAX_ELEMS) or
+ * PN_ERR_CUDA.
  */
 #define PN_NOALLOC_MAX_ELEMS (1LL << 31)
 int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype, double* out, void* stream);
@@ -506,6 +520,22 @@ int pn_set_l2_residency(pn_handle* h, int on);
  * formed in another order, so results agree to rounding.
  */
 int pn_set_stream_kernels(pn_handle* h, int mask);
+
+/*
+ * Self-test of the bounded mbarrier wait that the TMA-staged kernels use
+ * (an aid for tests; the paper has no counterpart).  One CTA arms an
+ * mbarrier: with deliver = 1 the phase completes at once; with deliver = 0 it
+ * expects 16 bytes that no copy brings, so the wait runs out after limit_ns
+ * (1 ns .. 10 s) of the GPU's global timer, sets the fault word and returns.
+ * No copy is issued.  With a handle the fault word is the handle's own (the
+ * one the operator and vector kernels set), so the next pn_solve on h returns
+ * PN_ERR_TIMEOUT and clears it; with h == NULL a temporary word is used.
+ * *timed_out (host) = 1 when this launch's wait ran out (a word already set
+ * before the call reads 0).  Returns PN_ERR_TIMEOUT when it did, PN_OK when
+ * the phase completed; PN_ERR_ARG, PN_ERR_ALLOC, PN_ERR_CUDA otherwise.
+ * Synchronises `stream`.
+ */
+int pn_wait_timeout_test(pn_handle* h, int deliver, long long limit_ns, int* timed_out, void* stream);
 
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */

@@ -24,13 +24,36 @@ int pn_cuda_fail(pn_handle* h, cudaError_t e, const char* where) {
 }
 
 int pn_sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    if (dev >= 0 && dev < kMaxDev) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
+    } else if (dev >= 0 && dev < kMaxDev) {
+        cache[dev].store(n, std::memory_order_relaxed);
     }
     return n;
+}
+
+cudaError_t pn_smem_attr_once(std::atomic<unsigned long long>& done, const void* func, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
 }
 
 namespace {
@@ -108,7 +131,7 @@ __global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int
 
 void free_all(pn_handle* h) {
     void* ptrs[] = {h->d_planes, h->d_terms, h->d_st_f, h->d_ss_f, h->d_st_d, h->d_ss_d,
-                    h->d_q_f,    h->d_q_d,   h->d_partials, h->d_scalars, h->d_work};
+                    h->d_q_f,    h->d_q_d,   h->d_partials, h->d_scalars, h->d_work, h->d_ir};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);

@@ -564,11 +564,10 @@ int face_blocks(const pn_handle* h) { return face_ranges(h).b[5]; }
 template <int N, int MODE>
 cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& p, cudaStream_t s) {
     auto kern = tiled::k_apply_tiled<N, kTY, MODE>;
-    static bool configured[8] = {false};
-    if (!configured[N]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static std::atomic<unsigned long long> configured{0};
+    {
+        cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(kern), 200 * 1024);
         if (e != cudaSuccess) return e;
-        configured[N] = true;
     }
     // columns right of the tiles and plane tails: disjoint outputs and partial
     // slots, same inputs; on the handle's side stream, concurrently, or after

@@ -435,13 +435,10 @@ const Maps* maps_for(const pn_handle* h, const void* x) {
 template <int N, int MODE>
 cudaError_t launch_n(const Maps& m, const Args& a, dim3 grid, cudaStream_t s) {
     auto kern = k_apply_tma<N, MODE>;
-    static bool configured = false;
+    static std::atomic<unsigned long long> configured{0};
     const size_t bytes = smem_bytes(N);
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(kern), int(bytes));
+    if (e != cudaSuccess) return e;
     kern<<<grid, dim3(TX, NG, TY), bytes, s>>>(m, a);
     return cudaGetLastError();
 }

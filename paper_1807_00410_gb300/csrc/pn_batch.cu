@@ -885,14 +885,21 @@ int ensure_graph(pn_batch* b) {
 
 // One cycle as a cooperative launch; PN_ERR_TIMEOUT when a barrier wait ran out.
 int launch_persistent(pn_batch* b) {
-    static int occ = 0;
+    // resident CTAs per SM, cached per device ordinal
+    static std::atomic<int> occ_cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, PN_ERR_CUDA, "pn_batch: cudaGetDevice failed");
+    }
+    int occ = (dev >= 0 && dev < 64) ? occ_cache[dev].load(std::memory_order_relaxed) : 0;
     if (occ == 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_cycle_persistent, 256, 0) != cudaSuccess ||
             occ < 1) {
             cudaGetLastError();
-            occ = 0;
             return bfail(b, PN_ERR_CUDA, "pn_batch: the persistent kernel cannot be resident");
         }
+        if (dev >= 0 && dev < 64) occ_cache[dev].store(occ, std::memory_order_relaxed);
     }
     const int grid = std::max(1, std::min(occ * pn_sm_count(), int(std::max(b->opc.size(), b->vc.size()))));
     CycleArgs a;

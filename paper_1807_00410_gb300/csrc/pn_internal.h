@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -46,8 +47,14 @@ inline void parity_bits(int l, int m, int& px, int& py, int& pz) {
 
 }  // namespace pn
 
-// Number of SMs of the current device (cached per process).
+// Number of SMs of the current device (cached per device ordinal).
 int pn_sm_count();
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device: bit d of *done records that device d has it (the
+// attribute belongs to the device context, so every device needs its own
+// call).  Two host threads may both make the call; it is idempotent.
+cudaError_t pn_smem_attr_once(std::atomic<unsigned long long>& done, const void* func, int bytes);
 
 struct pn_handle {
     int N = 0, K = 0, R = 0;
@@ -102,6 +109,13 @@ struct pn_handle {
     // Krylov workspace (lazily grown)
     void* d_work = nullptr;
     size_t work_bytes = 0;
+    // iterative refinement's vectors (FP64 residual, FP32 right-hand side and
+    // correction) and the LGMRES correction ring: allocated by the first solve
+    // that needs them, grown on demand, kept until pn_destroy, so that later
+    // solves allocate nothing
+    void* d_ir = nullptr;
+    size_t ir_bytes = 0;
+    int64_t work_allocs = 0;  // device allocations made for d_work and d_ir so far (pn_get_workspace)
 
     // launch profiler of pn_solve (opts.profile): event pairs pending readout
     bool prof_on = false;

@@ -169,11 +169,8 @@ cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int 
 
 // ---- reductions -------------------------------------------------------------
 
-static int g_reduce_blocks = 0;
-int reduce_blocks() {
-    if (g_reduce_blocks == 0) g_reduce_blocks = 2 * pn_sm_count();
-    return g_reduce_blocks;
-}
+// two blocks per SM of the current device (pn_sm_count caches per device)
+int reduce_blocks() { return 2 * pn_sm_count(); }
 
 // FP64 dot.  FP32 inputs: each thread sums runs of up to 32 products in FP32
 // and accumulates each run's sum in FP64.
@@ -217,7 +214,7 @@ cudaError_t launch_reduce(const double* partials, int nblocks, int nvals, double
 
 cudaError_t launch_dot(const pn_handle* h, const void* a, const void* b, int64_t n, int dtype,
                        double* out_dev, cudaStream_t s) {
-    const int nb = reduce_blocks();
+    const int nb = h->red_blocks;  // the handle's partials buffer is sized for it
     if (dtype == PN_F32) {
         k_dot_f32<<<nb, 256, 0, s>>>((const float4*)a, (const float4*)b, n / 4, h->d_partials);
     } else {

@@ -46,16 +46,24 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-__device__ __forceinline__ void wait(uint32_t bar, uint32_t parity, unsigned int* err, bool& failed) {
+// Waits for phase `parity` of `bar` to complete, for at most limit_ns of
+// %globaltimer; when the limit runs out it sets *err (if not null), marks the
+// caller failed (its later waits return at once) and returns.
+__device__ __forceinline__ void wait_ns(uint32_t bar, uint32_t parity, unsigned int* err, bool& failed,
+                                        uint64_t limit_ns) {
     if (try_wait(bar, parity) || failed) return;
     const uint64_t t0 = global_ns();
     while (!try_wait(bar, parity)) {
-        if (global_ns() - t0 > 2000000000ull) {
+        if (global_ns() - t0 > limit_ns) {
             failed = true;
             if (err) atomicExch(err, 1u);
             return;
         }
     }
+}
+
+__device__ __forceinline__ void wait(uint32_t bar, uint32_t parity, unsigned int* err, bool& failed) {
+    wait_ns(bar, parity, err, failed, 2000000000ull);
 }
 
 // 1D bulk copy global -> shared of `bytes` (a multiple of 16; both addresses

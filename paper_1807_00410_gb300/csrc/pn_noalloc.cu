@@ -110,10 +110,18 @@ extern "C" int pn_dot_noalloc(const void* x, const void* y, int64_t n, int dtype
         *out = 0.0;
         return PN_OK;
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the result comes back through a host copy and a stream synchronisation,
+    // which a capturing stream cannot take
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return PN_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return PN_ERR_ARG;
     double* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != PN_OK) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nb = int((n + kPerBlock - 1) / kPerBlock);
     if (dtype == PN_F32)
         k_dot_blocks<float><<<nb, kThreads, 0, s>>>(static_cast<const float*>(x), static_cast<const float*>(y), n,

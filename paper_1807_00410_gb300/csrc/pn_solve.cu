@@ -530,8 +530,10 @@ int ensure_work(pn_handle* h, size_t bytes) {
     if (h->d_work) cudaFree(h->d_work);
     h->d_work = nullptr;
     h->work_bytes = 0;
+    ++h->work_allocs;
     if (cudaMalloc(&h->d_work, bytes) != cudaSuccess) {
         cudaGetLastError();
+        h->d_work = nullptr;
         return pn_fail(h, PN_ERR_ALLOC, "pn_solve: cannot allocate Krylov workspace");
     }
     h->work_bytes = bytes;
@@ -987,12 +989,11 @@ template <int CH, int ST, int MINB>
 cudaError_t launch_md(int64_t n, const __half* V16, int nv, const float* w, float inv_sigma, double* partials,
                       unsigned int* ticket, double* H, int ldh, double* add, double* cs, double* sn, double* g, int j,
                       double* S, unsigned int* err, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_mdot16_tma<CH, ST, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(md_smem_bytes<CH, ST>()));
+    static std::atomic<unsigned long long> configured{0};
+    {
+        cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(k_mdot16_tma<CH, ST, MINB>),
+                                          int(md_smem_bytes<CH, ST>()));
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     k_mdot16_tma<CH, ST, MINB><<<MINB * pn_sm_count(), 256, md_smem_bytes<CH, ST>(), s>>>(
         n, V16, n, nv, w, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S, err);
@@ -1002,12 +1003,11 @@ cudaError_t launch_md(int64_t n, const __half* V16, int nv, const float* w, floa
 template <int CH, int ST, int MINB>
 cudaError_t launch_mx(int64_t n, const float* w, const __half* V16, int nv, const double* add, float inv_sigma,
                       float sigma, const double* S, __half* V16_out, float* vcur, unsigned int* err, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_maxpy16_tma<CH, ST, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(md_smem_bytes<CH, ST>()));
+    static std::atomic<unsigned long long> configured{0};
+    {
+        cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(k_maxpy16_tma<CH, ST, MINB>),
+                                          int(md_smem_bytes<CH, ST>()));
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     k_maxpy16_tma<CH, ST, MINB><<<MINB * pn_sm_count(), 256, md_smem_bytes<CH, ST>(), s>>>(
         n, w, V16, n, nv, add, inv_sigma, sigma, S, V16_out, vcur, err);
@@ -1543,35 +1543,38 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
     pn_handle* h = c.h;
     int fell_back = 0;
     const int64_t n = h->n_elems;
-    // r64 and the FP32 rhs / correction live outside the GMRES workspace
-    double* r64 = nullptr;
-    float* r32 = nullptr;
-    float* d32 = nullptr;
-    if (cudaMalloc(&r64, n * sizeof(double)) != cudaSuccess || cudaMalloc(&r32, n * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&d32, n * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        if (r64) cudaFree(r64);
-        if (r32) cudaFree(r32);
-        return pn_fail(h, PN_ERR_ALLOC, "ir: cannot allocate refinement vectors");
+    // r64, the FP32 rhs / correction and the LGMRES ring live in the handle's
+    // refinement workspace (outside the GMRES workspace): [r64][r32][d32][z ring]
+    const int ka = (o.augment > 0 && o.basis == PN_BASIS_F16 && !net) ? o.augment : 0;
+    const size_t b64 = size_t(n) * sizeof(double), b32 = size_t(n) * sizeof(float);  // n: a multiple of 32
+    const size_t need = b64 + 2 * b32 + size_t(ka ? ka + 1 : 0) * b32;
+    if (h->ir_bytes < need) {
+        if (h->d_ir) cudaFree(h->d_ir);
+        h->d_ir = nullptr;
+        h->ir_bytes = 0;
+        ++h->work_allocs;
+        if (cudaMalloc(&h->d_ir, need) != cudaSuccess) {
+            cudaGetLastError();
+            h->d_ir = nullptr;
+            return pn_fail(h, PN_ERR_ALLOC, "ir: cannot allocate the refinement vectors");
+        }
+        h->ir_bytes = need;
+    }
+    double* r64 = static_cast<double*>(h->d_ir);
+    float* r32 = reinterpret_cast<float*>(static_cast<char*>(h->d_ir) + b64);
+    float* d32 = r32 + n;
+    // LGMRES corrections (FP16-basis inner solver): kept across restarts and
+    // refinement steps (the same operator throughout)
+    Aug aug;
+    if (ka > 0) {
+        aug.k = ka;
+        aug.z = d32 + n;
     }
     const int nb = nb_vec();
     double* S = h->d_scalars;
     int outer = 0, inner = 0;
     double rel = 0.0;
     int rc = PN_OK;
-    // LGMRES corrections (FP16-basis inner solver): kept across restarts and
-    // refinement steps (the same operator throughout)
-    Aug aug;
-    if (o.augment > 0 && o.basis == PN_BASIS_F16 && !net) {
-        aug.k = o.augment;
-        if (cudaMalloc(&aug.z, size_t(aug.k + 1) * n * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(r64);
-            cudaFree(r32);
-            cudaFree(d32);
-            return pn_fail(h, PN_ERR_ALLOC, "ir: cannot allocate the augmentation vectors");
-        }
-    }
     for (;;) {
         c.pb();
         c.lk(pn::launch_op(h, pn::OP_RESIDUAL, x, r64, PN_F64, h->d_partials, c.s), "ir: residual", pn::op_launch_count(h, PN_F64));
@@ -1613,10 +1616,6 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
         ++outer;
     }
     if (rc == PN_OK) rc = c.rc;
-    cudaFree(r64);
-    cudaFree(r32);
-    cudaFree(d32);
-    if (aug.z) cudaFree(aug.z);
     st.iterations = inner;
     st.outer_iterations = outer;
     st.rel_residual = rel;
@@ -1626,6 +1625,13 @@ int ir_gmres(Ctx& c, double* x, const pn_solve_opts& o, pn_solve_stats& st, stru
 }
 
 }  // namespace
+
+extern "C" int pn_get_workspace(const pn_handle* h, int64_t* bytes, int64_t* allocations) {
+    if (!h) return PN_ERR_ARG;
+    if (bytes) *bytes = int64_t(h->work_bytes + h->ir_bytes);
+    if (allocations) *allocations = h->work_allocs;
+    return PN_OK;
+}
 
 extern "C" int pn_solve(pn_handle* h, void* u, const pn_solve_opts* opts, pn_solve_stats* stats, void* stream) {
     if (!h) return PN_ERR_ARG;

@@ -50,7 +50,8 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_batch_last_error", "pn_batch_apply", "pn_batch_solve", "pn_batch_set_tiling", "pn_batch_get_tiling",
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
-           "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels"]
+           "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels",
+           "pn_get_workspace", "pn_wait_timeout_test"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -112,6 +113,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_default_solve_opts": (None, [ctypes.POINTER(_SolveOpts)]),
         "pn_solve": (i, [vp, vp, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveStats), vp]),
         "pn_profile_get": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d)]),
+        "pn_get_workspace": (i, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "pn_wait_timeout_test": (i, [vp, i, ctypes.c_longlong, ctypes.POINTER(i), vp]),
         "pn_dot_noalloc": (i, [vp, vp, i64, i, ctypes.POINTER(d), vp]),
         "pn_single_scatter_beam": (i, [i, i, vp, vp, d, d, i, i, d, d, d, vp, i, vp]),
         "pn_unstagger": (i, [vp, vp, vp, i, vp]),
@@ -476,6 +479,13 @@ class System:
             out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
         return out
 
+    def workspace(self) -> dict:
+        """Solver workspace held by the handle (pn_get_workspace): device bytes
+        and the number of device allocations made for it so far."""
+        b, n = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.pn_get_workspace(self._h, ctypes.byref(b), ctypes.byref(n)))
+        return {"bytes": b.value, "allocations": n.value}
+
     def tune_apply(self, stream=None) -> dict:
         """The operator autotuner (pn_tune_apply): keeps the fastest main kernel
         and z-chunking."""
@@ -682,6 +692,17 @@ class Batch:
         if rc != PN_OK and raise_on_error:
             raise PnError(rc, self._lib.pn_batch_last_error(self._h).decode() + f" (stats {out})")
         return out
+
+
+def wait_timeout_test(system=None, deliver: bool = False, limit_ns: int = 2_000_000, stream=None):
+    """pn_wait_timeout_test: arm one mbarrier and wait on it with a limit of
+    limit_ns (deliver = False: a phase that never completes).  Returns
+    (return code, timed_out)."""
+    lib = load_library()
+    t = ctypes.c_int(-1)
+    h = system._h if system is not None else None
+    rc = lib.pn_wait_timeout_test(h, 1 if deliver else 0, int(limit_ns), ctypes.byref(t), _stream_ptr(stream))
+    return rc, t.value
 
 
 def barrier_test(blocks: int, expected: int, spin_limit: int, stream=None):

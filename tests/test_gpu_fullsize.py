@@ -1,0 +1,114 @@
+"""The benchmarked solve at its full size, judged by the FP64 CPU oracle.
+
+The bench times one configuration: P5 on 64^3 cells (9.6 M unknowns), FP64
+iterative refinement around FP32 LGMRES(12, 4) with one Gram-Schmidt pass, the
+Krylov basis stored in FP16, the bulk-copy staged multi-dot and multi-axpy,
+the L2 window over the step vectors and the autotuned operator.  Here the
+same call, with the same options, on the same seeded medium, must return a
+solution whose residual ||Q - A u|| / ||Q||, computed by the oracle's own
+matrix-free FP64 operator (section "Discretized RTE": A = T + C - S), meets
+the solve's target 1e-6.  The staged vector kernels walk every G-th
+1024-element chunk with a two-slot ring (G = 3 blocks per SM); a second case
+is sized so that every block takes at least three chunks, so the ring's slots
+are reused and the mbarrier phase flips inside one launch.
+"""
+import numpy as np
+import pytest
+
+import pn_inputs
+from oracle import grid as ogrid
+from oracle import pn as opn
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+# the bench's solve options (bench.py: run_ours)
+BENCH_OPTS = dict(solver="ir", tol=1e-6, restart=12, inner_tol=1e-2, max_iter=30000, check_every=5, ortho="cgs1",
+                  basis="f16", augment=4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1807_00410_gb300 import build
+    build.build()
+
+
+def _oracle_residual(p, gpu, u):
+    med = opn.Medium(p.sigma_t, p.albedo, p.g, p.Q00, p.sigma_t_min)
+    lay = ogrid.Layout(p.N, p.R)
+    uo = lay.join(gpu.to_planes(u))
+    b = opn.rhs(lay, med)
+    r = b - opn.apply_matrix_free(lay, med, uo)
+    return float(np.linalg.norm(r) / np.linalg.norm(b)), lay.split(uo)[0]
+
+
+def test_benchmarked_p5_64_solve_meets_oracle_residual_and_repeats_without_allocating():
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.p5_64_fbm(0)
+    gpu = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00, sigma_t_min=p.sigma_t_min)
+    gpu.tune_apply()
+    gpu.set_l2_residency(True)
+    gpu.set_stream_kernels(3)
+    u = gpu.zeros(torch.float64)
+    st = gpu.solve(u, **BENCH_OPTS)
+    assert st["rel_residual"] <= 1e-6
+    rel, _ = _oracle_residual(p, gpu, u)
+    assert rel <= 1.0001e-6, f"oracle residual {rel:.3e} (library {st['rel_residual']:.3e})"
+    # the second solve reuses the handle's workspace (no device allocation)
+    # and, every reduction having a fixed order, repeats the first bit for bit
+    ws = gpu.workspace()
+    assert ws["allocations"] >= 1 and ws["bytes"] > 0
+    u2 = gpu.zeros(torch.float64)
+    st2 = gpu.solve(u2, **BENCH_OPTS)
+    assert gpu.workspace() == ws
+    assert st2["iterations"] == st["iterations"] and torch.equal(u, u2)
+    gpu.close()
+
+
+def test_staged_vector_kernels_reuse_their_ring_slots_in_an_oracle_judged_solve():
+    """P3 on 48^3 cells: 2.0 M vector elements, more than three chunks of 1024
+    for each of the 3 x SMs blocks of the staged kernels.  The staged and the
+    direct vector kernels both give solutions meeting the oracle residual that
+    agree to the accuracy the residual allows."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(3, 48, 5, 0.5 * 48 / 64, 40.0 * 48 / 64, 0.95, 0.3)
+    gpu = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert gpu.layout.n_elems >= 3 * (3 * sms) * 1024
+    sols = []
+    for mask in (3, 0):
+        gpu.set_stream_kernels(mask)
+        u = gpu.zeros(torch.float64)
+        st = gpu.solve(u, **BENCH_OPTS)
+        assert st["rel_residual"] <= 1e-6
+        rel, l00 = _oracle_residual(p, gpu, u)
+        assert rel <= 1.0001e-6, f"mask {mask}: oracle residual {rel:.3e}"
+        sols.append(l00)
+    assert np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[1]) <= 2e-5
+    gpu.close()
+
+
+def test_bounded_mbarrier_wait_runs_out_and_pn_solve_reports_timeout():
+    """The bounded wait of the TMA-staged kernels (pn_mbar.cuh), made to run
+    out without any copy: an mbarrier armed for 16 bytes that nothing brings,
+    waited on for 2 ms.  The wait returns and sets the fault word; on a
+    handle's word the next pn_solve returns PN_ERR_TIMEOUT and clears it, and
+    the solve after that succeeds.  A phase that completes does not time out."""
+    from paper_1807_00410_gb300 import PnError, System
+    from paper_1807_00410_gb300.pn import wait_timeout_test
+    assert wait_timeout_test(None, deliver=True, limit_ns=2_000_000) == (0, 0)
+    assert wait_timeout_test(None, deliver=False, limit_ns=2_000_000) == (-7, 1)
+    p = pn_inputs.fbm_point(3, 16, 3, 0.5, 20.0, 0.9, 0.3)
+    gpu = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00)
+    opts = dict(solver="ir", tol=1e-6, restart=12, ortho="cgs1", basis="f16", augment=4)
+    assert wait_timeout_test(gpu, deliver=True, limit_ns=2_000_000) == (0, 0)
+    gpu.solve(gpu.zeros(torch.float64), **opts)
+    assert wait_timeout_test(gpu, deliver=False, limit_ns=2_000_000) == (-7, 1)
+    with pytest.raises(PnError) as ei:
+        gpu.solve(gpu.zeros(torch.float64), **opts)
+    assert ei.value.code == -7
+    st = gpu.solve(gpu.zeros(torch.float64), **opts)
+    assert st["rel_residual"] <= 1e-6
+    gpu.close()

@@ -76,3 +76,24 @@ def test_dot_noalloc_ragged_length_and_limits():
     assert rc == pn.PN_ERR_ARG
     rc, _ = _call(lib, a, b, n, 7)
     assert rc == pn.PN_ERR_ARG
+
+
+def test_dot_noalloc_refuses_a_capturing_stream():
+    """The call returns its result through a host copy and a stream
+    synchronisation, which a stream being captured into a CUDA graph cannot
+    take: on such a stream it returns PN_ERR_ARG before any device work, and
+    the capture stays valid."""
+    pn, lib = _lib()
+    a = torch.ones(4096, dtype=torch.float64, device="cuda")
+    b = torch.full_like(a, 2.0)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        c = a * 3.0
+        rc, _ = _call(lib, a, b, a.numel(), pn.PN_F64)
+    assert rc == pn.PN_ERR_ARG
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.all(c == 3.0)
+    rc, got = _call(lib, a, b, a.numel(), pn.PN_F64)
+    assert rc == pn.PN_OK and got == 2.0 * a.numel()
