@@ -301,41 +301,56 @@ __device__ __forceinline__ void ph_givens(const BInst* __restrict__ I, BState* s
     if (!S.live) return;  // uniform over the block
     const BInst& in = I[inst];
     __shared__ double vals[NV1];
+    // the column and the earlier rotations in shared memory: thread 0's
+    // rotation chain then reads no global memory (on the global arrays, which
+    // may alias, each step was a dependent round trip to L2)
+    __shared__ double cc[BM_MAX + 2], css[BM_MAX], sns[BM_MAX];
     block_chunk_sums(partials, NV1, vc_first[inst], vc_count[inst], j + 1, true, vals);
-    if (threadIdx.x != 0) return;
-    const double w2 = vals[BM_MAX];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        css[i] = in.cs[i];
+        sns[i] = in.sn[i];
+    }
+    __syncthreads();
     const int ldh = m + 1;
     double* col = in.H + int64_t(j) * ldh;
-    double hh = 0.0;
-    for (int i = 0; i <= j; ++i) {
-        in.proj[i] = vals[i];
-        col[i] = vals[i];
-        hh += vals[i] * vals[i];
+    if (threadIdx.x == 0) {
+        const double w2 = vals[BM_MAX];
+        double hh = 0.0;
+        for (int i = 0; i <= j; ++i) {
+            cc[i] = vals[i];
+            hh += vals[i] * vals[i];
+        }
+        // one Gram-Schmidt pass: |w - V h|^2 = |w|^2 - |h|^2 for orthonormal V
+        double nrm2 = w2 - hh;
+        if (!(nrm2 > 1e-12 * w2)) nrm2 = 0.0;  // breakdown: the Krylov space is invariant
+        const double hn = sqrt(fmax(nrm2, 0.0));
+        cc[j + 1] = hn;
+        S.scale = hn > 0.0 ? 1.0 / hn : 0.0;
+        for (int i = 0; i < j; ++i) {
+            const double t = css[i] * cc[i] + sns[i] * cc[i + 1];
+            cc[i + 1] = -sns[i] * cc[i] + css[i] * cc[i + 1];
+            cc[i] = t;
+        }
+        const double a = cc[j], b = cc[j + 1];
+        const double den = hypot(a, b);
+        const double c = den > 0.0 ? a / den : 1.0;
+        const double s = den > 0.0 ? b / den : 0.0;
+        in.cs[j] = c;
+        in.sn[j] = s;
+        cc[j] = den;
+        cc[j + 1] = 0.0;
+        const double gj = in.g[j];
+        in.g[j + 1] = -s * gj;
+        in.g[j] = c * gj;
+        S.res = fabs(-s * gj);
+        S.kdim = j + 1;
+        if (S.res <= S.target || j + 1 >= m || !(hn > 0.0)) S.live = 0;
     }
-    // one Gram-Schmidt pass: |w - V h|^2 = |w|^2 - |h|^2 for orthonormal V
-    double nrm2 = w2 - hh;
-    if (!(nrm2 > 1e-12 * w2)) nrm2 = 0.0;  // breakdown: the Krylov space is invariant
-    const double hn = sqrt(fmax(nrm2, 0.0));
-    col[j + 1] = hn;
-    S.scale = hn > 0.0 ? 1.0 / hn : 0.0;
-    for (int i = 0; i < j; ++i) {
-        const double t = in.cs[i] * col[i] + in.sn[i] * col[i + 1];
-        col[i + 1] = -in.sn[i] * col[i] + in.cs[i] * col[i + 1];
-        col[i] = t;
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
+        col[i] = cc[i];
+        if (i <= j) in.proj[i] = vals[i];
     }
-    const double a = col[j], b = col[j + 1];
-    const double den = hypot(a, b);
-    const double c = den > 0.0 ? a / den : 1.0;
-    const double s = den > 0.0 ? b / den : 0.0;
-    in.cs[j] = c;
-    in.sn[j] = s;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    in.g[j + 1] = -s * in.g[j];
-    in.g[j] = c * in.g[j];
-    S.res = fabs(in.g[j + 1]);
-    S.kdim = j + 1;
-    if (S.res <= S.target || j + 1 >= m || !(hn > 0.0)) S.live = 0;
 }
 
 __global__ void kb_givens(const BInst* __restrict__ I, BState* st, const int* vc_first, const int* vc_count,

@@ -276,50 +276,77 @@ __device__ __forceinline__ double lane_sum_partials(const double* p, int nb, int
     return t;
 }
 
-__device__ __forceinline__ void givens_core(double* H, int ldh, const double* add, double* cs, double* sn,
-                                            double* g, int j, double* S, int pythagoras, double nrm2_in) {
+// The Givens update of Arnoldi column j, run by one whole warp.  On entry the
+// shared array c[0..j] holds the column's projections h_{0..j} (the column of
+// H after Gram-Schmidt); `scr` (shared, >= 2 (j + 1) doubles) is scratch.
+//  * pythagoras != 0 (a single Gram-Schmidt pass): ||w - V h||^2 =
+//    ||w||^2 - ||h||^2 for orthonormal V; a remainder at rounding level is a
+//    breakdown (w lies in the span of V: the Krylov space is invariant and the
+//    least-squares solution exact): h_{j+1,j} = 0, the next basis vector 0, the
+//    residual estimate 0.  Otherwise nrm2_in is ||w||^2 after orthogonalisation.
+//  * the previous rotations are applied to the column, rotation j is formed,
+//    g is updated, |g[j+1]| goes to S[S_RES] and 1/h_{j+1,j} to S[S_SCALE].
+// The lanes load the earlier rotations and store the column in parallel; lane
+// 0 runs the sequential rotation chain in shared memory (on the global arrays,
+// which may alias, every step of the chain was a dependent round trip to L2).
+__device__ __forceinline__ void givens_warp(double* c, double* scr, double* H, int ldh, double* cs, double* sn, double* g, int j,
+                            double* S, int pythagoras, double nrm2_in) {
+    const int lane = threadIdx.x & 31;
+    double* css = scr;
+    double* sns = scr + (j + 1);
+    for (int i = lane; i < j; i += 32) {
+        css[i] = cs[i];
+        sns[i] = sn[i];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double nrm2 = nrm2_in;
+        if (pythagoras) {
+            double hh = 0.0;
+            for (int i = 0; i <= j; ++i) hh += c[i] * c[i];
+            nrm2 = nrm2 - hh;
+            // (rounding level: about 1e-14 of |w|^2 for FP32 vectors (pythagoras = 1),
+            // 1e-30 for FP64 (2), 1e-6 for a basis stored in FP16 (3))
+            const double tiny = pythagoras == 2 ? 1e-26 : (pythagoras == 3 ? 1e-5 : 1e-12);
+            if (!(nrm2 > tiny * nrm2_in)) nrm2 = 0.0;
+        }
+        const double hn = sqrt(fmax(nrm2, 0.0));
+        c[j + 1] = hn;
+        S[S_SCALE] = hn > 0.0 ? 1.0 / hn : 0.0;
+        for (int i = 0; i < j; ++i) {
+            const double t = css[i] * c[i] + sns[i] * c[i + 1];
+            c[i + 1] = -sns[i] * c[i] + css[i] * c[i + 1];
+            c[i] = t;
+        }
+        const double a = c[j], b = c[j + 1];
+        const double den = hypot(a, b);
+        const double cr = den > 0.0 ? a / den : 1.0;
+        const double sr = den > 0.0 ? b / den : 0.0;
+        cs[j] = cr;
+        sn[j] = sr;
+        c[j] = den;
+        c[j + 1] = 0.0;
+        const double gj = g[j];
+        g[j + 1] = -sr * gj;
+        g[j] = cr * gj;
+        S[S_RES] = fabs(-sr * gj);
+    }
+    __syncwarp();
     double* col = H + int64_t(j) * ldh;
-    double nrm2 = nrm2_in;
-    if (pythagoras) {
-        // single Gram-Schmidt pass: ||w - V h||^2 = ||w||^2 - ||h||^2 for orthonormal V.
-        // A remainder at rounding level is a breakdown (w lies in the span of V:
-        // the Krylov space is invariant and the least-squares solution exact):
-        // h_{j+1,j} = 0, the next basis vector 0, the residual estimate 0.
-        double hh = 0.0;
-        for (int i = 0; i <= j; ++i) hh += col[i] * col[i];
-        nrm2 = nrm2 - hh;
-        // (rounding level: about 1e-14 of |w|^2 for FP32 vectors (pythagoras = 1),
-        // 1e-30 for FP64 (2), 1e-6 for a basis stored in FP16 (3))
-        const double tiny = pythagoras == 2 ? 1e-26 : (pythagoras == 3 ? 1e-5 : 1e-12);
-        if (!(nrm2 > tiny * nrm2_in)) nrm2 = 0.0;
-    } else {
-        for (int i = 0; i <= j; ++i) col[i] += add[i];
-    }
-    const double hn = sqrt(fmax(nrm2, 0.0));
-    col[j + 1] = hn;
-    S[S_SCALE] = hn > 0.0 ? 1.0 / hn : 0.0;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double den = hypot(a, b);
-    const double c = den > 0.0 ? a / den : 1.0;
-    const double s = den > 0.0 ? b / den : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
-    S[S_RES] = fabs(g[j + 1]);
+    for (int i = lane; i <= j + 1; i += 32) col[i] = c[i];
 }
 
-__global__ void k_givens(double* H, int ldh, const double* add, double* cs, double* sn, double* g, int j,
-                         double* S, int pythagoras) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    givens_core(H, ldh, add, cs, sn, g, j, S, pythagoras, S[S_NRM2]);
+// Givens update of column j after classical Gram-Schmidt (one warp): the
+// column of H plus the second pass's corrections `add` (pythagoras = 0), or
+// the column alone with ||w||^2 in S[S_NRM2] (pythagoras != 0).
+__global__ void __launch_bounds__(32) k_givens(double* H, int ldh, const double* add, double* cs, double* sn,
+                                               double* g, int j, double* S, int pythagoras) {
+    __shared__ double c[202];
+    __shared__ double scr[402];  // j <= 199 (restart <= 200)
+    const double* col = H + int64_t(j) * ldh;
+    for (int i = threadIdx.x; i <= j; i += 32) c[i] = pythagoras ? col[i] : col[i] + add[i];
+    __syncwarp();
+    givens_warp(c, scr, H, ldh, cs, sn, g, j, S, pythagoras, S[S_NRM2]);
 }
 
 // One fused CGS1 step for j + 1 <= PN_MAX_MDOT basis vectors (FP32):
@@ -384,15 +411,17 @@ __global__ void __launch_bounds__(256) k_mdot_givens_f32(int64_t n4, const float
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double* col = H + int64_t(j) * ldh;
-        for (int i = 0; i <= j; ++i) {
+    if (warp == 0) {
+        // red is free again: c[0..j+1] at red[0..], the rotations' scratch after it
+        double* cc = &red[0][0];
+        for (int i = lane; i <= j; i += 32) {
+            cc[i] = tot[i];
             add[i] = tot[i];
-            col[i] = tot[i];
         }
-        S[S_NRM2] = tot[NV];
-        givens_core(H, ldh, add, cs, sn, g, j, S, 1, tot[NV]);
-        *ticket = 0u;
+        if (lane == 0) S[S_NRM2] = tot[NV];
+        __syncwarp();
+        givens_warp(cc, cc + (NV + 2), H, ldh, cs, sn, g, j, S, 1, tot[NV]);
+        if (lane == 0) *ticket = 0u;
     }
 }
 
@@ -705,16 +734,18 @@ __device__ __forceinline__ void mdot16_finish(const float (&part)[PN_MAX_MDOT + 
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double* col = H + int64_t(j) * ldh;
-        for (int i = 0; i <= j; ++i) {
+    if (warp == 0) {
+        // red is free again: c[0..j+1] at red[0..], the rotations' scratch after it
+        double* cc = &red[0][0];
+        for (int i = lane; i <= j; i += 32) {
             const double hi = tot[i] * double(inv_sigma);
+            cc[i] = hi;
             add[i] = hi;
-            col[i] = hi;
         }
-        S[S_NRM2] = tot[NV];
-        givens_core(H, ldh, add, cs, sn, g, j, S, 3, tot[NV]);
-        *ticket = 0u;
+        if (lane == 0) S[S_NRM2] = tot[NV];
+        __syncwarp();
+        givens_warp(cc, cc + (NV + 2), H, ldh, cs, sn, g, j, S, 3, tot[NV]);
+        if (lane == 0) *ticket = 0u;
     }
 }
 
