@@ -310,7 +310,7 @@ CPU_SAMPLE_ITERS = 20
 # iterations FP64 CGLS needs to reach 1e-6 on the P5 64^3 workload (medium
 # seed 0), measured by the bench's own `paper_cgls` run of the library's FP64
 # CGLS on GB300 (the GPU arm reports the count it measured next to this one)
-REF_CGLS_ITERS = 0
+REF_CGLS_ITERS = 650
 
 
 # ----------------------------------------------------------------------------
