@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0, help="medium seed offset (the medium of rank r is seed + r)")
     ap.add_argument("--stream-tma", type=int, default=3,
                     help="FP16-basis GMRES: bulk-copy staged multi-dot (bit 0) and multi-axpy (bit 1)")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="launch the Arnoldi-step kernels without programmatic dependent launch")
     ap.add_argument("--no-l2-resident", action="store_true",
                     help="do not keep the solver's FP32 step vectors resident in L2")
     ap.add_argument("--augment", type=int, default=4,
@@ -421,6 +423,7 @@ def run_ours(args):
     tiling = sysm.tune_apply()  # the operator's kernel and z-chunking, picked by timing (setup, untimed)
     sysm.set_l2_residency(not args.no_l2_resident)
     sysm.set_stream_kernels(args.stream_tma)
+    sysm.set_pdl(not args.no_pdl)
     if args.apply_kernel != "auto":
         sysm.set_apply_kernel(args.apply_kernel)
         tiling["kernel"] = sysm.apply_kernel
@@ -585,6 +588,7 @@ def run_ours(args):
                                   f"FP64 iterative refinement around FP32 GMRES({args.restart})"),
                        "restart": args.restart,
                        "augment": opts["augment"], "ortho": args.ortho, "l2_resident": not args.no_l2_resident,
+                       "pdl": not args.no_pdl,
                        "stream_tma": args.stream_tma,
                        "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"],
                        "apply_face_serial": tiling["face_serial"],

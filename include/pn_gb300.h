@@ -537,6 +537,16 @@ int pn_set_stream_kernels(pn_handle* h, int mask);
  */
 int pn_wait_timeout_test(pn_handle* h, int deliver, long long limit_ns, int* timed_out, void* stream);
 
+/*
+ * Programmatic dependent launch in the FP16-basis GMRES (PN_BASIS_F16): the
+ * kernels of each Arnoldi step (operator, fused CGS1 step, multi-axpy) are
+ * launched so that each may start while the one before it finishes; each
+ * kernel waits for its predecessor's results before it reads them (copies of
+ * inputs that are already complete go out before the wait).  on = 1
+ * (default) or 0.  Results do not depend on it (bitwise).
+ */
+int pn_set_pdl(pn_handle* h, int on);
+
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */
 #define PN_PROF_RESIDUAL 1   /* residual operator launches */

@@ -600,6 +600,12 @@ int pn_set_stream_kernels(pn_handle* h, int tma) {
     return PN_OK;
 }
 
+int pn_set_pdl(pn_handle* h, int on) {
+    if (!h) return PN_ERR_ARG;
+    h->pdl_enabled = on ? 1 : 0;
+    return PN_OK;
+}
+
 int pn_set_l2_residency(pn_handle* h, int on) {
     if (!h) return PN_ERR_ARG;
     h->l2_resident = on ? 1 : 0;

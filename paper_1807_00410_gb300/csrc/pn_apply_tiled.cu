@@ -31,6 +31,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "pn_pdl.cuh"
 #include "pn_tiled.cuh"
 
 namespace pn {
@@ -293,6 +294,8 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
 
 template <int N, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
+    pdl_wait();  // programmatic dependent launch (pn_pdl.cuh)
+    pdl_trigger();
     if (a.live && !*a.live) return;  // uniform over the grid
     extern __shared__ float smem[];
     // warp w runs group w % 4 (one group's code per scheduler; see pn_apply_tma.cu)
@@ -427,7 +430,7 @@ struct FaceRanges {
 };
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr) {
+__device__ __forceinline__ void face_body(const Args& a, int x_lo, const FaceRanges& fr) {
     if (a.live && !*a.live) return;  // uniform over the grid
     constexpr Tab T = TabN<N>::value;
     constexpr int K = T.K;
@@ -497,6 +500,18 @@ __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr)
             a.partials[blockIdx.x] = tsum;
         }
     }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr) {
+    // Launched right after the main kernel, whose outputs it does not read
+    // (disjoint slots, same inputs): with programmatic dependent launch it
+    // starts once every main CTA is past its own wait (so the input is
+    // complete), runs alongside, and waits for the main kernel before it
+    // exits, so its completion implies the main kernel's.
+    pdl_trigger();
+    face_body<N, MODE>(a, x_lo, fr);
+    pdl_wait();
 }
 
 }  // namespace tiled
@@ -572,7 +587,11 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
     // columns right of the tiles and plane tails: disjoint outputs and partial
     // slots, same inputs; on the handle's side stream, concurrently, or after
     // the main kernel on the same stream (h->face_serial, chosen by the tuner)
-    cudaStream_t fs = (h->side && !h->face_serial) ? h->side : s;
+    // With programmatic dependent launch (h->pdl, inside the Arnoldi loop) both
+    // kernels go to s: the face kernel starts while the main kernel runs and
+    // waits for it before it exits (k_face_x).
+    const bool pdl = h->pdl != 0;
+    cudaStream_t fs = (h->side && !h->face_serial && !pdl) ? h->side : s;
     cudaError_t e = cudaSuccess;
     if (fs != s) {
         e = cudaEventRecord(h->ev_fork, s);
@@ -582,15 +601,13 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
     if (h->tile_kernel == PN_APPLY_KERNEL_TMA && tma_serves(h)) {
         e = launch_tma_main(h, MODE, a, p.grid, s);
     } else {
-        kern<<<p.grid, p.block, p.smem, s>>>(a);
-        e = cudaGetLastError();
+        e = launch_pdl(pdl, kern, p.grid, p.block, p.smem, s, a);
     }
     if (e != cudaSuccess) return e;
     tiled::Args af = a;
     if (af.partials) af.partials += p.grid.x * p.grid.y * p.grid.z;
     const tiled::FaceRanges fr = face_ranges(h);
-    tiled::k_face_x<N, MODE><<<fr.b[5], 256, 0, fs>>>(af, p.x_end, fr);
-    e = cudaGetLastError();
+    e = launch_pdl(pdl, tiled::k_face_x<N, MODE>, dim3(fr.b[5]), dim3(256), 0, fs, af, p.x_end, fr);
     if (e != cudaSuccess || fs == s) return e;
     e = cudaEventRecord(h->ev_join, fs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);

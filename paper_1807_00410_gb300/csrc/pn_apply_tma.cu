@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "pn_mbar.cuh"
+#include "pn_pdl.cuh"
 #include "pn_tiled.cuh"
 
 namespace pn {
@@ -304,6 +305,10 @@ __device__ __forceinline__ void run_group(const Maps& m, const Args& a, float* r
 template <int N, int MODE>
 __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)) ? 2 : 1)
     k_apply_tma(const __grid_constant__ Maps m, Args a) {
+    // programmatic dependent launch: the input (and the gate) come from the
+    // previous kernel; the next kernel may start once every CTA is past here
+    pdl_wait();
+    pdl_trigger();
     if (a.live && !*a.live) return;  // uniform over the grid
     constexpr Lay L = LayN<N>::value;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -433,27 +438,27 @@ const Maps* maps_for(const pn_handle* h, const void* x) {
 }
 
 template <int N, int MODE>
-cudaError_t launch_n(const Maps& m, const Args& a, dim3 grid, cudaStream_t s) {
+cudaError_t launch_n(const Maps& m, const Args& a, dim3 grid, cudaStream_t s, bool pdl) {
     auto kern = k_apply_tma<N, MODE>;
     static std::atomic<unsigned long long> configured{0};
     const size_t bytes = smem_bytes(N);
     cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(kern), int(bytes));
     if (e != cudaSuccess) return e;
-    kern<<<grid, dim3(TX, NG, TY), bytes, s>>>(m, a);
-    return cudaGetLastError();
+    return launch_pdl(pdl, kern, grid, dim3(TX, NG, TY), bytes, s, m, a);
 }
 
 template <int MODE>
 cudaError_t launch_mode(const pn_handle* h, const Maps& m, const Args& a, dim3 grid, cudaStream_t s) {
+    const bool pdl = h->pdl != 0;
     switch (h->N) {
-        case 0: return launch_n<0, MODE>(m, a, grid, s);
-        case 1: return launch_n<1, MODE>(m, a, grid, s);
-        case 2: return launch_n<2, MODE>(m, a, grid, s);
-        case 3: return launch_n<3, MODE>(m, a, grid, s);
-        case 4: return launch_n<4, MODE>(m, a, grid, s);
-        case 5: return launch_n<5, MODE>(m, a, grid, s);
-        case 6: return launch_n<6, MODE>(m, a, grid, s);
-        default: return launch_n<7, MODE>(m, a, grid, s);
+        case 0: return launch_n<0, MODE>(m, a, grid, s, pdl);
+        case 1: return launch_n<1, MODE>(m, a, grid, s, pdl);
+        case 2: return launch_n<2, MODE>(m, a, grid, s, pdl);
+        case 3: return launch_n<3, MODE>(m, a, grid, s, pdl);
+        case 4: return launch_n<4, MODE>(m, a, grid, s, pdl);
+        case 5: return launch_n<5, MODE>(m, a, grid, s, pdl);
+        case 6: return launch_n<6, MODE>(m, a, grid, s, pdl);
+        default: return launch_n<7, MODE>(m, a, grid, s, pdl);
     }
 }
 

@@ -75,6 +75,12 @@ struct pn_handle {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int l2_resident = 1;
     int stream_tma = 3;  // FP16-basis GMRES: bulk-copy (TMA) staged multi-dot (bit 0) and multi-axpy (bit 1)
+    // set by the FP16-basis GMRES around its Arnoldi-step operator launches:
+    // the tiled operator's kernels are launched with programmatic dependent
+    // launch (pn_pdl.cuh), overlapping their start with the previous kernel's
+    // tail; pn_set_pdl turns it off (default on)
+    int pdl = 0;
+    int pdl_enabled = 1;
     int64_t nz_box = 0;  // z-slices of a plane box: R + 1 (3D) or 1 (2D)
     double h = 0.0;
     double g = 0.0;  // Henyey-Greenstein mean cosine

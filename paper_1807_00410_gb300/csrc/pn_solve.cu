@@ -18,6 +18,7 @@
 
 #include "pn_internal.h"
 #include "pn_mbar.cuh"
+#include "pn_pdl.cuh"
 
 namespace {
 
@@ -754,6 +755,8 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
                                                        unsigned int* ticket, double* H, int ldh, double* add,
                                                        double* cs, double* sn, double* g, int j, double* S) {
     constexpr int NV = PN_MAX_MDOT;
+    pn::pdl_wait();  // w comes from the operator launched before (programmatic dependent launch)
+    pn::pdl_trigger();
     float part[NV + 1];
 #pragma unroll
     for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
@@ -817,19 +820,36 @@ __global__ void __launch_bounds__(256, MINB) k_mdot16_tma(int64_t n, const __hal
         pn::mbar::fence_init();
     }
     __syncthreads();
-    auto issue = [&](int64_t c, int st) {
+    // a chunk's copies: the basis slices (written by earlier launches) and w
+    // (written by the operator just before this kernel), one mbarrier
+    auto issue_v = [&](int64_t c, int st) {
         const int64_t e0 = c * MD_CH;
         const int64_t rem = n - e0;
         const uint32_t cnt = uint32_t(rem < MD_CH ? rem : MD_CH);
         const uint32_t bar = bar_s + 8u * st;
         pn::mbar::arrive_expect_tx(bar, cnt * 4u + uint32_t(nv) * cnt * 2u);
-        pn::mbar::bulk_g2s(pn::mbar::smem_u32(sw + st * MD_CH), w + e0, cnt * 4u, bar);
         for (int v = 0; v < nv; ++v)
             pn::mbar::bulk_g2s(pn::mbar::smem_u32(sv + (size_t(st) * NV + v) * MD_CH), V16 + v * vstride + e0, cnt * 2u,
                            bar);
     };
+    auto issue_w = [&](int64_t c, int st) {
+        const int64_t e0 = c * MD_CH;
+        const int64_t rem = n - e0;
+        const uint32_t cnt = uint32_t(rem < MD_CH ? rem : MD_CH);
+        pn::mbar::bulk_g2s(pn::mbar::smem_u32(sw + st * MD_CH), w + e0, cnt * 4u, bar_s + 8u * st);
+    };
+    auto issue = [&](int64_t c, int st) {
+        issue_v(c, st);
+        issue_w(c, st);
+    };
+    // programmatic dependent launch: the basis copies of the first chunks go
+    // out before the wait for the operator, w's after it
     if (tid == 0)
-        for (int k = 0; k < MD_ST && k < nk; ++k) issue(blockIdx.x + k * G, k);
+        for (int k = 0; k < MD_ST && k < nk; ++k) issue_v(blockIdx.x + k * G, k);
+    pn::pdl_wait();
+    pn::pdl_trigger();
+    if (tid == 0)
+        for (int k = 0; k < MD_ST && k < nk; ++k) issue_w(blockIdx.x + k * G, k);
     float part[NV + 1];
 #pragma unroll
     for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
@@ -878,6 +898,8 @@ __global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* __res
                                                  const double* add, float inv_sigma, float sigma, const double* S,
                                                  uint4* __restrict__ V16_out, float4* __restrict__ vcur) {
     constexpr int NV = PN_MAX_MDOT;
+    pn::pdl_wait();  // the projections come from the multi-dot launched before
+    pn::pdl_trigger();
     float cj[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
@@ -949,10 +971,6 @@ __global__ void __launch_bounds__(256, MINB) k_maxpy16_tma(int64_t n, const floa
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + size_t(MD_ST) * MD_CH * 4 + size_t(MD_ST) * NV * MD_CH * 2);
     const uint32_t bar_s = pn::mbar::smem_u32(bars);
     const int tid = threadIdx.x;
-    float cj[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
-    const float sc = float(S[S_SCALE]);
     // block b takes chunks b, b + G, b + 2G, ...: at any moment the blocks work
     // on neighbouring chunks, so each stream is read from one region of DRAM
     const int64_t nch = (n + MD_CH - 1) / MD_CH;
@@ -974,8 +992,17 @@ __global__ void __launch_bounds__(256, MINB) k_maxpy16_tma(int64_t n, const floa
             pn::mbar::bulk_g2s(pn::mbar::smem_u32(sv + (size_t(st) * NV + v) * MD_CH), V16 + v * vstride + e0,
                                cnt * 2u, bar);
     };
+    // programmatic dependent launch: w (from the operator two launches back,
+    // complete once the multi-dot before this kernel passed its own wait) and
+    // the basis are copied before the wait for the multi-dot's projections
     if (tid == 0)
         for (int k = 0; k < MD_ST && k < nk; ++k) issue(blockIdx.x + k * G, k);
+    pn::pdl_wait();
+    pn::pdl_trigger();
+    float cj[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
+    const float sc = float(S[S_SCALE]);
     bool failed = false;
     for (int64_t kk = 0; kk < nk; ++kk) {
         const int64_t c = blockIdx.x + kk * G;
@@ -1019,30 +1046,31 @@ __global__ void __launch_bounds__(256, MINB) k_maxpy16_tma(int64_t n, const floa
 template <int CH, int ST, int MINB>
 cudaError_t launch_md(int64_t n, const __half* V16, int nv, const float* w, float inv_sigma, double* partials,
                       unsigned int* ticket, double* H, int ldh, double* add, double* cs, double* sn, double* g, int j,
-                      double* S, unsigned int* err, cudaStream_t s) {
+                      double* S, unsigned int* err, cudaStream_t s, bool pdl) {
     static std::atomic<unsigned long long> configured{0};
     {
         cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(k_mdot16_tma<CH, ST, MINB>),
                                           int(md_smem_bytes<CH, ST>()));
         if (e != cudaSuccess) return e;
     }
-    k_mdot16_tma<CH, ST, MINB><<<MINB * pn_sm_count(), 256, md_smem_bytes<CH, ST>(), s>>>(
-        n, V16, n, nv, w, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S, err);
-    return cudaGetLastError();
+    return pn::launch_pdl(pdl, k_mdot16_tma<CH, ST, MINB>, dim3(MINB * pn_sm_count()), dim3(256),
+                          md_smem_bytes<CH, ST>(), s, n, V16, int64_t(n), nv, w, inv_sigma, partials, ticket, H, ldh,
+                          add, cs, sn, g, j, S, err);
 }
 
 template <int CH, int ST, int MINB>
 cudaError_t launch_mx(int64_t n, const float* w, const __half* V16, int nv, const double* add, float inv_sigma,
-                      float sigma, const double* S, __half* V16_out, float* vcur, unsigned int* err, cudaStream_t s) {
+                      float sigma, const double* S, __half* V16_out, float* vcur, unsigned int* err, cudaStream_t s,
+                      bool pdl) {
     static std::atomic<unsigned long long> configured{0};
     {
         cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(k_maxpy16_tma<CH, ST, MINB>),
                                           int(md_smem_bytes<CH, ST>()));
         if (e != cudaSuccess) return e;
     }
-    k_maxpy16_tma<CH, ST, MINB><<<MINB * pn_sm_count(), 256, md_smem_bytes<CH, ST>(), s>>>(
-        n, w, V16, n, nv, add, inv_sigma, sigma, S, V16_out, vcur, err);
-    return cudaGetLastError();
+    return pn::launch_pdl(pdl, k_maxpy16_tma<CH, ST, MINB>, dim3(MINB * pn_sm_count()), dim3(256),
+                          md_smem_bytes<CH, ST>(), s, n, w, V16, int64_t(n), nv, add, inv_sigma, sigma, S, V16_out,
+                          vcur, err);
 }
 
 // 1024-element chunks, two slots, three blocks per SM: the best of
@@ -1050,14 +1078,15 @@ cudaError_t launch_mx(int64_t n, const float* w, const __half* V16, int nv, cons
 // slots, blocks per SM) on the P5 64^3 solve.
 cudaError_t launch_mdot16_tma(int64_t n, const __half* V16, int nv, const float* w, float inv_sigma,
                               double* partials, unsigned int* ticket, double* H, int ldh, double* add, double* cs,
-                              double* sn, double* g, int j, double* S, unsigned int* err, cudaStream_t s) {
-    return launch_md<1024, 2, 3>(n, V16, nv, w, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S, err, s);
+                              double* sn, double* g, int j, double* S, unsigned int* err, cudaStream_t s, bool pdl) {
+    return launch_md<1024, 2, 3>(n, V16, nv, w, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S, err, s,
+                                 pdl);
 }
 
 cudaError_t launch_maxpy16_tma(int64_t n, const float* w, const __half* V16, int nv, const double* add,
                                float inv_sigma, float sigma, const double* S, __half* V16_out, float* vcur,
-                               unsigned int* err, cudaStream_t s) {
-    return launch_mx<1024, 2, 3>(n, w, V16, nv, add, inv_sigma, sigma, S, V16_out, vcur, err, s);
+                               unsigned int* err, cudaStream_t s, bool pdl) {
+    return launch_mx<1024, 2, 3>(n, w, V16, nv, add, inv_sigma, sigma, S, V16_out, vcur, err, s, pdl);
 }
 
 // First basis vector: r / beta (beta^2 = S[S_BETA2]) into V16_0 (scaled) and vcur.
@@ -1309,8 +1338,13 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
         for (; j < s && total < max_iter; ++j) {
             c.pb();
             const float* zin = j < m ? vcur : zaug(j - m);
+            // the Arnoldi step's kernels (operator, multi-dot, multi-axpy) are
+            // chained by programmatic dependent launch (pn_pdl.cuh)
+            const bool pdl = h->pdl_enabled != 0;
+            h->pdl = pdl ? 1 : 0;
             c.lk(pn::launch_op(h, pn::OP_APPLY, zin, w, PN_F32, nullptr, c.s), "gmres16: A v",
                  pn::op_launch_count(h, PN_F32));
+            h->pdl = 0;
             c.pe(PN_PROF_APPLY, ob);
             c.pb();
             // staged from MD_MIN_NV basis vectors on (ncu, P5 64^3, cold: the
@@ -1319,24 +1353,26 @@ int gmres_f16(Ctx& c, float* x, const float* bvec, double bnorm2, double tol, in
             if ((h->stream_tma & 1) && j + 1 >= MD_MIN_NV) {
                 c.ok(launch_mdot16_tma(n, V16, j + 1, w, inv_sigma, h->d_partials,
                                        reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add, cs, sn, g, j, S,
-                                       reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s),
+                                       reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s, pdl),
                      "gmres16: mdot");
             } else {
-                k_mdot16_givens<<<nb_mdot(), 256, 0, c.s>>>(n8, (const uint4*)V16, vs8, j + 1, (const float4*)w,
-                                                            inv_sigma, h->d_partials,
-                                                            reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh,
-                                                            add, cs, sn, g, j, S);
+                c.ok(pn::launch_pdl(pdl, k_mdot16_givens, dim3(nb_mdot()), dim3(256), 0, c.s, n8, (const uint4*)V16,
+                                    vs8, j + 1, (const float4*)w, inv_sigma, h->d_partials,
+                                    reinterpret_cast<unsigned int*>(S + S_TICKET), H, ldh, add, cs, sn, g, j, S),
+                     "gmres16: mdot");
             }
             c.launched("gmres16: mdot");
             c.pe(PN_PROF_MDOT, double(h->n_active) * (2.0 * (j + 1) + 4.0));
             c.pb();
             if ((h->stream_tma & 2) && j + 1 >= MD_MIN_NV) {  // (23.3 against 30.5 us at one vector)
                 c.ok(launch_maxpy16_tma(n, w, V16, j + 1, add, inv_sigma, sigma, S, V16 + size_t(j + 1) * n, vcur,
-                                        reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s),
+                                        reinterpret_cast<unsigned int*>(S + PN_S_FAULT), c.s, pdl),
                      "gmres16: maxpy");
             } else {
-                k_maxpy16<<<nb, 256, 0, c.s>>>(n8, (const float4*)w, (const uint4*)V16, vs8, j + 1, add, inv_sigma,
-                                               sigma, S, (uint4*)V16 + int64_t(j + 1) * vs8, (float4*)vcur);
+                c.ok(pn::launch_pdl(pdl, k_maxpy16, dim3(nb), dim3(256), 0, c.s, n8, (const float4*)w,
+                                    (const uint4*)V16, vs8, j + 1, (const double*)add, inv_sigma, sigma,
+                                    (const double*)S, (uint4*)V16 + int64_t(j + 1) * vs8, (float4*)vcur),
+                     "gmres16: maxpy");
             }
             c.launched("gmres16: maxpy");
             c.pe(PN_PROF_MAXPY, double(h->n_active) * (4.0 + 2.0 * (j + 1) + 2.0 + 4.0));

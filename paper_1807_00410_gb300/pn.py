@@ -51,7 +51,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
            "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels",
-           "pn_get_workspace", "pn_wait_timeout_test"]
+           "pn_get_workspace", "pn_wait_timeout_test", "pn_set_pdl"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -148,6 +148,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_get_apply_kernel": (i, [vp, ctypes.POINTER(i)]),
         "pn_set_l2_residency": (i, [vp, i]),
         "pn_set_stream_kernels": (i, [vp, i]),
+        "pn_set_pdl": (i, [vp, i]),
         "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
@@ -512,6 +513,11 @@ class System:
     def set_stream_kernels(self, mask: int):
         """FP16-basis GMRES: bit 0 bulk-copy (TMA) staged multi-dot, bit 1 multi-axpy."""
         self._check(self._lib.pn_set_stream_kernels(self._h, int(mask)))
+
+    def set_pdl(self, on: bool):
+        """Chain the FP16-basis GMRES's Arnoldi-step kernels by programmatic
+        dependent launch (default on; results unchanged)."""
+        self._check(self._lib.pn_set_pdl(self._h, 1 if on else 0))
 
     def set_l2_residency(self, on: bool):
         """Keep the FP16-basis GMRES's two FP32 step vectors resident in L2."""

@@ -112,3 +112,26 @@ def test_bounded_mbarrier_wait_runs_out_and_pn_solve_reports_timeout():
     st = gpu.solve(gpu.zeros(torch.float64), **opts)
     assert st["rel_residual"] <= 1e-6
     gpu.close()
+
+
+def test_programmatic_dependent_launch_changes_no_bit():
+    """The FP16-basis GMRES chains its Arnoldi-step kernels by programmatic
+    dependent launch: each kernel may start while its predecessor finishes and
+    waits for its results before reading them.  With and without it the solve
+    computes the same bits (P5 on 40^3 cells, every kernel of the step in use:
+    the face-column kernel alongside the main operator kernel, the direct and
+    the staged vector kernels)."""
+    from paper_1807_00410_gb300 import System
+    p = pn_inputs.fbm_point(5, 40, 9, 0.5 * 40 / 64, 40.0 * 40 / 64, 0.95, 0.3)
+    gpu = System(p.N, p.R, p.sigma_t, p.albedo, p.g, p.Q00)
+    sols = []
+    for on in (True, False, True):
+        gpu.set_pdl(on)
+        u = gpu.zeros(torch.float64)
+        st = gpu.solve(u, **BENCH_OPTS)
+        assert st["rel_residual"] <= 1e-6
+        sols.append((u, st["iterations"]))
+    assert all(torch.equal(sols[0][0], u) and sols[0][1] == it for u, it in sols[1:])
+    rel, _ = _oracle_residual(p, gpu, sols[0][0])
+    assert rel <= 1.0001e-6
+    gpu.close()
