@@ -295,7 +295,6 @@ __device__ __forceinline__ void run_group(const Args& a, float* smem, int tx, in
 template <int N, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
     pdl_wait();  // programmatic dependent launch (pn_pdl.cuh)
-    pdl_trigger();
     if (a.live && !*a.live) return;  // uniform over the grid
     extern __shared__ float smem[];
     // warp w runs group w % 4 (one group's code per scheduler; see pn_apply_tma.cu)
@@ -310,6 +309,7 @@ __global__ void __launch_bounds__(TX * TY * NG, 1) k_apply_tiled(Args a) {
         case 2: run_group<N, TY, 2, MODE>(a, smem, tx, ty, x, y, za, zb, racc); break;
         default: run_group<N, TY, 3, MODE>(a, smem, tx, ty, x, y, za, zb, racc); break;
     }
+    pdl_trigger();
     if (MODE == OP_RESIDUAL && a.partials != nullptr) {
         __shared__ double red[TX * TY * NG / 32];
         for (int o = 16; o > 0; o >>= 1) racc += __shfl_down_sync(0xffffffffu, racc, o);
@@ -504,14 +504,13 @@ __device__ __forceinline__ void face_body(const Args& a, int x_lo, const FaceRan
 
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr) {
-    // Launched right after the main kernel, whose outputs it does not read
-    // (disjoint slots, same inputs): with programmatic dependent launch it
-    // starts once every main CTA is past its own wait (so the input is
-    // complete), runs alongside, and waits for the main kernel before it
-    // exits, so its completion implies the main kernel's.
-    pdl_trigger();
-    face_body<N, MODE>(a, x_lo, fr);
+    // Launched right after the main kernel (programmatic dependent launch:
+    // its CTAs become resident during the main kernel's last wave), it waits
+    // for the main kernel before any work, so the two run one after the other
+    // (running them side by side slowed the main kernel down).
     pdl_wait();
+    face_body<N, MODE>(a, x_lo, fr);
+    pdl_trigger();
 }
 
 }  // namespace tiled
@@ -588,8 +587,7 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
     // slots, same inputs; on the handle's side stream, concurrently, or after
     // the main kernel on the same stream (h->face_serial, chosen by the tuner)
     // With programmatic dependent launch (h->pdl, inside the Arnoldi loop) both
-    // kernels go to s: the face kernel starts while the main kernel runs and
-    // waits for it before it exits (k_face_x).
+    // kernels go to s (k_face_x waits for the main kernel).
     const bool pdl = h->pdl != 0;
     cudaStream_t fs = (h->side && !h->face_serial && !pdl) ? h->side : s;
     cudaError_t e = cudaSuccess;

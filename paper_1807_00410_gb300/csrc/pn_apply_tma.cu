@@ -306,9 +306,9 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)) ? 2 : 1)
     k_apply_tma(const __grid_constant__ Maps m, Args a) {
     // programmatic dependent launch: the input (and the gate) come from the
-    // previous kernel; the next kernel may start once every CTA is past here
+    // previous kernel; the next kernel may start once every CTA has finished
+    // its z-march (the trigger below)
     pdl_wait();
-    pdl_trigger();
     if (a.live && !*a.live) return;  // uniform over the grid
     constexpr Lay L = LayN<N>::value;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
         case 2: run_group<N, 2, MODE>(m, a, ring, sg, bar_s, tx, ty, za, zb, racc); break;
         default: run_group<N, 3, MODE>(m, a, ring, sg, bar_s, tx, ty, za, zb, racc); break;
     }
+    pdl_trigger();
     if (MODE == OP_RESIDUAL && a.partials != nullptr) {
         __shared__ double red[NT / 32];
         for (int o = 16; o > 0; o >>= 1) racc += __shfl_down_sync(0xffffffffu, racc, o);

@@ -4,10 +4,12 @@
 // the stream is still running: its CTAs become resident as soon as every CTA
 // of the previous kernel has executed pdl_trigger() (or exited), run their
 // prologue, and block in pdl_wait() until the previous kernel has completed
-// and its memory is visible.  The solver's kernels trigger only after their
-// own wait, so when a kernel starts, the kernel two launches back has
-// completed: its outputs may be read before the kernel's own wait.  Both
-// instructions are no-ops in a kernel launched without the attribute.
+// and its memory is visible.  The solver's kernels trigger at the end of each
+// CTA's main work (triggering at the start let the next kernel's CTAs take SM
+// resources from the running one), after their own wait, so when a kernel
+// starts, the kernel two launches back has completed: its outputs may be read
+// before the kernel's own wait.  Both instructions are no-ops in a kernel
+// launched without the attribute.
 #pragma once
 
 #include <cuda_runtime.h>

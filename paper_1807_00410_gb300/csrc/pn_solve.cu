@@ -756,7 +756,6 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
                                                        double* cs, double* sn, double* g, int j, double* S) {
     constexpr int NV = PN_MAX_MDOT;
     pn::pdl_wait();  // w comes from the operator launched before (programmatic dependent launch)
-    pn::pdl_trigger();
     float part[NV + 1];
 #pragma unroll
     for (int v = 0; v <= NV; ++v) part[v] = 0.0f;
@@ -780,6 +779,7 @@ __global__ void __launch_bounds__(256) k_mdot16_givens(int64_t n8, const uint4* 
         for (int k = 0; k < 8; ++k) t = fmaf(wf[k], wf[k], t);
         part[NV] = t;
     }
+    pn::pdl_trigger();  // the multi-axpy may start during the reduction tail
     mdot16_finish(part, nv, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S);
 }
 
@@ -847,7 +847,6 @@ __global__ void __launch_bounds__(256, MINB) k_mdot16_tma(int64_t n, const __hal
     if (tid == 0)
         for (int k = 0; k < MD_ST && k < nk; ++k) issue_v(blockIdx.x + k * G, k);
     pn::pdl_wait();
-    pn::pdl_trigger();
     if (tid == 0)
         for (int k = 0; k < MD_ST && k < nk; ++k) issue_w(blockIdx.x + k * G, k);
     float part[NV + 1];
@@ -886,6 +885,7 @@ __global__ void __launch_bounds__(256, MINB) k_mdot16_tma(int64_t n, const __hal
         __syncthreads();  // slot st is free again
         if (tid == 0 && kk + MD_ST < nk) issue(c + MD_ST * G, st);
     }
+    pn::pdl_trigger();  // the multi-axpy may start during the reduction tail
     mdot16_finish(part, nv, inv_sigma, partials, ticket, H, ldh, add, cs, sn, g, j, S);
 }
 
@@ -899,7 +899,6 @@ __global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* __res
                                                  uint4* __restrict__ V16_out, float4* __restrict__ vcur) {
     constexpr int NV = PN_MAX_MDOT;
     pn::pdl_wait();  // the projections come from the multi-dot launched before
-    pn::pdl_trigger();
     float cj[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
@@ -951,6 +950,7 @@ __global__ void __launch_bounds__(256) k_maxpy16(int64_t n8, const float4* __res
             vcur[2 * ii + 1] = make_float4(acc[g][4], acc[g][5], acc[g][6], acc[g][7]);
         }
     }
+    pn::pdl_trigger();
 }
 
 // The multi-axpy of k_maxpy16 with its streams (w and the nv basis slices)
@@ -998,7 +998,6 @@ __global__ void __launch_bounds__(256, MINB) k_maxpy16_tma(int64_t n, const floa
     if (tid == 0)
         for (int k = 0; k < MD_ST && k < nk; ++k) issue(blockIdx.x + k * G, k);
     pn::pdl_wait();
-    pn::pdl_trigger();
     float cj[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) cj[v] = v < nv ? -float(add[v]) * inv_sigma : 0.0f;
@@ -1040,6 +1039,7 @@ __global__ void __launch_bounds__(256, MINB) k_maxpy16_tma(int64_t n, const floa
         __syncthreads();  // slot st is free again
         if (tid == 0 && kk + MD_ST < nk) issue(c + MD_ST * G, st);
     }
+    pn::pdl_trigger();
 }
 
 // Launchers of the staged vector kernels: chunk size, slots and blocks per SM.
