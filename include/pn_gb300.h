@@ -330,6 +330,22 @@ int pn_cnn_train_step(pn_cnn* net, const float* in, const float* target, int B, 
                       double* loss_out, void* stream);
 
 /*
+ * Convolution kernel of the network's 3x3x3 layers (forward and input
+ * gradient): PN_CNN_CONV_TCGEN05 (default) runs them on the fifth-generation
+ * tensor cores (tcgen05.mma, BF16 operands staged by TMA, FP32 accumulators
+ * in tensor memory); PN_CNN_CONV_MMA_SYNC on warp-level mma.sync with
+ * fragments loaded from global memory (kept for comparison).  Both compute
+ * the same products in FP32 accumulation (sums in another order).
+ * pn_cnn_take_error: PN_ERR_TIMEOUT (and clears it) if a bounded wait of a
+ * tcgen05 convolution ran out since the last call, else PN_OK; synchronises
+ * the device.  pn_cnn_train_step (with loss_out) reports the same error.
+ */
+#define PN_CNN_CONV_MMA_SYNC 0
+#define PN_CNN_CONV_TCGEN05  1
+int pn_cnn_set_conv_kernel(pn_cnn* net, int kernel);
+int pn_cnn_take_error(pn_cnn* net);
+
+/*
  * *out (host) = sum_i x_i y_i for i < n, without allocating anything.
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory where they need a reduction (a host application that

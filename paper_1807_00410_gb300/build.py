@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["pn_tables.cpp", "pn_api.cu", "pn_kernels.cu", "pn_apply_tiled.cu", "pn_apply_tma.cu", "pn_solve.cu", "pn_source.cu", "pn_cnn_kernels.cu", "pn_cnn.cu", "pn_precond.cu", "pn_noalloc.cu", "pn_batch.cu", "pn_selftest.cu"]
+SOURCES = ["pn_tables.cpp", "pn_api.cu", "pn_kernels.cu", "pn_apply_tiled.cu", "pn_apply_tma.cu", "pn_solve.cu", "pn_source.cu", "pn_cnn_kernels.cu", "pn_cnn_tc.cu", "pn_cnn.cu", "pn_precond.cu", "pn_noalloc.cu", "pn_batch.cu", "pn_selftest.cu"]
 
 
 def nvcc() -> str:

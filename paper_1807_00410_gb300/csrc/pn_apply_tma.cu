@@ -465,6 +465,8 @@ cudaError_t launch_mode(const pn_handle* h, const Maps& m, const Args& a, dim3 g
 
 }  // namespace tma
 
+void* tensor_map_encoder() { return reinterpret_cast<void*>(tma::encode_fn()); }
+
 bool tma_serves(const pn_handle* h) {
     if (!tiled_serves(h) || h->N > 7 || !tma::encode_fn()) return false;
     // the tile geometry is fixed (32 x 4 columns); x must be 16-byte aligned,

@@ -66,7 +66,9 @@ struct pn_cnn {
     size_t act_bytes = 0;
     Buf xin, a0, cat0, d0, yout, p0, a1, cat1, d1, p1, a2, cat2, d2, p2, a3, bt;
     Buf gy, g_d0, g_cat0, g_d1, g_cat1, g_d2, g_cat2, g_bt, g_a3, g_p2, g_a2, g_p1, g_a1, g_p0, g_a0;
-    float* d_loss = nullptr;  // per-sample sums (2 * B floats) and the total
+    float* d_loss = nullptr;  // per-sample sums (2 * B floats) and the total, then the error word
+    unsigned int* d_err = nullptr;  // set by a tcgen05 convolution whose bounded wait ran out (in d_loss's tail)
+    int conv_kernel = PN_CNN_CONV_TCGEN05;
     std::string err;
 };
 
@@ -110,6 +112,8 @@ int conv(pn_cnn* n, const char* name, const Buf& in, int in_co, const Buf& out, 
     a.co = L->cop;
     a.relu = relu ? 1 : 0;
     a.g = grid_at(n, in.level);
+    a.use_tc = n->conv_kernel == PN_CNN_CONV_TCGEN05 ? 1 : 0;
+    a.err = n->d_err;
     CK(pn::cnn::conv3(a, s));
     return PN_OK;
 }
@@ -147,6 +151,8 @@ int conv_back(pn_cnn* n, const char* name, const Buf& in, int in_co, const Buf& 
         a.co = L->cip;
         a.relu = 0;
         a.g = grid_at(n, in.level);
+        a.use_tc = n->conv_kernel == PN_CNN_CONV_TCGEN05 ? 1 : 0;
+        a.err = n->d_err;
         CK(pn::cnn::conv3(a, s));
     }
     return PN_OK;
@@ -430,11 +436,13 @@ int pn_cnn_create(pn_cnn** out, int c_in, int c_out, const int widths[4]) {
         cudaMalloc(&n->d_m, bytes) != cudaSuccess || cudaMalloc(&n->d_v, bytes) != cudaSuccess ||
         cudaMalloc(&n->d_wbf, off * sizeof(bf16)) != cudaSuccess ||
         cudaMalloc(&n->d_wflip, off * sizeof(bf16)) != cudaSuccess ||
-        cudaMalloc(&n->d_loss, 2 * 4096 * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&n->d_loss, (2 * 4096 + 64) * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         pn_cnn_destroy(n);
         return PN_ERR_ALLOC;
     }
+    n->d_err = reinterpret_cast<unsigned int*>(n->d_loss + 2 * 4096 + 32);
+    cudaMemset(n->d_err, 0, sizeof(unsigned int));
     cudaMemset(n->d_w32, 0, bytes);
     cudaMemset(n->d_g, 0, bytes);
     cudaMemset(n->d_m, 0, bytes);
@@ -511,6 +519,23 @@ int pn_cnn_get_grads(pn_cnn* n, float* host, int64_t count) {
     return copy_params(n, host, count, n->d_g, false);
 }
 
+int pn_cnn_set_conv_kernel(pn_cnn* n, int kernel) {
+    if (!n) return PN_ERR_ARG;
+    if (kernel != PN_CNN_CONV_TCGEN05 && kernel != PN_CNN_CONV_MMA_SYNC)
+        return fail(n, PN_ERR_ARG, "pn_cnn_set_conv_kernel: bad kernel");
+    n->conv_kernel = kernel;
+    return PN_OK;
+}
+
+int pn_cnn_take_error(pn_cnn* n) {
+    if (!n) return PN_ERR_ARG;
+    unsigned int e = 0;
+    CK(cudaMemcpy(&e, n->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e == 0) return PN_OK;
+    CK(cudaMemset(n->d_err, 0, sizeof(e)));
+    return fail(n, PN_ERR_TIMEOUT, "pn_cnn: a bounded wait of the tcgen05 convolution ran out");
+}
+
 int pn_cnn_forward(pn_cnn* n, const float* in, float* out, int B, int Z, int Y, int X, void* stream) {
     if (!n || !in) return PN_ERR_ARG;
     int rc = check_dims(n, B, Z, Y, X);
@@ -570,6 +595,8 @@ int pn_cnn_train_step(pn_cnn* n, const float* in, const float* target, int B, in
         std::vector<float> acc(2 * B);
         CK(cudaMemcpyAsync(acc.data(), n->d_loss, 2 * B * sizeof(float), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        rc = pn_cnn_take_error(n);
+        if (rc != PN_OK) return rc;
         double l = 0.0;
         for (int b = 0; b < B; ++b) l += acc[2 * b] / std::max(acc[2 * b + 1], 1e-30f);
         *loss_out = l / B;

@@ -34,6 +34,8 @@ struct ConvArgs {
     int out_cs, out_co, co;
     int relu;
     Grid g;
+    int use_tc = 1;               // 1: the tcgen05 kernel (pn_cnn_tc.cu); 0: the mma.sync kernel
+    unsigned int* err = nullptr;  // error word of the tcgen05 kernel's bounded waits
 };
 
 // dW[tap][co][ci] += sum_v gy[v][o] x[v + t][c]; db[o] += sum_v gy[v][o] (if db).
@@ -59,6 +61,10 @@ struct PoolArgs {
 };
 
 cudaError_t conv3(const ConvArgs& a, cudaStream_t s);
+// the same convolution on the tcgen05 tensor cores (pn_cnn_tc.cu); err: the
+// network's error word (set where a bounded wait ran out)
+bool conv3_tc_serves(const ConvArgs& a);
+cudaError_t conv3_tc(const ConvArgs& a, unsigned int* err, cudaStream_t s);
 cudaError_t conv3_wgrad(const WgradArgs& a, cudaStream_t s);
 cudaError_t flip_weights(const bf16* w, bf16* wt, int co, int ci, cudaStream_t s);
 cudaError_t to_bf16(const float* src, bf16* dst, int64_t n, cudaStream_t s);

@@ -306,7 +306,8 @@ static int grid1d(int64_t n) {
 }
 
 cudaError_t conv3(const ConvArgs& a, cudaStream_t s) {
-    // output-channel chunk of 32 (NT = 4) or 16 (NT = 2)
+    if (a.use_tc && conv3_tc_serves(a)) return conv3_tc(a, a.err, s);
+    // mma.sync: output-channel chunk of 32 (NT = 4) or 16 (NT = 2)
     const int64_t blocks = (a.g.nvox + 127) / 128;
     if (a.co % 32 == 0) k_conv3<4><<<dim3(unsigned(blocks), a.co / 32), 256, 0, s>>>(a);
     else k_conv3<2><<<dim3(unsigned(blocks), a.co / 16), 256, 0, s>>>(a);

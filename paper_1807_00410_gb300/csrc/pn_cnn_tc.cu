@@ -1,0 +1,362 @@
+// 3x3x3 convolution of the learned preconditioner's network on the fifth-
+// generation tensor cores (tcgen05), as an implicit GEMM:
+//
+//     out[v][o] = act(bias[o] + sum_{tap} sum_c in[v + tap][c] w[tap][o][c])
+//
+// M = 128 voxels of one tile (8 x 4 y 4 z of one sample), N = the layer's
+// output channels (16..128, a multiple of 16), K = 27 taps x input channels,
+// walked in steps of 16 channels of one tap.  BF16 operands, FP32
+// accumulation in tensor memory (TMEM).
+//
+//  * Operands reach shared memory by TMA: the activations through a 5D tensor
+//    map (channels, x, y, z, sample) whose box is 8 channels x 8 x 4 x 4
+//    voxels, shifted by the tap's offset, so the copy engine writes the zero
+//    padding of the convolution (coordinates outside the grid read as 0); the
+//    weights [tap][o][c] through a 3D map, a box of 8 channels x N rows.  Two
+//    boxes (channels c..c+7 and c+8..c+15) make one K step of each operand.
+//  * That puts both operands in the canonical K-major layout without swizzle:
+//    core matrices of 8 rows x 16 bytes, rows of one core matrix 16 bytes
+//    apart, the next 8 rows 128 bytes on (stride byte offset), the next 8
+//    channels one box on (leading byte offset).
+//  * One thread issues the copies into a ring of kStages slots and the MMAs
+//    (tcgen05.mma.cta_group::1.kind::f16, 128 x N x 16); each MMA's commit
+//    frees its slot; after the last one the four warps read the accumulator
+//    (tcgen05.ld 32x32b, warp w owns TMEM lanes 32w..32w+31 = voxels of the
+//    tile), add the bias, apply the ReLU and store BF16.
+//  * Every wait is bounded (about 2 s of %globaltimer); one that runs out sets
+//    the network's error word, the kernel waits (bounded) for its copies in
+//    flight and for its MMAs, and still frees its TMEM before it returns.
+//
+// The input gradient of a layer is this kernel on the tap-flipped, transposed
+// weights ([tap][c][o]).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "pn_cnn.h"
+#include "pn_internal.h"
+#include "pn_mbar.cuh"
+
+namespace pn {
+namespace cnn {
+namespace tc {
+
+constexpr int kThreads = 128;
+constexpr int kStages = 6;
+constexpr uint32_t kABox = 2048;    // one 8-channel box of the 128-voxel tile (bytes)
+constexpr uint32_t kSlack = 32768;  // unused shared memory after the ring (see smem_bytes)
+
+// bytes of one ring slot: the activation tile (two boxes) and the weight slice
+// (two boxes of n rows), rounded to 1024
+__host__ __device__ constexpr uint32_t slot_bytes(int n) { return ((2 * kABox + uint32_t(n) * 32u) + 1023u) / 1024u * 1024u; }
+
+// The ring, then kSlack bytes that no access is meant to reach: an MMA
+// descriptor whose two byte offsets were read the other way round would
+// address at most 15 x 2048 + 2 x 128 bytes past a slot (N <= 128), inside
+// this range.
+__host__ __device__ constexpr uint32_t smem_bytes(int n) { return kStages * slot_bytes(n) + kSlack + 1024u; }
+
+struct Args {
+    int ci, co;          // input / output channels of the GEMM (multiples of 16)
+    int in_co;           // first input channel of the slice read
+    int kc;              // ci / 16
+    int ntx, nty, ntz;   // tiles per axis (8, 4, 4 voxels)
+    int X, Y, Z;
+    const float* bias;   // or null
+    bf16* out;
+    int out_cs, out_co;
+    int relu;
+    uint32_t idesc;      // instruction descriptor (kind::f16, BF16 x BF16 -> F32, M = 128, N = co)
+    uint32_t tmem_cols;  // power of two >= max(32, co)
+    unsigned int* err;   // set to 1 where a bounded wait ran out
+};
+
+// ---- PTX wrappers ---------------------------------------------------------------
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset (next
+// core matrix along K), stride byte offset (next 8 rows), descriptor version
+// 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrives on `bar` once every MMA this thread issued before it has completed
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv3_tc(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap wts, Args a) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_slot;
+    unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+    const uint32_t ring_s = mbar::smem_u32(ring);
+    const uint32_t SB = slot_bytes(a.co);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // tile of this CTA: 8 x 4 y 4 z voxels of one sample
+    int t = blockIdx.x;
+    const int tx = t % a.ntx;
+    t /= a.ntx;
+    const int ty = t % a.nty;
+    t /= a.nty;
+    const int tz = t % a.ntz;
+    const int b = t / a.ntz;
+    const int x0 = tx * 8, y0 = ty * 4, z0 = tz * 4;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar::init(mbar::smem_u32(&full[s]), 1u);
+            mbar::init(mbar::smem_u32(&empty[s]), 1u);
+        }
+        mbar::init(mbar::smem_u32(&done), 1u);
+        mbar::fence_init();
+    }
+    if (warp == 0) {
+        // the accumulator: 128 lanes x tmem_cols FP32 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         mbar::smem_u32(&tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    const int steps = 27 * a.kc;
+    const uint32_t tx_bytes = 2 * kABox + uint32_t(a.co) * 32u;
+    bool failed = false;
+    if (threadIdx.x == 0) {
+        auto issue = [&](int k) {
+            const int slot = k % kStages;
+            const int tap = k / a.kc, kk = k - tap * a.kc;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            const uint32_t bar = mbar::smem_u32(&full[slot]);
+            const uint32_t sa = ring_s + uint32_t(slot) * SB;
+            const uint32_t sb = sa + 2 * kABox;
+            const int c = a.in_co + kk * 16;
+            mbar::arrive_expect_tx(bar, tx_bytes);
+            tma_load_5d(sa, &act, c, x0 + dx, y0 + dy, z0 + dz, b, bar);
+            tma_load_5d(sa + kABox, &act, c + 8, x0 + dx, y0 + dy, z0 + dz, b, bar);
+            tma_load_3d(sb, &wts, kk * 16, 0, tap, bar);
+            tma_load_3d(sb + uint32_t(a.co) * 16u, &wts, kk * 16 + 8, 0, tap, bar);
+        };
+        const int pro = steps < kStages ? steps : kStages;
+        int issued = 0;    // steps whose copies went out
+        int consumed = 0;  // steps whose copies were waited for
+        for (int k = 0; k < pro; ++k, ++issued) issue(k);
+        for (int k = 0; k < steps && !failed; ++k) {
+            const int slot = k % kStages;
+            mbar::wait(mbar::smem_u32(&full[slot]), uint32_t(k / kStages) & 1u, a.err, failed);
+            if (failed) break;
+            consumed = k + 1;
+            fence_after_sync();
+            const uint32_t sa = ring_s + uint32_t(slot) * SB;
+            const uint64_t ad = smem_desc(sa, kABox, 128u);
+            const uint64_t bd = smem_desc(sa + 2 * kABox, uint32_t(a.co) * 16u, 128u);
+            mma_bf16(tmem, ad, bd, a.idesc, k > 0 ? 1u : 0u);
+            mma_commit(mbar::smem_u32(&empty[slot]));
+            // refill the previous step's slot with the step kStages after it
+            const int kp = k - 1, kn = kp + kStages;
+            if (kp >= 0 && kn < steps) {
+                mbar::wait(mbar::smem_u32(&empty[kp % kStages]), uint32_t(kp / kStages) & 1u, a.err, failed);
+                if (!failed) {
+                    issue(kn);
+                    ++issued;
+                }
+            }
+        }
+        // every MMA issued has completed once `done` flips
+        mma_commit(mbar::smem_u32(&done));
+        if (failed) {
+            // wait (bounded) for the copies still in flight: steps [consumed, issued)
+            bool f2 = false;
+            for (int k = consumed; k < issued; ++k)
+                mbar::wait(mbar::smem_u32(&full[k % kStages]), uint32_t(k / kStages) & 1u, a.err, f2);
+        }
+    }
+    __syncwarp();
+    // the accumulator is complete (or the kernel gave up: the error word is set)
+    {
+        bool f3 = false;
+        mbar::wait(mbar::smem_u32(&done), 0u, a.err, f3);
+    }
+    fence_after_sync();
+
+    // epilogue: warp w holds voxels 32w..32w+31 of the tile (TMEM lanes)
+    const int m = warp * 32 + lane;
+    const int vx = x0 + (m & 7), vy = y0 + ((m >> 3) & 3), vz = z0 + (m >> 5);
+    const bool ok = vx < a.X && vy < a.Y && vz < a.Z;
+    const int64_t v = ((int64_t(b) * a.Z + vz) * a.Y + vy) * a.X + vx;
+    bf16* op = a.out + v * a.out_cs + a.out_co;
+    for (int c0 = 0; c0 < a.co; c0 += 16) {
+        float r[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float lo = r[2 * i], hi = r[2 * i + 1];
+            if (a.bias) {
+                lo += a.bias[c0 + 2 * i];
+                hi += a.bias[c0 + 2 * i + 1];
+            }
+            if (a.relu) {
+                lo = fmaxf(lo, 0.0f);
+                hi = fmaxf(hi, 0.0f);
+            }
+            pk[i] = pack_bf16x2(lo, hi);
+        }
+        if (ok) {
+            uint4* dst = reinterpret_cast<uint4*>(op + c0);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    }
+}
+
+// ---- host ------------------------------------------------------------------------
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+}  // namespace tc
+
+bool conv3_tc_serves(const ConvArgs& a) {
+    return tensor_map_encoder() != nullptr && a.ci % 16 == 0 && a.co % 16 == 0 && a.co >= 16 && a.co <= 128 &&
+           a.co_total == a.co && a.in_cs % 8 == 0 && a.in_co % 8 == 0 && a.out_cs % 8 == 0 && a.out_co % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(a.in) & 15u) == 0 && (reinterpret_cast<uintptr_t>(a.w) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0 && a.g.nvox > 0;
+}
+
+cudaError_t conv3_tc(const ConvArgs& a, unsigned int* err, cudaStream_t s) {
+    const tc::EncodeTiled enc = reinterpret_cast<tc::EncodeTiled>(tensor_map_encoder());
+    if (!enc || !conv3_tc_serves(a)) return cudaErrorNotSupported;
+    CUtensorMap act, wts;
+    std::memset(&act, 0, sizeof(act));
+    std::memset(&wts, 0, sizeof(wts));
+    {
+        const cuuint64_t dim[5] = {cuuint64_t(a.in_cs), cuuint64_t(a.g.X), cuuint64_t(a.g.Y), cuuint64_t(a.g.Z),
+                                   cuuint64_t(a.g.B)};
+        const cuuint64_t row = cuuint64_t(a.in_cs) * 2;
+        const cuuint64_t str[4] = {row, row * a.g.X, row * a.g.X * a.g.Y, row * a.g.X * a.g.Y * a.g.Z};
+        const cuuint32_t box[5] = {8u, 8u, 4u, 4u, 1u};
+        const cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
+        if (enc(&act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(a.in), dim, str, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dim[3] = {cuuint64_t(a.ci), cuuint64_t(a.co), 27};
+        const cuuint64_t str[2] = {cuuint64_t(a.ci) * 2, cuuint64_t(a.ci) * 2 * a.co};
+        const cuuint32_t box[3] = {8u, cuuint32_t(a.co), 1u};
+        const cuuint32_t es[3] = {1u, 1u, 1u};
+        if (enc(&wts, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(a.w), dim, str, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    tc::Args p{};
+    p.ci = a.ci;
+    p.co = a.co;
+    p.in_co = a.in_co;
+    p.kc = a.ci / 16;
+    p.ntx = (a.g.X + 7) / 8;
+    p.nty = (a.g.Y + 3) / 4;
+    p.ntz = (a.g.Z + 3) / 4;
+    p.X = a.g.X;
+    p.Y = a.g.Y;
+    p.Z = a.g.Z;
+    p.bias = a.bias;
+    p.out = a.out;
+    p.out_cs = a.out_cs;
+    p.out_co = a.out_co;
+    p.relu = a.relu;
+    // kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16
+    // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+    // 17, M >> 4 at bit 24
+    p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(a.co >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+    uint32_t cols = 32;
+    while (cols < uint32_t(a.co)) cols <<= 1;
+    p.tmem_cols = cols;
+    p.err = err;
+    const int64_t tiles = int64_t(p.ntx) * p.nty * p.ntz * a.g.B;
+    if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    const uint32_t smem = tc::smem_bytes(a.co);
+    static std::atomic<unsigned long long> configured{0};
+    cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(tc::k_conv3_tc),
+                                      int(tc::smem_bytes(128)));
+    if (e != cudaSuccess) return e;
+    tc::k_conv3_tc<<<unsigned(tiles), tc::kThreads, smem, s>>>(act, wts, p);
+    return cudaGetLastError();
+}
+
+}  // namespace cnn
+}  // namespace pn

@@ -154,6 +154,9 @@ int op_partial_count(const pn_handle* h, int dtype);
 // Kernels one launch_op makes (the tiled operator: tiled + face-column kernel).
 int op_launch_count(const pn_handle* h, int dtype);
 
+// The driver's cuTensorMapEncodeTiled (pn_apply_tma.cu), or null.
+void* tensor_map_encoder();
+
 // Tiled FP32 operator (pn_apply_tiled.cu): covers x < tiled_x_end(h) of every
 // plane box; one FP64 residual partial per CTA.
 cudaError_t launch_tiled(const pn_handle* h, int mode, const float* x, float* y, const float* bvec,

@@ -51,7 +51,8 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_batch_tune", "pn_batch_set_mode", "pn_batch_barrier_test", "pn_tune_apply",
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
            "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels",
-           "pn_get_workspace", "pn_wait_timeout_test", "pn_set_pdl"]
+           "pn_get_workspace", "pn_wait_timeout_test", "pn_set_pdl", "pn_cnn_set_conv_kernel",
+           "pn_cnn_take_error"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -149,6 +150,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_set_l2_residency": (i, [vp, i]),
         "pn_set_stream_kernels": (i, [vp, i]),
         "pn_set_pdl": (i, [vp, i]),
+        "pn_cnn_set_conv_kernel": (i, [vp, i]),
+        "pn_cnn_take_error": (i, [vp]),
         "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
@@ -763,6 +766,16 @@ class Net:
         a = np.empty(self.n_params, dtype=np.float32)
         self._check(self._lib.pn_cnn_get_grads(self._h, ctypes.c_void_p(a.ctypes.data), a.size))
         return a
+
+    CONV_KERNELS = {"mma_sync": 0, "tcgen05": 1}
+
+    def set_conv_kernel(self, kernel: str):
+        """Kernel of the 3x3x3 convolutions: "tcgen05" (default) or "mma_sync"."""
+        self._check(self._lib.pn_cnn_set_conv_kernel(self._h, self.CONV_KERNELS[kernel]))
+
+    def take_error(self):
+        """Raise if a bounded wait of a tcgen05 convolution ran out (clears it)."""
+        self._check(self._lib.pn_cnn_take_error(self._h))
 
     def forward(self, x, stream=None):
         torch = _torch()

@@ -206,3 +206,29 @@ def test_ir_fgmres_with_untrained_network_meets_oracle_residual():
     assert opn.relative_residual(S.A, S.b, S.layout.join(gpu.to_planes(u))) <= 1.0001e-6
     net.close()
     gpu.close()
+
+
+@pytest.mark.parametrize("R,B", [(8, 1), (16, 2), (32, 1)])
+def test_tcgen05_and_mma_sync_convolutions_agree(R, B):
+    """The tcgen05 implicit-GEMM convolution (TMA-staged operands, FP32
+    accumulators in tensor memory) and the mma.sync one compute the same
+    network: forward outputs and every parameter gradient agree to the BF16
+    storage of the activations (relative L2 <= 1e-2), and no bounded wait of
+    the tcgen05 kernel ran out.  R = 8 puts the coarsest level at one voxel
+    per sample, so most of each 8 x 4 x 4 tile lies outside the grid."""
+    widths = (16, 32, 48, 64)
+    pn, params, x, net = _setup(widths, 19, 16, R, B, 11)
+    xt = torch.tensor(np.moveaxis(x, 1, -1), dtype=torch.float32).cuda()
+    g = torch.Generator(device="cpu").manual_seed(2)
+    gout = torch.randn(tuple(xt.shape[:-1]) + (16,), generator=g).cuda()
+    outs, grads = [], []
+    for kernel in ("tcgen05", "mma_sync"):
+        net.set_conv_kernel(kernel)
+        outs.append(net.forward(xt).cpu().double().numpy())
+        net.backward(gout)
+        grads.append(net.get_grads().astype(np.float64))
+    net.take_error()
+    assert _rel(outs[0], outs[1]) < 1e-2
+    assert _rel(grads[0], grads[1]) < 1e-2
+    assert np.abs(outs[0]).max() > 0
+    net.close()
