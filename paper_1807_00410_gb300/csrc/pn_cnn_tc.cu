@@ -3,26 +3,29 @@
 //
 //     out[v][o] = act(bias[o] + sum_{tap} sum_c in[v + tap][c] w[tap][o][c])
 //
-// M = 128 voxels of one tile (8 x 4 y 4 z of one sample), N = the layer's
-// output channels (16..128, a multiple of 16), K = 27 taps x input channels,
-// walked in steps of 16 channels of one tap.  BF16 operands, FP32
-// accumulation in tensor memory (TMEM).
+// M = 128 voxels of one tile (8 x 16 y 1 z of one sample), N = n <= 64 output
+// channels (the host splits wider layers into launches of at most 64), K = 27
+// taps x input channels.  BF16 operands, FP32 accumulation in tensor memory
+// (TMEM).
 //
-//  * Operands reach shared memory by TMA: the activations through a 5D tensor
-//    map (channels, x, y, z, sample) whose box is 8 channels x 8 x 4 x 4
-//    voxels, shifted by the tap's offset, so the copy engine writes the zero
-//    padding of the convolution (coordinates outside the grid read as 0); the
-//    weights [tap][o][c] through a 3D map, a box of 8 channels x N rows.  Two
-//    boxes (channels c..c+7 and c+8..c+15) make one K step of each operand.
-//  * That puts both operands in the canonical K-major layout without swizzle:
-//    core matrices of 8 rows x 16 bytes, rows of one core matrix 16 bytes
-//    apart, the next 8 rows 128 bytes on (stride byte offset), the next 8
-//    channels one box on (leading byte offset).
-//  * One thread issues the copies into a ring of kStages slots and the MMAs
-//    (tcgen05.mma.cta_group::1.kind::f16, 128 x N x 16); each MMA's commit
-//    frees its slot; after the last one the four warps read the accumulator
-//    (tcgen05.ld 32x32b, warp w owns TMEM lanes 32w..32w+31 = voxels of the
-//    tile), add the bias, apply the ReLU and store BF16.
+//  * The tile's input, with its one-voxel halo, reaches shared memory by TMA
+//    once per 16-channel block: two boxes (channels c..c+7 and c+8..c+15) of
+//    10 x 18 x 3 voxels from a 5D tensor map (channels, x, y, z, sample); the
+//    copy engine writes 0 for coordinates outside the grid (the convolution's
+//    zero padding).  The weights of all 27 taps for the block come with it:
+//    two boxes of 8 channels x n rows x 27 taps ([tap][o][c]).
+//  * Both operands are then in the canonical K-major layout without swizzle
+//    (core matrices of 8 rows x 16 bytes): for tap (dx, dy, dz) the A operand
+//    is the block shifted by (dx, dy, dz) -- rows x = 0..7 of one tile row are
+//    8 consecutive 16-byte rows of the block, the next tile row 10 rows (160
+//    bytes) on (stride byte offset), the second 8 channels one box on (leading
+//    byte offset) -- so one block serves the 27 MMAs of the 16-channel step
+//    (tcgen05.mma.cta_group::1.kind::f16, 128 x n x 16).
+//  * One thread issues the copies into a ring of slots (one 16-channel block
+//    each) and the MMAs; each block's commit frees its slot; after the last
+//    one the four warps read the accumulator (tcgen05.ld 32x32b, warp w owns
+//    TMEM lanes 32w..32w+31 = voxels of the tile), add the bias, apply the ReLU
+//    and store BF16.
 //  * Every wait is bounded (about 2 s of %globaltimer); one that runs out sets
 //    the network's error word, the kernel waits (bounded) for its copies in
 //    flight and for its MMAs, and still frees its TMEM before it returns.
@@ -33,6 +36,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -45,32 +49,31 @@ namespace cnn {
 namespace tc {
 
 constexpr int kThreads = 128;
-constexpr int kStages = 6;
-constexpr uint32_t kABox = 2048;    // one 8-channel box of the 128-voxel tile (bytes)
-constexpr uint32_t kSlack = 32768;  // unused shared memory after the ring (see smem_bytes)
+constexpr int kMaxN = 64;                 // output channels per launch
+constexpr int HX = 10, HY = 18, HZ = 3;   // halo'd input block (voxels)
+constexpr uint32_t kABytes = 8u * HX * HY * HZ * 2u;  // one 8-channel box: 8640
+constexpr uint32_t kASlot = 8704;         // its slot (128-byte multiple)
 
-// bytes of one ring slot: the activation tile (two boxes) and the weight slice
-// (two boxes of n rows), rounded to 1024
-__host__ __device__ constexpr uint32_t slot_bytes(int n) { return ((2 * kABox + uint32_t(n) * 32u) + 1023u) / 1024u * 1024u; }
-
-// The ring, then kSlack bytes that no access is meant to reach: an MMA
-// descriptor whose two byte offsets were read the other way round would
-// address at most 15 x 2048 + 2 x 128 bytes past a slot (N <= 128), inside
-// this range.
-__host__ __device__ constexpr uint32_t smem_bytes(int n) { return kStages * slot_bytes(n) + kSlack + 1024u; }
+// bytes of one ring slot for n output channels: two input boxes and two
+// weight boxes (27 taps x n rows x 8 channels each), rounded to 1024
+__host__ __device__ constexpr uint32_t wbox_bytes(int n) { return 27u * uint32_t(n) * 16u; }
+__host__ __device__ constexpr uint32_t slot_bytes(int n) { return (2 * kASlot + 2 * wbox_bytes(n) + 1023u) / 1024u * 1024u; }
+__host__ __device__ constexpr int stages_for(int n) { return n <= 32 ? 3 : 2; }
+__host__ __device__ constexpr uint32_t smem_bytes(int n) { return uint32_t(stages_for(n)) * slot_bytes(n) + 1024u; }
 
 struct Args {
-    int ci, co;          // input / output channels of the GEMM (multiples of 16)
+    int n;               // output channels of this launch (16..64, a multiple of 16)
     int in_co;           // first input channel of the slice read
-    int kc;              // ci / 16
-    int ntx, nty, ntz;   // tiles per axis (8, 4, 4 voxels)
+    int kc;              // input channels / 16
+    int o0;              // first output channel (row of the weights, offset of bias and output)
+    int ntx, nty;        // tiles per axis (8 x, 16 y; one z slice per tile)
     int X, Y, Z;
     const float* bias;   // or null
     bf16* out;
     int out_cs, out_co;
     int relu;
-    uint32_t idesc;      // instruction descriptor (kind::f16, BF16 x BF16 -> F32, M = 128, N = co)
-    uint32_t tmem_cols;  // power of two >= max(32, co)
+    uint32_t idesc;      // instruction descriptor (kind::f16, BF16 x BF16 -> F32, M = 128, N = n)
+    uint32_t tmem_cols;  // power of two >= max(32, n)
     unsigned int* err;   // set to 1 where a bounded wait ran out
 };
 
@@ -145,25 +148,28 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv3_tc(const __grid_constant__ CUtensorMap act, const __grid_constant__ CUtensorMap wts, Args a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    constexpr int kMaxStages = 3;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], done;
     __shared__ uint32_t tmem_slot;
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
     const uint32_t ring_s = mbar::smem_u32(ring);
-    const uint32_t SB = slot_bytes(a.co);
+    const uint32_t SB = slot_bytes(a.n);
+    const int S = stages_for(a.n);
+    const uint32_t WB = wbox_bytes(a.n);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // tile of this CTA: 8 x 4 y 4 z voxels of one sample
+    // tile of this CTA: 8 x 16 y voxels of one z slice of one sample
     int t = blockIdx.x;
     const int tx = t % a.ntx;
     t /= a.ntx;
     const int ty = t % a.nty;
     t /= a.nty;
-    const int tz = t % a.ntz;
-    const int b = t / a.ntz;
-    const int x0 = tx * 8, y0 = ty * 4, z0 = tz * 4;
+    const int z0 = t % a.Z;
+    const int b = t / a.Z;
+    const int x0 = tx * 8, y0 = ty * 16;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar::init(mbar::smem_u32(&full[s]), 1u);
             mbar::init(mbar::smem_u32(&empty[s]), 1u);
         }
@@ -183,43 +189,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    const int steps = 27 * a.kc;
-    const uint32_t tx_bytes = 2 * kABox + uint32_t(a.co) * 32u;
+    const int steps = a.kc;  // 16-channel blocks
+    const uint32_t tx_bytes = 2 * kABytes + 2 * WB;
     bool failed = false;
     if (threadIdx.x == 0) {
         auto issue = [&](int k) {
-            const int slot = k % kStages;
-            const int tap = k / a.kc, kk = k - tap * a.kc;
-            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            const int slot = k % S;
             const uint32_t bar = mbar::smem_u32(&full[slot]);
             const uint32_t sa = ring_s + uint32_t(slot) * SB;
-            const uint32_t sb = sa + 2 * kABox;
-            const int c = a.in_co + kk * 16;
+            const uint32_t sb = sa + 2 * kASlot;
+            const int c = a.in_co + k * 16;
             mbar::arrive_expect_tx(bar, tx_bytes);
-            tma_load_5d(sa, &act, c, x0 + dx, y0 + dy, z0 + dz, b, bar);
-            tma_load_5d(sa + kABox, &act, c + 8, x0 + dx, y0 + dy, z0 + dz, b, bar);
-            tma_load_3d(sb, &wts, kk * 16, 0, tap, bar);
-            tma_load_3d(sb + uint32_t(a.co) * 16u, &wts, kk * 16 + 8, 0, tap, bar);
+            tma_load_5d(sa, &act, c, x0 - 1, y0 - 1, z0 - 1, b, bar);
+            tma_load_5d(sa + kASlot, &act, c + 8, x0 - 1, y0 - 1, z0 - 1, b, bar);
+            tma_load_3d(sb, &wts, k * 16, a.o0, 0, bar);
+            tma_load_3d(sb + WB, &wts, k * 16 + 8, a.o0, 0, bar);
         };
-        const int pro = steps < kStages ? steps : kStages;
-        int issued = 0;    // steps whose copies went out
-        int consumed = 0;  // steps whose copies were waited for
+        const int pro = steps < S ? steps : S;
+        int issued = 0;    // blocks whose copies went out
+        int consumed = 0;  // blocks whose copies were waited for
         for (int k = 0; k < pro; ++k, ++issued) issue(k);
         for (int k = 0; k < steps && !failed; ++k) {
-            const int slot = k % kStages;
-            mbar::wait(mbar::smem_u32(&full[slot]), uint32_t(k / kStages) & 1u, a.err, failed);
+            const int slot = k % S;
+            mbar::wait(mbar::smem_u32(&full[slot]), uint32_t(k / S) & 1u, a.err, failed);
             if (failed) break;
             consumed = k + 1;
             fence_after_sync();
             const uint32_t sa = ring_s + uint32_t(slot) * SB;
-            const uint64_t ad = smem_desc(sa, kABox, 128u);
-            const uint64_t bd = smem_desc(sa + 2 * kABox, uint32_t(a.co) * 16u, 128u);
-            mma_bf16(tmem, ad, bd, a.idesc, k > 0 ? 1u : 0u);
+            const uint32_t sb = sa + 2 * kASlot;
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // 0..2: offset + 1
+                const uint32_t a0 = sa + uint32_t((dz * HY + dy) * HX + dx) * 16u;
+                const uint64_t ad = smem_desc(a0, kASlot, uint32_t(HX) * 16u);
+                const uint64_t bd = smem_desc(sb + uint32_t(tap) * uint32_t(a.n) * 16u, WB, 128u);
+                mma_bf16(tmem, ad, bd, a.idesc, (k > 0 || tap > 0) ? 1u : 0u);
+            }
             mma_commit(mbar::smem_u32(&empty[slot]));
-            // refill the previous step's slot with the step kStages after it
-            const int kp = k - 1, kn = kp + kStages;
+            // refill the previous block's slot with the block S after it
+            const int kp = k - 1, kn = kp + S;
             if (kp >= 0 && kn < steps) {
-                mbar::wait(mbar::smem_u32(&empty[kp % kStages]), uint32_t(kp / kStages) & 1u, a.err, failed);
+                mbar::wait(mbar::smem_u32(&empty[kp % S]), uint32_t(kp / S) & 1u, a.err, failed);
                 if (!failed) {
                     issue(kn);
                     ++issued;
@@ -229,10 +238,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // every MMA issued has completed once `done` flips
         mma_commit(mbar::smem_u32(&done));
         if (failed) {
-            // wait (bounded) for the copies still in flight: steps [consumed, issued)
+            // wait (bounded) for the copies still in flight: blocks [consumed, issued)
             bool f2 = false;
             for (int k = consumed; k < issued; ++k)
-                mbar::wait(mbar::smem_u32(&full[k % kStages]), uint32_t(k / kStages) & 1u, a.err, f2);
+                mbar::wait(mbar::smem_u32(&full[k % S]), uint32_t(k / S) & 1u, a.err, f2);
         }
     }
     __syncwarp();
@@ -245,20 +254,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // epilogue: warp w holds voxels 32w..32w+31 of the tile (TMEM lanes)
     const int m = warp * 32 + lane;
-    const int vx = x0 + (m & 7), vy = y0 + ((m >> 3) & 3), vz = z0 + (m >> 5);
-    const bool ok = vx < a.X && vy < a.Y && vz < a.Z;
-    const int64_t v = ((int64_t(b) * a.Z + vz) * a.Y + vy) * a.X + vx;
-    bf16* op = a.out + v * a.out_cs + a.out_co;
-    for (int c0 = 0; c0 < a.co; c0 += 16) {
+    const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
+    const bool ok = vx < a.X && vy < a.Y;
+    const int64_t v = ((int64_t(b) * a.Z + z0) * a.Y + vy) * a.X + vx;
+    bf16* op = a.out + v * a.out_cs + a.out_co + a.o0;
+    const float* bias = a.bias ? a.bias + a.o0 : nullptr;
+    for (int c0 = 0; c0 < a.n; c0 += 16) {
         float r[16];
         tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
         uint32_t pk[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float lo = r[2 * i], hi = r[2 * i + 1];
-            if (a.bias) {
-                lo += a.bias[c0 + 2 * i];
-                hi += a.bias[c0 + 2 * i + 1];
+            if (bias) {
+                lo += bias[c0 + 2 * i];
+                hi += bias[c0 + 2 * i + 1];
             }
             if (a.relu) {
                 lo = fmaxf(lo, 0.0f);
@@ -289,7 +299,7 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 }  // namespace tc
 
 bool conv3_tc_serves(const ConvArgs& a) {
-    return tensor_map_encoder() != nullptr && a.ci % 16 == 0 && a.co % 16 == 0 && a.co >= 16 && a.co <= 128 &&
+    return tensor_map_encoder() != nullptr && a.ci % 16 == 0 && a.co % 16 == 0 && a.co >= 16 && a.co <= 256 &&
            a.co_total == a.co && a.in_cs % 8 == 0 && a.in_co % 8 == 0 && a.out_cs % 8 == 0 && a.out_co % 8 == 0 &&
            (reinterpret_cast<uintptr_t>(a.in) & 15u) == 0 && (reinterpret_cast<uintptr_t>(a.w) & 15u) == 0 &&
            (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0 && a.g.nvox > 0;
@@ -298,64 +308,69 @@ bool conv3_tc_serves(const ConvArgs& a) {
 cudaError_t conv3_tc(const ConvArgs& a, unsigned int* err, cudaStream_t s) {
     const tc::EncodeTiled enc = reinterpret_cast<tc::EncodeTiled>(tensor_map_encoder());
     if (!enc || !conv3_tc_serves(a)) return cudaErrorNotSupported;
-    CUtensorMap act, wts;
+    CUtensorMap act;
     std::memset(&act, 0, sizeof(act));
-    std::memset(&wts, 0, sizeof(wts));
     {
         const cuuint64_t dim[5] = {cuuint64_t(a.in_cs), cuuint64_t(a.g.X), cuuint64_t(a.g.Y), cuuint64_t(a.g.Z),
                                    cuuint64_t(a.g.B)};
         const cuuint64_t row = cuuint64_t(a.in_cs) * 2;
         const cuuint64_t str[4] = {row, row * a.g.X, row * a.g.X * a.g.Y, row * a.g.X * a.g.Y * a.g.Z};
-        const cuuint32_t box[5] = {8u, 8u, 4u, 4u, 1u};
+        const cuuint32_t box[5] = {8u, cuuint32_t(tc::HX), cuuint32_t(tc::HY), cuuint32_t(tc::HZ), 1u};
         const cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
         if (enc(&act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(a.in), dim, str, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    {
+    static std::atomic<unsigned long long> configured{0};
+    uint32_t smem_max = 0;
+    for (int n = 16; n <= tc::kMaxN; n += 16) smem_max = std::max(smem_max, tc::smem_bytes(n));
+    cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(tc::k_conv3_tc), int(smem_max));
+    if (e != cudaSuccess) return e;
+    const int ntx = (a.g.X + 7) / 8, nty = (a.g.Y + 15) / 16;
+    const int64_t tiles = int64_t(ntx) * nty * a.g.Z * a.g.B;
+    if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    // output channels in launches of at most 64 (the accumulator's width)
+    for (int o0 = 0; o0 < a.co; o0 += tc::kMaxN) {
+        const int n = std::min(tc::kMaxN, a.co - o0);
+        CUtensorMap wts;
+        std::memset(&wts, 0, sizeof(wts));
         const cuuint64_t dim[3] = {cuuint64_t(a.ci), cuuint64_t(a.co), 27};
         const cuuint64_t str[2] = {cuuint64_t(a.ci) * 2, cuuint64_t(a.ci) * 2 * a.co};
-        const cuuint32_t box[3] = {8u, cuuint32_t(a.co), 1u};
+        const cuuint32_t box[3] = {8u, cuuint32_t(n), 27u};
         const cuuint32_t es[3] = {1u, 1u, 1u};
         if (enc(&wts, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(a.w), dim, str, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
+        tc::Args p{};
+        p.n = n;
+        p.in_co = a.in_co;
+        p.kc = a.ci / 16;
+        p.o0 = o0;
+        p.ntx = ntx;
+        p.nty = nty;
+        p.X = a.g.X;
+        p.Y = a.g.Y;
+        p.Z = a.g.Z;
+        p.bias = a.bias;
+        p.out = a.out;
+        p.out_cs = a.out_cs;
+        p.out_co = a.out_co;
+        p.relu = a.relu;
+        // kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16
+        // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+        // 17, M >> 4 at bit 24
+        p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+        uint32_t cols = 32;
+        while (cols < uint32_t(n)) cols <<= 1;
+        p.tmem_cols = cols;
+        p.err = err;
+        tc::k_conv3_tc<<<unsigned(tiles), tc::kThreads, tc::smem_bytes(n), s>>>(act, wts, p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    tc::Args p{};
-    p.ci = a.ci;
-    p.co = a.co;
-    p.in_co = a.in_co;
-    p.kc = a.ci / 16;
-    p.ntx = (a.g.X + 7) / 8;
-    p.nty = (a.g.Y + 3) / 4;
-    p.ntz = (a.g.Z + 3) / 4;
-    p.X = a.g.X;
-    p.Y = a.g.Y;
-    p.Z = a.g.Z;
-    p.bias = a.bias;
-    p.out = a.out;
-    p.out_cs = a.out_cs;
-    p.out_co = a.out_co;
-    p.relu = a.relu;
-    // kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16
-    // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
-    // 17, M >> 4 at bit 24
-    p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(a.co >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-    uint32_t cols = 32;
-    while (cols < uint32_t(a.co)) cols <<= 1;
-    p.tmem_cols = cols;
-    p.err = err;
-    const int64_t tiles = int64_t(p.ntx) * p.nty * p.ntz * a.g.B;
-    if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
-    const uint32_t smem = tc::smem_bytes(a.co);
-    static std::atomic<unsigned long long> configured{0};
-    cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(tc::k_conv3_tc),
-                                      int(tc::smem_bytes(128)));
-    if (e != cudaSuccess) return e;
-    tc::k_conv3_tc<<<unsigned(tiles), tc::kThreads, smem, s>>>(act, wts, p);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace cnn

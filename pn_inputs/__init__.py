@@ -140,6 +140,20 @@ def p7_256_cloud(seed: int = 0, R: int = 256) -> Problem:
     return cloud_point(7, R, seed, 100.0, 0.99, 0.6, 0.1)
 
 
+def p7_256_cloud_beam(seed: int = 0, R: int = 256):
+    """The P7 256^3 cloud of p7_256_cloud lit by a collimated beam instead of a
+    point source: (problem, beam) with beam = (axis, sign, radius, centre), the
+    axis and direction seeded, radius 0.1, the line through a seeded point of
+    the middle of the entry face (the source moments are built from it by the
+    single-scatter source builder)."""
+    p = cloud_point(7, R, seed, 100.0, 0.99, 0.6, 0.1)
+    rng = np.random.Generator(np.random.PCG64(seed + 31337))
+    axis = int(rng.integers(3))
+    sign = int(rng.choice([-1, 1]))
+    centre = tuple(float(c) for c in rng.uniform(0.35, 0.65, size=2))
+    return p, (axis, sign, 0.1, centre)
+
+
 def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """Uniform random values (test vectors)."""
     rng = np.random.Generator(np.random.PCG64(seed))
