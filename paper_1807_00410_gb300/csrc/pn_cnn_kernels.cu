@@ -210,69 +210,96 @@ __global__ void k_to_bf16(const float* src, bf16* dst, int64_t n) {
         dst[i] = __float2bfloat16_rn(src[i]);
 }
 
-// out[v][c] = mean of the 2x2x2 block (channel slices), grid of the input
-__global__ void k_pool2(PoolArgs a) {
-    const int64_t n = a.g_out.nvox * a.c;
+// The resampling and ReLU kernels move 8 channels (16 bytes) per thread:
+// every channel count and slice offset of the network is a multiple of 16.
+__device__ __forceinline__ void bf8_to_f(const uint4 u, float (&f)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __bfloat1622float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 f_to_bf8(const float (&f)[8]) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    return u;
+}
+
+__device__ __forceinline__ const uint4* at8(const bf16* base, int64_t v, int cs, int co, int c8) {
+    return reinterpret_cast<const uint4*>(base + v * cs + co + 8 * c8);
+}
+
+// fine voxel index of child q (0..7) of coarse voxel o
+__device__ __forceinline__ int64_t child(const Vox& o, int q, const Grid& gi) {
+    return ((int64_t(o.b) * gi.Z + 2 * o.z + (q >> 2)) * gi.Y + 2 * o.y + ((q >> 1) & 1)) * gi.X + 2 * o.x + (q & 1);
+}
+
+// out[v][c] = scale * sum of the 2x2x2 block of the input grid (channel
+// slices); accumulate adds to out.  scale 1/8: mean pooling; 1: the backward
+// of nearest upsampling.
+__global__ void k_pool2(PoolArgs a, float scale) {
+    const int g8 = a.c / 8;
+    const int64_t n = a.g_out.nvox * g8;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const int c = int(i % a.c);
-        const Vox o = vox_of(i / a.c, a.g_out);
-        float s = 0.0f;
+        const int c8 = int(i % g8);
+        const int64_t vo = i / g8;
+        const Vox o = vox_of(vo, a.g_out);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int64_t vi =
-                ((int64_t(o.b) * a.g_in.Z + 2 * o.z + (q >> 2)) * a.g_in.Y + 2 * o.y + ((q >> 1) & 1)) * a.g_in.X +
-                2 * o.x + (q & 1);
-            s += __bfloat162float(a.in[vi * a.in_cs + a.in_co + c]);
+            float f[8];
+            bf8_to_f(*at8(a.in, child(o, q, a.g_in), a.in_cs, a.in_co, c8), f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k] += f[k];
         }
-        const int64_t vo = i / a.c;
-        const float r = s * 0.125f;
-        if (a.accumulate) {
-            bf16* p = a.out + vo * a.out_cs + a.out_co + c;
-            *p = __float2bfloat16_rn(__bfloat162float(*p) + r);
-        } else {
-            a.out[vo * a.out_cs + a.out_co + c] = __float2bfloat16_rn(r);
-        }
+        uint4* dst = reinterpret_cast<uint4*>(a.out + vo * a.out_cs + a.out_co + 8 * c8);
+        float r[8];
+        if (a.accumulate) bf8_to_f(*dst, r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = (a.accumulate ? r[k] : 0.0f) + s[k] * scale;
+        *dst = f_to_bf8(r);
     }
 }
 
 // Backward of pooling / forward of nearest upsampling: out[v] (fine grid) =
 // scale * in[parent(v)]; accumulate adds to out.
 __global__ void k_up2(PoolArgs a, float scale) {
-    const int64_t n = a.g_out.nvox * a.c;
+    const int g8 = a.c / 8;
+    const int64_t n = a.g_out.nvox * g8;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const int c = int(i % a.c);
-        const int64_t vo = i / a.c;
+        const int c8 = int(i % g8);
+        const int64_t vo = i / g8;
         const Vox o = vox_of(vo, a.g_out);
         const int64_t vi = ((int64_t(o.b) * a.g_in.Z + o.z / 2) * a.g_in.Y + o.y / 2) * a.g_in.X + o.x / 2;
-        const float r = scale * __bfloat162float(a.in[vi * a.in_cs + a.in_co + c]);
-        bf16* p = a.out + vo * a.out_cs + a.out_co + c;
-        *p = __float2bfloat16_rn(a.accumulate ? __bfloat162float(*p) + r : r);
-    }
-}
-
-// Backward of upsampling: out[v] (coarse) = sum of the 8 children of in.
-__global__ void k_up2_bwd(PoolArgs a) {
-    const int64_t n = a.g_out.nvox * a.c;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const int c = int(i % a.c);
-        const Vox o = vox_of(i / a.c, a.g_out);
-        float s = 0.0f;
-        for (int q = 0; q < 8; ++q) {
-            const int64_t vi =
-                ((int64_t(o.b) * a.g_in.Z + 2 * o.z + (q >> 2)) * a.g_in.Y + 2 * o.y + ((q >> 1) & 1)) * a.g_in.X +
-                2 * o.x + (q & 1);
-            s += __bfloat162float(a.in[vi * a.in_cs + a.in_co + c]);
-        }
-        a.out[(i / a.c) * a.out_cs + a.out_co + c] = __float2bfloat16_rn(s);
+        float f[8], r[8];
+        bf8_to_f(*at8(a.in, vi, a.in_cs, a.in_co, c8), f);
+        uint4* dst = reinterpret_cast<uint4*>(a.out + vo * a.out_cs + a.out_co + 8 * c8);
+        if (a.accumulate) bf8_to_f(*dst, r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = (a.accumulate ? r[k] : 0.0f) + scale * f[k];
+        *dst = f_to_bf8(r);
     }
 }
 
 // g[v][c] *= (y[v][c] > 0)   (ReLU backward; y is the layer's output)
 __global__ void k_relu_bwd(bf16* gr, int g_cs, int g_co, const bf16* y, int y_cs, int y_co, int c, int64_t nvox) {
-    const int64_t n = nvox * c;
+    const int g8 = c / 8;
+    const int64_t n = nvox * g8;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(i % c);
-        const int64_t v = i / c;
-        if (!(__bfloat162float(y[v * y_cs + y_co + k]) > 0.0f)) gr[v * g_cs + g_co + k] = __float2bfloat16_rn(0.0f);
+        const int c8 = int(i % g8);
+        const int64_t v = i / g8;
+        float yv[8], gv[8];
+        bf8_to_f(*at8(y, v, y_cs, y_co, c8), yv);
+        uint4* dst = reinterpret_cast<uint4*>(gr + v * g_cs + g_co + 8 * c8);
+        bf8_to_f(*dst, gv);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gv[k] = yv[k] > 0.0f ? gv[k] : 0.0f;
+        *dst = f_to_bf8(gv);
     }
 }
 
@@ -335,23 +362,24 @@ cudaError_t to_bf16(const float* src, bf16* dst, int64_t n, cudaStream_t s) {
 }
 
 cudaError_t pool2(const PoolArgs& a, cudaStream_t s) {
-    k_pool2<<<grid1d(a.g_out.nvox * a.c), 256, 0, s>>>(a);
+    k_pool2<<<grid1d(a.g_out.nvox * (a.c / 8)), 256, 0, s>>>(a, 0.125f);
     return cudaGetLastError();
 }
 
 cudaError_t up2(const PoolArgs& a, float scale, cudaStream_t s) {
-    k_up2<<<grid1d(a.g_out.nvox * a.c), 256, 0, s>>>(a, scale);
+    k_up2<<<grid1d(a.g_out.nvox * (a.c / 8)), 256, 0, s>>>(a, scale);
     return cudaGetLastError();
 }
 
 cudaError_t up2_bwd(const PoolArgs& a, cudaStream_t s) {
-    k_up2_bwd<<<grid1d(a.g_out.nvox * a.c), 256, 0, s>>>(a);
+    if (a.accumulate) return cudaErrorInvalidValue;  // the backward of upsampling overwrites
+    k_pool2<<<grid1d(a.g_out.nvox * (a.c / 8)), 256, 0, s>>>(a, 1.0f);
     return cudaGetLastError();
 }
 
 cudaError_t relu_bwd(bf16* gr, int g_cs, int g_co, const bf16* y, int y_cs, int y_co, int c, int64_t nvox,
                      cudaStream_t s) {
-    k_relu_bwd<<<grid1d(nvox * c), 256, 0, s>>>(gr, g_cs, g_co, y, y_cs, y_co, c, nvox);
+    k_relu_bwd<<<grid1d(nvox * (c / 8)), 256, 0, s>>>(gr, g_cs, g_co, y, y_cs, y_co, c, nvox);
     return cudaGetLastError();
 }
 

