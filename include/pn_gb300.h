@@ -162,6 +162,10 @@ const char* pn_last_error(const pn_handle* h);
  * y = A x  (the matrix-free staggered operator; Eq. "(T + C - S) u = A u").
  * x, y: device vectors of `dtype` in the padded layout; must not alias.
  * Inactive slots of x are ignored; inactive slots of y are written 0.
+ * The first FP64 operator call on a 3D vacuum-boundary handle (pn_apply,
+ * pn_apply_t, pn_residual or a solver's refinement residual) allocates the
+ * per-class means of sigma_t and sigma_s at every slot (16 planes of FP64),
+ * kept until pn_destroy.
  */
 int pn_apply(pn_handle* h, const void* x, void* y, int dtype, void* stream);
 
@@ -562,6 +566,16 @@ int pn_wait_timeout_test(pn_handle* h, int deliver, long long limit_ns, int* tim
  * (default) or 0.  Results do not depend on it (bitwise).
  */
 int pn_set_pdl(pn_handle* h, int on);
+
+/*
+ * Arithmetic peak of the current GPU (a measurement aid; the paper has no
+ * counterpart): *gflops_out (host) = FMA throughput in GFLOP/s (2 flops per
+ * FMA) of a kernel of independent FP64 (dtype PN_F64) or FP32 (PN_F32) FMA
+ * chains filling every SM, best of five timed launches.  The denominator of
+ * the roofline of kernels bound by FP64 arithmetic.  Allocates 8 bytes and
+ * two events; synchronises `stream`.
+ */
+int pn_fma_peak(int dtype, double* gflops_out, void* stream);
 
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */

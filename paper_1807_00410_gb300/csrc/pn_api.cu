@@ -131,7 +131,7 @@ __global__ void k_fill_plane(const double* F, int R, int px, int py, int pz, int
 
 void free_all(pn_handle* h) {
     void* ptrs[] = {h->d_planes, h->d_terms, h->d_st_f, h->d_ss_f, h->d_st_d, h->d_ss_d,
-                    h->d_q_f,    h->d_q_d,   h->d_partials, h->d_scalars, h->d_work, h->d_ir};
+                    h->d_q_f,    h->d_q_d,   h->d_partials, h->d_scalars, h->d_work, h->d_ir, h->d_cmean};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);

@@ -223,28 +223,43 @@ int ensure_acts(pn_cnn* n, int B, int Z, int Y, int X) {
     return PN_OK;
 }
 
-// FP32 [v][c_in] -> BF16 [v][cinp] (zero padded);  BF16 [v][coutp] -> FP32 [v][c_out]
+// FP32 [v][c] -> BF16 [v][cp] (zero padded; cp a multiple of 8): one thread
+// per (voxel, group of 8 padded channels), one 16-byte store.  Also the
+// gradient of the output (same layouts).
 __global__ void k_pack(const float* in, int c, bf16* out, int cp, int64_t nvox) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox * cp; i += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(i % cp);
-        const int64_t v = i / cp;
-        out[i] = __float2bfloat16_rn(k < c ? in[v * c + k] : 0.0f);
+    const int g8 = cp / 8;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox * g8; i += int64_t(gridDim.x) * blockDim.x) {
+        const int k0 = int(i % g8) * 8;
+        const int64_t v = i / g8;
+        const float* src = in + v * c;
+        uint4 u;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + 2 * q;
+            h[q] = __floats2bfloat162_rn(k < c ? src[k] : 0.0f, k + 1 < c ? src[k + 1] : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(out + v * cp + k0) = u;
     }
 }
 
+// BF16 [v][cp] -> FP32 [v][c]: one thread per (voxel, group of 8 channels),
+// one 16-byte load.
 __global__ void k_unpack(const bf16* in, int cp, float* out, int c, int64_t nvox) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox * c; i += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(i % c);
-        const int64_t v = i / c;
-        out[i] = __bfloat162float(in[v * cp + k]);
-    }
-}
-
-// FP32 gradient [v][c_out] -> BF16 [v][coutp]
-__global__ void k_pack_grad(const float* g, int c, bf16* out, int cp, int64_t nvox) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox * cp; i += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(i % cp);
-        out[i] = __float2bfloat16_rn(k < c ? g[(i / cp) * c + k] : 0.0f);
+    const int g8 = (c + 7) / 8;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox * g8; i += int64_t(gridDim.x) * blockDim.x) {
+        const int k0 = int(i % g8) * 8;
+        const int64_t v = i / g8;
+        const uint4 u = *reinterpret_cast<const uint4*>(in + v * cp + k0);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+        float* dst = out + v * c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            const int k = k0 + 2 * q;
+            if (k < c) dst[k] = f.x;
+            if (k + 1 < c) dst[k + 1] = f.y;
+        }
     }
 }
 
@@ -544,12 +559,12 @@ int pn_cnn_forward(pn_cnn* n, const float* in, float* out, int B, int Z, int Y, 
     if (rc != PN_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nv = int64_t(B) * Z * Y * X;
-    k_pack<<<grid1(nv * n->cinp), 256, 0, s>>>(in, n->c_in, n->xin.p, n->cinp, nv);
+    k_pack<<<grid1(nv * (n->cinp / 8)), 256, 0, s>>>(in, n->c_in, n->xin.p, n->cinp, nv);
     CK(cudaGetLastError());
     rc = forward(n, s);
     if (rc != PN_OK) return rc;
     if (out) {
-        k_unpack<<<grid1(nv * n->c_out), 256, 0, s>>>(n->yout.p, n->coutp, out, n->c_out, nv);
+        k_unpack<<<grid1(nv * ((n->c_out + 7) / 8)), 256, 0, s>>>(n->yout.p, n->coutp, out, n->c_out, nv);
         CK(cudaGetLastError());
     }
     return PN_OK;
@@ -559,7 +574,7 @@ int pn_cnn_backward(pn_cnn* n, const float* grad_out, void* stream) {
     if (!n || !grad_out || !n->act_mem) return PN_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nv = int64_t(n->B) * n->Z * n->Y * n->X;
-    k_pack_grad<<<grid1(nv * n->coutp), 256, 0, s>>>(grad_out, n->c_out, n->gy.p, n->coutp, nv);
+    k_pack<<<grid1(nv * (n->coutp / 8)), 256, 0, s>>>(grad_out, n->c_out, n->gy.p, n->coutp, nv);
     CK(cudaGetLastError());
     return backward(n, s);
 }

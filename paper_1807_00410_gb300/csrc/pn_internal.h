@@ -122,6 +122,9 @@ struct pn_handle {
     void* d_ir = nullptr;
     size_t ir_bytes = 0;
     int64_t work_allocs = 0;  // device allocations made for d_work and d_ir so far (pn_get_workspace)
+    // FP64 operator: per parity class the means of sigma_t and sigma_s over the
+    // voxel centres adjacent to each slot (16 planes; built on first use)
+    double* d_cmean = nullptr;
 
     // launch profiler of pn_solve (opts.profile): event pairs pending readout
     bool prof_on = false;

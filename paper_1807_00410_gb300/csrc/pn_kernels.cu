@@ -7,6 +7,7 @@
 // table, and is the correctness baseline for the tiled FP32 kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "pn_internal.h"
@@ -107,6 +108,143 @@ __global__ void __launch_bounds__(256) k_op_slab(OpArgs<T> a, int x_lo) {
     }
 }
 
+// ---- FP64 operator of 3D vacuum-boundary handles ---------------------------------
+//
+// The refinement residual of the mixed-precision solvers runs in FP64, which
+// GB300 executes at a small fraction of its FP32 rate: the kernel keeps the
+// FP64 work per output to the operator's own arithmetic.  The mean of sigma_t
+// and of sigma_s over the voxel centres adjacent to each slot (section
+// "Precomputation": parameters interpolated to the staggered locations)
+// depends only on the slot's parity class, so it is computed once per handle
+// (cmean_build: 8 classes x 2 fields, the slot layout of a plane) and read as
+// two values per output.  Work items are (plane, z slice, 8-row band); block b
+// of G takes items b, b + G, ... (the residual's per-block FP64 partials are
+// then summed in a fixed order); a plane's term list goes to shared memory
+// once per item.
+
+// the class means: cm[(2 c + f) * plane_stride + slot], f = 0 (sigma_t), 1 (sigma_s)
+__global__ void __launch_bounds__(256) k_cmean_build(double* cm, const double* st, const double* ss, int R,
+                                                     int64_t pitch_x, int64_t pitch_y, int64_t plane_stride) {
+    const int c = blockIdx.y;
+    const int px = c & 1, py = (c >> 1) & 1, pz = c >> 2;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < plane_stride;
+         s += int64_t(gridDim.x) * blockDim.x) {
+        const int x = int(s % pitch_x);
+        const int64_t t = s / pitch_x;
+        const int y = int(t % (R + 1));
+        const int z = int(t / (R + 1));
+        double mt = 0.0, ms = 0.0;
+        if (x < R + px && y < R + py && z < R + pz && z <= R) {
+            mt = centre_mean(st, R, x, y, z, px, py, pz);
+            ms = centre_mean(ss, R, x, y, z, px, py, pz);
+        }
+        cm[int64_t(2 * c) * plane_stride + s] = mt;
+        cm[int64_t(2 * c + 1) * plane_stride + s] = ms;
+    }
+}
+
+constexpr int kF64MaxTerms = 16;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_op_f64(OpArgs<double> a, const double* cm, int nyb, int64_t items) {
+    __shared__ Term ts[kF64MaxTerms];
+    __shared__ Plane ps;
+    const int R = a.R;
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    double racc = 0.0;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int yb = int(it % nyb);
+        const int64_t u = it / nyb;
+        const int z = int(u % (R + 1));
+        const int p = int(u / (R + 1));
+        __syncthreads();  // the previous item's reads of ps and ts are done
+        if (threadIdx.x == 0) ps = a.planes[p];
+        __syncthreads();
+        const int nt = ps.t1 - ps.t0;
+        if (int(threadIdx.x) < nt) ts[threadIdx.x] = a.terms[ps.t0 + threadIdx.x];
+        __syncthreads();
+        const int px = ps.px, py = ps.py, pz = ps.pz;
+        const double fl = ps.fl_d;
+        const int cls = px + 2 * py + 4 * pz;
+        const double* cmt = cm + int64_t(2 * cls) * a.plane_stride;
+        const double* cms = cmt + a.plane_stride;
+        const int64_t pbase = int64_t(p) * a.plane_stride;
+        const int y = yb * 8 + ly;
+        if (y > R) continue;  // (no barrier follows before the next item's first)
+        const int64_t row = int64_t(z) * a.pitch_y + int64_t(y) * a.pitch_x;
+        const bool rowact = y < R + py && z < R + pz;
+        for (int x = lx; x < a.pitch_x; x += 32) {
+            const int64_t s = row + x;
+            double out = 0.0;
+            if (rowact && x < R + px) {
+                const double diag = fma(-fl, cms[s], cmt[s]);
+                double tr = 0.0;
+                for (int ti = 0; ti < nt; ++ti) {
+                    const Term tm = ts[ti];
+                    int i, b;
+                    int64_t stride;
+                    if (tm.axis == 0) { i = x; b = px; stride = 1; }
+                    else if (tm.axis == 1) { i = y; b = py; stride = a.pitch_x; }
+                    else { i = z; b = pz; stride = a.pitch_y; }
+                    const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
+                    const double vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : 0.0;
+                    const double vm = (i - b >= 0) ? a.x[qb - b * stride] : 0.0;
+                    tr = fma(tm.cd, vp - vm, tr);
+                }
+                const double own = diag * a.x[pbase + s];
+                out = MODE == OP_APPLY_T ? own - tr : own + tr;
+                if (MODE == OP_RESIDUAL) {
+                    const double bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : 0.0);
+                    out = bq - out;
+                    racc = fma(out, out, racc);
+                }
+            }
+            a.y[pbase + s] = out;
+        }
+    }
+    if (MODE == OP_RESIDUAL && a.partials != nullptr) {
+        const double bs = block_sum(racc);
+        if (threadIdx.x == 0) a.partials[blockIdx.x] = bs;
+    }
+}
+
+// plane tails (slots beyond each plane's box) are written 0 by this kernel
+__global__ void __launch_bounds__(256) k_zero_tails(double* y, int K, int64_t box, int64_t plane_stride) {
+    const int64_t tail = plane_stride - box;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < int64_t(K) * tail;
+         i += int64_t(gridDim.x) * blockDim.x)
+        y[(i / tail) * plane_stride + box + i % tail] = 0.0;
+}
+
+static bool use_f64_tiled(const pn_handle* h, int dtype) {
+    if (dtype != PN_F64 || h->dims != 3 || h->periodic) return false;
+    for (const Plane& P : h->planes)
+        if (P.t1 - P.t0 > kF64MaxTerms) return false;
+    return true;
+}
+
+static int64_t f64_items(const pn_handle* h) { return int64_t(h->K) * (h->R + 1) * ((h->R + 1 + 7) / 8); }
+
+static int f64_grid(const pn_handle* h) {
+    return int(std::min<int64_t>(f64_items(h), 8 * int64_t(pn_sm_count())));
+}
+
+// the class means of the handle (built on the first FP64 operator launch and
+// kept until pn_destroy)
+static cudaError_t ensure_cmean(const pn_handle* h, cudaStream_t s) {
+    pn_handle* hm = const_cast<pn_handle*>(h);
+    if (hm->d_cmean) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&hm->d_cmean, size_t(16) * size_t(h->plane_stride) * sizeof(double));
+    if (e != cudaSuccess) {
+        hm->d_cmean = nullptr;
+        return e;
+    }
+    const int gx = int(std::min<int64_t>(4096, (h->plane_stride + 255) / 256));
+    k_cmean_build<<<dim3(gx, 8), 256, 0, s>>>(hm->d_cmean, h->d_st_d, h->d_ss_d, h->R, h->pitch_x, h->pitch_y,
+                                             h->plane_stride);
+    return cudaGetLastError();
+}
+
 static int naive_grid_x(const pn_handle* h) {
     int64_t want = (h->plane_stride + 1023) / 1024;
     if (want > 4096) want = 4096;
@@ -130,10 +268,11 @@ static bool use_tiled(const pn_handle* h, int dtype) {
 
 bool tiled_serves(const pn_handle* h) { return use_tiled(h, PN_F32); }
 
-int op_launch_count(const pn_handle* h, int dtype) { return use_tiled(h, dtype) ? 2 : 1; }
+int op_launch_count(const pn_handle* h, int dtype) { return (use_tiled(h, dtype) || use_f64_tiled(h, dtype)) ? 2 : 1; }
 
 int op_partial_count(const pn_handle* h, int dtype) {
     if (use_tiled(h, dtype)) return tiled_partial_count(h);
+    if (use_f64_tiled(h, dtype)) return f64_grid(h);
     return naive_grid_x(h) * h->K;
 }
 
@@ -163,6 +302,29 @@ cudaError_t launch_op(const pn_handle* h, int mode, const void* x, void* y, int 
     if (dtype == PN_F32)
         return op_t<float>(h, mode, (const float*)x, (float*)y, h->d_st_f, h->d_ss_f, h->d_q_f, (const float*)bvec,
                            partials, s);
+    if (use_f64_tiled(h, dtype)) {
+        cudaError_t e = ensure_cmean(h, s);
+        if (e != cudaSuccess) return e;
+        OpArgs<double> a;
+        a.x = (const double*)x; a.y = (double*)y; a.q = h->d_q_d; a.n_q = h->n_q_planes; a.bvec = (const double*)bvec;
+        a.st = h->d_st_d; a.ss = h->d_ss_d;
+        a.planes = h->d_planes; a.terms = h->d_terms;
+        a.R = h->R; a.nzb = int(h->nz_box); a.periodic = 0;
+        a.pitch_x = h->pitch_x; a.pitch_y = h->pitch_y; a.plane_stride = h->plane_stride;
+        a.partials = partials;
+        const int nyb = (h->R + 1 + 7) / 8;
+        const int G = f64_grid(h);
+        if (mode == OP_APPLY) k_op_f64<OP_APPLY><<<G, 256, 0, s>>>(a, h->d_cmean, nyb, f64_items(h));
+        else if (mode == OP_APPLY_T) k_op_f64<OP_APPLY_T><<<G, 256, 0, s>>>(a, h->d_cmean, nyb, f64_items(h));
+        else k_op_f64<OP_RESIDUAL><<<G, 256, 0, s>>>(a, h->d_cmean, nyb, f64_items(h));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t box = h->pitch_y * (h->R + 1);
+        const int64_t nt = int64_t(h->K) * (h->plane_stride - box);
+        k_zero_tails<<<int(std::max<int64_t>(1, std::min<int64_t>(1024, (nt + 255) / 256))), 256, 0, s>>>(
+            (double*)y, h->K, box, h->plane_stride);
+        return cudaGetLastError();
+    }
     return op_t<double>(h, mode, (const double*)x, (double*)y, h->d_st_d, h->d_ss_d, h->d_q_d,
                         (const double*)bvec, partials, s);
 }

@@ -67,3 +67,83 @@ extern "C" int pn_wait_timeout_test(pn_handle* h, int deliver, long long limit_n
     *timed_out = (after != 0u && before == 0u) ? 1 : 0;
     return *timed_out ? PN_ERR_TIMEOUT : PN_OK;
 }
+
+// ---- arithmetic peaks ---------------------------------------------------------
+//
+// pn_fma_peak: the FP64 (or FP32) FMA rate of this GPU, measured by a kernel of
+// independent FMA chains (8 per thread, 2048 iterations each, every SM full),
+// timed with CUDA events.  The denominator of the roofline of kernels bound
+// by FP64 arithmetic (GB300's FP64 rate is a small fraction of its FP32 rate).
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chains(T seed, int iters, T* sink) {
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = seed + T(threadIdx.x + k);
+    const T m = T(0.999999), c = T(1e-7);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = a[k] * m + c;  // one FMA each
+    }
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == T(-1)) sink[0] = s;  // keeps the chains alive; never true for these inputs
+}
+
+template <typename T>
+int fma_peak(double* gflops, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        cudaGetLastError();
+        return PN_ERR_CUDA;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma_chains<T>, 256, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return PN_ERR_CUDA;
+    }
+    const int blocks = occ * sms, iters = 2048;
+    T* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&sink, sizeof(T)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (sink) cudaFree(sink);
+        if (e0) cudaEventDestroy(e0);
+        return PN_ERR_ALLOC;
+    }
+    k_fma_chains<T><<<blocks, 256, 0, s>>>(T(1), iters, sink);  // warm-up
+    float best = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        k_fma_chains<T><<<blocks, 256, 0, s>>>(T(1), iters, sink);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) best = ms;
+    }
+    cudaFree(sink);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PN_ERR_CUDA;
+    }
+    const double flops = 2.0 * 8.0 * double(iters) * double(blocks) * 256.0;
+    *gflops = flops / (double(best) * 1e-3) / 1e9;
+    return PN_OK;
+}
+
+}  // namespace
+
+extern "C" int pn_fma_peak(int dtype, double* gflops_out, void* stream) {
+    if (!gflops_out || (dtype != PN_F32 && dtype != PN_F64)) return PN_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return dtype == PN_F64 ? fma_peak<double>(gflops_out, s) : fma_peak<float>(gflops_out, s);
+}

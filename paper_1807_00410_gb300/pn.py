@@ -52,7 +52,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
            "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels",
            "pn_get_workspace", "pn_wait_timeout_test", "pn_set_pdl", "pn_cnn_set_conv_kernel",
-           "pn_cnn_take_error"]
+           "pn_cnn_take_error", "pn_fma_peak"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -152,6 +152,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_set_pdl": (i, [vp, i]),
         "pn_cnn_set_conv_kernel": (i, [vp, i]),
         "pn_cnn_take_error": (i, [vp]),
+        "pn_fma_peak": (i, [i, ctypes.POINTER(d), vp]),
         "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
@@ -712,6 +713,16 @@ def wait_timeout_test(system=None, deliver: bool = False, limit_ns: int = 2_000_
     h = system._h if system is not None else None
     rc = lib.pn_wait_timeout_test(h, 1 if deliver else 0, int(limit_ns), ctypes.byref(t), _stream_ptr(stream))
     return rc, t.value
+
+
+def fma_peak(dtype="f64", stream=None) -> float:
+    """pn_fma_peak: measured FMA throughput of the GPU in GFLOP/s."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.pn_fma_peak(PN_F64 if dtype == "f64" else PN_F32, ctypes.byref(out), _stream_ptr(stream))
+    if rc != PN_OK:
+        raise PnError(rc, "pn_fma_peak failed")
+    return out.value
 
 
 def barrier_test(blocks: int, expected: int, spin_limit: int, stream=None):
