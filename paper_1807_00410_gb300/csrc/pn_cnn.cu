@@ -135,6 +135,8 @@ int conv_back(pn_cnn* n, const char* name, const Buf& in, int in_co, const Buf& 
     w.dw = n->d_g + L->w_off;
     w.db = n->d_g + L->b_off;
     w.g = grid_at(n, in.level);
+    w.use_tc = n->conv_kernel == PN_CNN_CONV_TCGEN05 ? 1 : 0;
+    w.err = n->d_err;
     CK(pn::cnn::conv3_wgrad(w, s));
     if (gin) {
         pn::cnn::ConvArgs a;

@@ -47,6 +47,8 @@ struct WgradArgs {
     float* dw;
     float* db;
     Grid g;
+    int use_tc = 1;               // 1: the tcgen05 kernel (pn_cnn_tc.cu); 0: the mma.sync kernel
+    unsigned int* err = nullptr;  // error word of the tcgen05 kernel's bounded waits
 };
 
 // Resampling between a fine grid and the grid of half its size.
@@ -66,6 +68,8 @@ cudaError_t conv3(const ConvArgs& a, cudaStream_t s);
 bool conv3_tc_serves(const ConvArgs& a);
 cudaError_t conv3_tc(const ConvArgs& a, unsigned int* err, cudaStream_t s);
 cudaError_t conv3_wgrad(const WgradArgs& a, cudaStream_t s);
+bool conv3_wgrad_tc_serves(const WgradArgs& a);
+cudaError_t conv3_wgrad_tc(const WgradArgs& a, unsigned int* err, cudaStream_t s);
 cudaError_t flip_weights(const bf16* w, bf16* wt, int co, int ci, cudaStream_t s);
 cudaError_t to_bf16(const float* src, bf16* dst, int64_t n, cudaStream_t s);
 cudaError_t pool2(const PoolArgs& a, cudaStream_t s);               // fine -> coarse mean

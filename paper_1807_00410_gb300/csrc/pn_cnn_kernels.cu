@@ -342,9 +342,14 @@ cudaError_t conv3(const ConvArgs& a, cudaStream_t s) {
 }
 
 cudaError_t conv3_wgrad(const WgradArgs& a, cudaStream_t s) {
-    const int chunks = int(std::min<int64_t>(64, std::max<int64_t>(1, a.g.nvox / 4096)));
-    k_conv3_wgrad<<<dim3(27, chunks), 256, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (a.use_tc && conv3_wgrad_tc_serves(a)) {
+        e = conv3_wgrad_tc(a, a.err, s);
+    } else {
+        const int chunks = int(std::min<int64_t>(64, std::max<int64_t>(1, a.g.nvox / 4096)));
+        k_conv3_wgrad<<<dim3(27, chunks), 256, 0, s>>>(a);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess || !a.db) return e;
     k_bias_grad<<<dim3(unsigned(std::min<int64_t>(1024, (a.g.nvox + 7) / 8)), (a.co + 31) / 32), 256, 0, s>>>(
         a.gy, a.gy_cs, a.gy_co, a.co, a.g.nvox, a.db);

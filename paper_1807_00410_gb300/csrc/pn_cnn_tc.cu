@@ -290,6 +290,164 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---- weight gradient --------------------------------------------------------------
+//
+//     dW[tap][o][c] += sum_v gy[v][o] x[v + tap][c]
+//
+// as D = A B per group of taps: M = 128 rows = (tap of the group, input
+// channel) -- 128 / ci taps stacked, the rows beyond them unused -- N = n <= 64
+// output channels, K = voxels.  Both operands come straight from the
+// channels-last tensors, so both are MN-major (the 8 channels of one 16-byte
+// row of a core matrix are the M or N index, its 8 rows 8 consecutive voxels):
+// per 128-voxel tile (8 x 16 y 1 z of one sample) the x slice of each stacked
+// tap arrives as 8-channel boxes (x, y, z shifted by the tap; coordinates
+// outside the grid read as 0), the gradient of the output as 8-channel boxes
+// of the unshifted tile.  In a box the voxel rows are 16 bytes apart: the next
+// 8 voxels (K) are 128 bytes on (leading byte offset), the next 8 channels (M
+// or N) one box (2048 bytes) on (stride byte offset).  Each CTA walks a range
+// of tiles, accumulating in TMEM, and adds its sums to dW with FP32 atomics.
+constexpr uint32_t kWBox = 2048;  // 8 channels x 128 voxels
+
+struct WArgs {
+    int ci, n;           // input channels of the layer; output channels of this launch (16..64)
+    int x_co, gy_co;     // channel offsets of the slices read
+    int o0;              // first output channel of this launch
+    int taps_per, t0;    // taps stacked in M (128 / ci, at most 27) and the group's first tap
+    int ntap;            // taps of this group (<= taps_per)
+    int ntx, nty, Z;     // tiles per axis and slices (one z slice per tile)
+    int64_t tiles;       // tiles in total
+    int64_t per;         // tiles per CTA
+    float* dw;           // [27][co][ci]
+    int co;              // output channels of the layer (row stride of dw)
+    uint32_t idesc;
+    uint32_t tmem_cols;
+    unsigned int* err;
+};
+
+__host__ __device__ constexpr uint32_t wslot_bytes(int n) { return 16u * kWBox + uint32_t(n / 8) * kWBox; }
+constexpr int kWStages = 3;
+__host__ __device__ constexpr uint32_t wsmem_bytes(int n) { return kWStages * wslot_bytes(n) + 1024u; }
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv3_wgrad_tc(const __grid_constant__ CUtensorMap xm, const __grid_constant__ CUtensorMap gm, WArgs a) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full[kWStages], empty[kWStages], done;
+    __shared__ uint32_t tmem_slot;
+    unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+    const uint32_t ring_s = mbar::smem_u32(ring);
+    const uint32_t SB = wslot_bytes(a.n);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tb = int64_t(blockIdx.x) * a.per;
+    const int64_t te = tb + a.per < a.tiles ? tb + a.per : a.tiles;
+    const int steps = te > tb ? int(te - tb) : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWStages; ++s) {
+            mbar::init(mbar::smem_u32(&full[s]), 1u);
+            mbar::init(mbar::smem_u32(&empty[s]), 1u);
+        }
+        mbar::init(mbar::smem_u32(&done), 1u);
+        mbar::fence_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         mbar::smem_u32(&tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int cg = a.ci / 8;  // 8-channel groups per tap
+    const uint32_t tx_bytes = uint32_t(a.ntap * cg + a.n / 8) * kWBox;
+    bool failed = false;
+    if (threadIdx.x == 0 && steps > 0) {
+        auto issue = [&](int k) {
+            int64_t t = tb + k;
+            const int tx = int(t % a.ntx);
+            t /= a.ntx;
+            const int ty = int(t % a.nty);
+            t /= a.nty;
+            const int z0 = int(t % a.Z);
+            const int b = int(t / a.Z);
+            const int x0 = tx * 8, y0 = ty * 16;
+            const int slot = k % kWStages;
+            const uint32_t bar = mbar::smem_u32(&full[slot]);
+            const uint32_t sa = ring_s + uint32_t(slot) * SB;
+            mbar::arrive_expect_tx(bar, tx_bytes);
+            for (int j = 0; j < a.ntap; ++j) {
+                const int tap = a.t0 + j;
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                for (int g = 0; g < cg; ++g)
+                    tma_load_5d(sa + uint32_t(j * cg + g) * kWBox, &xm, a.x_co + 8 * g, x0 + dx, y0 + dy, z0 + dz, b,
+                                bar);
+            }
+            const uint32_t sb = sa + 16u * kWBox;
+            for (int g = 0; g < a.n / 8; ++g)
+                tma_load_5d(sb + uint32_t(g) * kWBox, &gm, a.gy_co + a.o0 + 8 * g, x0, y0, z0, b, bar);
+        };
+        const int pro = steps < kWStages ? steps : kWStages;
+        int issued = 0, consumed = 0;
+        for (int k = 0; k < pro; ++k, ++issued) issue(k);
+        for (int k = 0; k < steps && !failed; ++k) {
+            const int slot = k % kWStages;
+            mbar::wait(mbar::smem_u32(&full[slot]), uint32_t(k / kWStages) & 1u, a.err, failed);
+            if (failed) break;
+            consumed = k + 1;
+            fence_after_sync();
+            const uint32_t sa = ring_s + uint32_t(slot) * SB;
+            const uint32_t sb = sa + 16u * kWBox;
+            for (int kk = 0; kk < 8; ++kk) {  // 16 voxels per MMA
+                const uint64_t ad = smem_desc(sa + uint32_t(kk) * 256u, 128u, kWBox);
+                const uint64_t bd = smem_desc(sb + uint32_t(kk) * 256u, 128u, kWBox);
+                mma_bf16(tmem, ad, bd, a.idesc, (k > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(mbar::smem_u32(&empty[slot]));
+            const int kp = k - 1, kn = kp + kWStages;
+            if (kp >= 0 && kn < steps) {
+                mbar::wait(mbar::smem_u32(&empty[kp % kWStages]), uint32_t(kp / kWStages) & 1u, a.err, failed);
+                if (!failed) {
+                    issue(kn);
+                    ++issued;
+                }
+            }
+        }
+        mma_commit(mbar::smem_u32(&done));
+        if (failed) {
+            bool f2 = false;
+            for (int k = consumed; k < issued; ++k)
+                mbar::wait(mbar::smem_u32(&full[k % kWStages]), uint32_t(k / kWStages) & 1u, a.err, f2);
+        }
+    }
+    __syncwarp();
+    if (steps > 0) {
+        bool f3 = false;
+        mbar::wait(mbar::smem_u32(&done), 0u, a.err, f3);
+        fence_after_sync();
+        // row m of D = (tap j of the group, channel c); its n columns = output channels
+        const int m = warp * 32 + lane;
+        const int j = m / a.ci, c = m % a.ci;
+        const bool ok = j < a.ntap;
+        float* dst = a.dw + (int64_t(a.t0 + j) * a.co + a.o0) * a.ci + c;
+        for (int c0 = 0; c0 < a.n; c0 += 16) {
+            float r[16];
+            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+            if (ok) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(dst + int64_t(c0 + i) * a.ci, r[i]);
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    }
+}
+
 // ---- host ------------------------------------------------------------------------
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -369,6 +527,89 @@ cudaError_t conv3_tc(const ConvArgs& a, unsigned int* err, cudaStream_t s) {
         tc::k_conv3_tc<<<unsigned(tiles), tc::kThreads, tc::smem_bytes(n), s>>>(act, wts, p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace cnn
+}  // namespace pn
+
+namespace pn {
+namespace cnn {
+
+bool conv3_wgrad_tc_serves(const WgradArgs& a) {
+    return tensor_map_encoder() != nullptr && a.ci % 16 == 0 && a.ci <= 128 && a.co % 16 == 0 && a.co >= 16 &&
+           a.x_cs % 8 == 0 && a.x_co % 8 == 0 && a.gy_cs % 8 == 0 && a.gy_co % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(a.x) & 15u) == 0 && (reinterpret_cast<uintptr_t>(a.gy) & 15u) == 0 &&
+           a.g.nvox > 0;
+}
+
+// dW[tap][o][c] += sum_v gy[v][o] x[v + tap][c] on the tcgen05 tensor cores;
+// the bias gradient is left to the caller.
+cudaError_t conv3_wgrad_tc(const WgradArgs& a, unsigned int* err, cudaStream_t s) {
+    const tc::EncodeTiled enc = reinterpret_cast<tc::EncodeTiled>(tensor_map_encoder());
+    if (!enc || !conv3_wgrad_tc_serves(a)) return cudaErrorNotSupported;
+    // 5D maps (channels, x, y, z, sample) with 8-channel x 8 x 16 x 1 boxes
+    auto map5 = [&](CUtensorMap& m, const bf16* base, int cs) -> bool {
+        std::memset(&m, 0, sizeof(m));
+        const cuuint64_t dim[5] = {cuuint64_t(cs), cuuint64_t(a.g.X), cuuint64_t(a.g.Y), cuuint64_t(a.g.Z),
+                                   cuuint64_t(a.g.B)};
+        const cuuint64_t row = cuuint64_t(cs) * 2;
+        const cuuint64_t str[4] = {row, row * a.g.X, row * a.g.X * a.g.Y, row * a.g.X * a.g.Y * a.g.Z};
+        const cuuint32_t box[5] = {8u, 8u, 16u, 1u, 1u};
+        const cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
+        return enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(base), dim, str, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap xm, gm;
+    if (!map5(xm, a.x, a.x_cs) || !map5(gm, a.gy, a.gy_cs)) return cudaErrorInvalidValue;
+    static std::atomic<unsigned long long> configured{0};
+    cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(tc::k_conv3_wgrad_tc),
+                                      int(tc::wsmem_bytes(tc::kMaxN)));
+    if (e != cudaSuccess) return e;
+    const int ntx = (a.g.X + 7) / 8, nty = (a.g.Y + 15) / 16;
+    const int64_t tiles = int64_t(ntx) * nty * a.g.Z * a.g.B;
+    const int taps_per = std::min(27, 128 / a.ci);
+    const int groups = (27 + taps_per - 1) / taps_per;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    for (int o0 = 0; o0 < a.co; o0 += tc::kMaxN) {
+        const int n = std::min(tc::kMaxN, a.co - o0);
+        // split K (the tiles) so that groups x chunks fills about two waves
+        const int64_t want = std::max<int64_t>(1, (2 * int64_t(sms) + groups - 1) / groups);
+        const int64_t chunks = std::min<int64_t>(tiles, want);
+        const int64_t per = (tiles + chunks - 1) / chunks;
+        const int64_t nchunks = (tiles + per - 1) / per;
+        for (int gi = 0; gi < groups; ++gi) {
+            tc::WArgs p{};
+            p.ci = a.ci;
+            p.n = n;
+            p.x_co = a.x_co;
+            p.gy_co = a.gy_co;
+            p.o0 = o0;
+            p.taps_per = taps_per;
+            p.t0 = gi * taps_per;
+            p.ntap = std::min(taps_per, 27 - p.t0);
+            p.ntx = ntx;
+            p.nty = nty;
+            p.Z = a.g.Z;
+            p.tiles = tiles;
+            p.per = per;
+            p.dw = a.dw;
+            p.co = a.co;
+            // kind::f16: D F32, A and B BF16, both MN-major (bits 15, 16 = 1), N >> 3 at bit 17, M >> 4 at bit 24
+            p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | (uint32_t(n >> 3) << 17) |
+                      (uint32_t(128 >> 4) << 24);
+            uint32_t cols = 32;
+            while (cols < uint32_t(n)) cols <<= 1;
+            p.tmem_cols = cols;
+            p.err = err;
+            tc::k_conv3_wgrad_tc<<<unsigned(nchunks), tc::kThreads, tc::wsmem_bytes(n), s>>>(xm, gm, p);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
