@@ -312,11 +312,11 @@ struct WArgs {
     int ci, n;           // input channels of the layer; output channels of this launch (16..64)
     int x_co, gy_co;     // channel offsets of the slices read
     int o0;              // first output channel of this launch
-    int taps_per, t0;    // taps stacked in M (128 / ci, at most 27) and the group's first tap
-    int ntap;            // taps of this group (<= taps_per)
+    int taps_per;        // taps stacked in M (128 / ci, at most 27); group g holds taps g * taps_per ...
+    int nchunks;         // CTAs per group: CTA b takes group b / nchunks, tile chunk b % nchunks
     int ntx, nty, Z;     // tiles per axis and slices (one z slice per tile)
     int64_t tiles;       // tiles in total
-    int64_t per;         // tiles per CTA
+    int64_t per;         // tiles per chunk
     float* dw;           // [27][co][ci]
     int co;              // output channels of the layer (row stride of dw)
     uint32_t idesc;
@@ -337,7 +337,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t ring_s = mbar::smem_u32(ring);
     const uint32_t SB = wslot_bytes(a.n);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tb = int64_t(blockIdx.x) * a.per;
+    const int group = int(blockIdx.x) / a.nchunks, chunk = int(blockIdx.x) % a.nchunks;
+    const int t0 = group * a.taps_per;
+    const int ntap = 27 - t0 < a.taps_per ? 27 - t0 : a.taps_per;
+    const int64_t tb = int64_t(chunk) * a.per;
     const int64_t te = tb + a.per < a.tiles ? tb + a.per : a.tiles;
     const int steps = te > tb ? int(te - tb) : 0;
 
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
     const int cg = a.ci / 8;  // 8-channel groups per tap
-    const uint32_t tx_bytes = uint32_t(a.ntap * cg + a.n / 8) * kWBox;
+    const uint32_t tx_bytes = uint32_t(ntap * cg + a.n / 8) * kWBox;
     bool failed = false;
     if (threadIdx.x == 0 && steps > 0) {
         auto issue = [&](int k) {
@@ -377,8 +380,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t bar = mbar::smem_u32(&full[slot]);
             const uint32_t sa = ring_s + uint32_t(slot) * SB;
             mbar::arrive_expect_tx(bar, tx_bytes);
-            for (int j = 0; j < a.ntap; ++j) {
-                const int tap = a.t0 + j;
+            for (int j = 0; j < ntap; ++j) {
+                const int tap = t0 + j;
                 const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
                 for (int g = 0; g < cg; ++g)
                     tma_load_5d(sa + uint32_t(j * cg + g) * kWBox, &xm, a.x_co + 8 * g, x0 + dx, y0 + dy, z0 + dz, b,
@@ -429,8 +432,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // row m of D = (tap j of the group, channel c); its n columns = output channels
         const int m = warp * 32 + lane;
         const int j = m / a.ci, c = m % a.ci;
-        const bool ok = j < a.ntap;
-        float* dst = a.dw + (int64_t(a.t0 + j) * a.co + a.o0) * a.ci + c;
+        const bool ok = j < ntap;
+        float* dst = a.dw + (int64_t(t0 + j) * a.co + a.o0) * a.ci + c;
         for (int c0 = 0; c0 < a.n; c0 += 16) {
             float r[16];
             tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
@@ -577,39 +580,36 @@ cudaError_t conv3_wgrad_tc(const WgradArgs& a, unsigned int* err, cudaStream_t s
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     for (int o0 = 0; o0 < a.co; o0 += tc::kMaxN) {
         const int n = std::min(tc::kMaxN, a.co - o0);
-        // split K (the tiles) so that groups x chunks fills about two waves
-        const int64_t want = std::max<int64_t>(1, (2 * int64_t(sms) + groups - 1) / groups);
+        // one launch: every tap group x chunks of tiles, about four CTAs per SM
+        const int64_t want = std::max<int64_t>(1, (4 * int64_t(sms) + groups - 1) / groups);
         const int64_t chunks = std::min<int64_t>(tiles, want);
         const int64_t per = (tiles + chunks - 1) / chunks;
         const int64_t nchunks = (tiles + per - 1) / per;
-        for (int gi = 0; gi < groups; ++gi) {
-            tc::WArgs p{};
-            p.ci = a.ci;
-            p.n = n;
-            p.x_co = a.x_co;
-            p.gy_co = a.gy_co;
-            p.o0 = o0;
-            p.taps_per = taps_per;
-            p.t0 = gi * taps_per;
-            p.ntap = std::min(taps_per, 27 - p.t0);
-            p.ntx = ntx;
-            p.nty = nty;
-            p.Z = a.g.Z;
-            p.tiles = tiles;
-            p.per = per;
-            p.dw = a.dw;
-            p.co = a.co;
-            // kind::f16: D F32, A and B BF16, both MN-major (bits 15, 16 = 1), N >> 3 at bit 17, M >> 4 at bit 24
-            p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | (uint32_t(n >> 3) << 17) |
-                      (uint32_t(128 >> 4) << 24);
-            uint32_t cols = 32;
-            while (cols < uint32_t(n)) cols <<= 1;
-            p.tmem_cols = cols;
-            p.err = err;
-            tc::k_conv3_wgrad_tc<<<unsigned(nchunks), tc::kThreads, tc::wsmem_bytes(n), s>>>(xm, gm, p);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-        }
+        tc::WArgs p{};
+        p.ci = a.ci;
+        p.n = n;
+        p.x_co = a.x_co;
+        p.gy_co = a.gy_co;
+        p.o0 = o0;
+        p.taps_per = taps_per;
+        p.nchunks = int(nchunks);
+        p.ntx = ntx;
+        p.nty = nty;
+        p.Z = a.g.Z;
+        p.tiles = tiles;
+        p.per = per;
+        p.dw = a.dw;
+        p.co = a.co;
+        // kind::f16: D F32, A and B BF16, both MN-major (bits 15, 16 = 1), N >> 3 at bit 17, M >> 4 at bit 24
+        p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | (uint32_t(n >> 3) << 17) |
+                  (uint32_t(128 >> 4) << 24);
+        uint32_t cols = 32;
+        while (cols < uint32_t(n)) cols <<= 1;
+        p.tmem_cols = cols;
+        p.err = err;
+        tc::k_conv3_wgrad_tc<<<unsigned(nchunks * groups), tc::kThreads, tc::wsmem_bytes(n), s>>>(xm, gm, p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
