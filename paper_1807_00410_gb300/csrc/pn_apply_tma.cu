@@ -87,9 +87,24 @@ struct LayN {
     static constexpr Lay value = make_lay(N);
 };
 
-// ring, sigma tile (2 slots x 2 fields), 2 x DEPTH mbarriers, alignment slack
+// Orders 6 and 7 (one CTA per SM) write their outputs through shared memory:
+// each thread group stages its two classes' outputs of a z-step (n planes x 4
+// rows x 32 slots per class) and one thread stores them with TMA tensor
+// stores, instead of one global store per output and thread.  Below order 6
+// the staging tile would cost the second CTA per SM.
+template <int N>
+struct StoreTma {
+    static constexpr bool value = N >= 6;
+};
+
+// output staging tile: K planes x TY rows x TX slots (floats)
+constexpr int ost_floats(int N, bool ts) { return ts ? (N + 1) * (N + 1) * TX * TY : 0; }
+
+// ring, output staging tile (orders >= 6), sigma tile (2 slots x 2 fields),
+// 2 x DEPTH mbarriers, alignment slack
 constexpr size_t smem_bytes(int N) {
-    return size_t(make_lay(N).floats) * 4 + size_t(4 * GSL) * 4 + 2 * DEPTH * 8 + 128;
+    return size_t(make_lay(N).floats) * 4 + size_t(ost_floats(N, N >= 6)) * 4 + size_t(4 * GSL) * 4 +
+           2 * DEPTH * 8 + 128;
 }
 
 struct Maps {
@@ -106,6 +121,25 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 }
 __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err, bool& failed) {
     mbar::wait(bar, parity, err, failed);
+}
+
+// TMA tensor store of a 4D box from shared memory (bulk async-group of the
+// issuing thread), its group commit and waits, and the proxy fence that makes
+// this thread's shared-memory writes visible to the copy engine
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// barrier of one thread group (4 warps); id 1 + group (0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(TX * TY) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -141,9 +175,10 @@ __device__ __forceinline__ void issue(const Maps& m, uint32_t ring_s, uint32_t b
 // slice s + 1.  Same arithmetic, in the same order, as the register-staged
 // kernel's compute_class.
 template <int N, int C, int MODE>
-__device__ __forceinline__ void tma_class(const Args& a, const float* ring, int tx, int ty, int u, int u1,
-                                          bool store_ok, bool active, size_t outoff, float st, float ss,
+__device__ __forceinline__ void tma_class(const Args& a, const float* ring, float* ost, int tx, int ty, int u,
+                                          int u1, bool store_ok, bool active, size_t outoff, float st, float ss,
                                           const float (&rhs)[MAXC], float& rrun) {
+    constexpr bool TS = StoreTma<N>::value;
     constexpr Tab T = TabN<N>::value;
     constexpr ClassTab CT = T.cls[C];
     constexpr Lay L = LayN<N>::value;
@@ -186,14 +221,17 @@ __device__ __forceinline__ void tma_class(const Args& a, const float* ring, int 
             if (MODE == OP_RESIDUAL) out = rhs[i] - out;
             out = active ? out : 0.0f;
             if (MODE == OP_RESIDUAL) rrun = fmaf(out, out, rrun);
-            if (store_ok) yo[uint32_t(i) * ps] = out;
+            if (TS) ost[(CT.plane0 + i) * (TX * TY) + ty * TX + tx] = out;  // rows beyond R: clipped by the store
+            else if (store_ok) yo[uint32_t(i) * ps] = out;
         }
     }
 }
 
 template <int N, int GRP, int MODE>
-__device__ __forceinline__ void run_group(const Maps& m, const Args& a, float* ring, float* sg, uint32_t bar_s,
-                                          int tx, int ty, int za, int zb, double& racc) {
+__device__ __forceinline__ void run_group(const Maps& m, const Maps& ms, const Args& a, float* ring, float* ost,
+                                          float* sg, uint32_t bar_s, int tx, int ty, int za, int zb, double& racc) {
+    constexpr bool TS = StoreTma<N>::value;
+    const bool elected = tx == 0 && ty == 0;  // issues this group's output stores
     constexpr int CE = GRP, CO = kOdd[GRP];
     constexpr int bxe = CE & 1, bye = (CE >> 1) & 1, bxo = CO & 1, byo = (CO >> 1) & 1;
     constexpr bool same_xy = bxe == bxo && bye == byo;
@@ -273,9 +311,26 @@ __device__ __forceinline__ void run_group(const Maps& m, const Args& a, float* r
         const float mot = same_xy ? met : tiled::xy_mean_g(g, GX, tx, ty, bxo, byo);
         const float mos = same_xy ? mes : tiled::xy_mean_g(g + GSL, GX, tx, ty, bxo, byo);
         const size_t outoff = size_t(uint32_t(s) * a.pitch_y) + col;
-        tma_class<N, CE, MODE>(a, ring, tx, ty, u, u1, store_ok, acte && s < R, outoff, met, mes, rhse, rrun);
-        tma_class<N, CO, MODE>(a, ring, tx, ty, u, u1, store_ok, acto, outoff, 0.5f * (mot + mot_prev),
+        if (TS) {
+            // the group's staging tile is free once its previous stores have read it
+            if (elected) bulk_wait_read0();
+            group_sync(GRP);
+        }
+        tma_class<N, CE, MODE>(a, ring, ost, tx, ty, u, u1, store_ok, acte && s < R, outoff, met, mes, rhse, rrun);
+        tma_class<N, CO, MODE>(a, ring, ost, tx, ty, u, u1, store_ok, acto, outoff, 0.5f * (mot + mot_prev),
                                0.5f * (mos + mos_prev), rhso, rrun);
+        if (TS) {
+            constexpr Tab T = TabN<N>::value;
+            fence_async_smem();
+            group_sync(GRP);
+            if (elected) {
+                if (T.cls[CE].n)
+                    tma_store_4d(&ms.tm[CE], smem_u32(ost + T.cls[CE].plane0 * (TX * TY)), x0, y0, s, 0);
+                if (T.cls[CO].n)
+                    tma_store_4d(&ms.tm[CO], smem_u32(ost + T.cls[CO].plane0 * (TX * TY)), x0, y0, s, 0);
+                bulk_commit();
+            }
+        }
         if (MODE == OP_RESIDUAL && ++rcnt == 4) {
             racc += double(rrun);
             rrun = 0.0f;
@@ -285,6 +340,7 @@ __device__ __forceinline__ void run_group(const Maps& m, const Args& a, float* r
         mos_prev = mos;
     }
     racc += double(rrun);
+    if (TS && elected) bulk_wait0();  // the group's last stores are complete
     if (tid == 0) {
         // every copy issued above was waited for; after a wait that ran out,
         // wait (bounded) for the last copy of each slot before returning
@@ -304,7 +360,7 @@ __device__ __forceinline__ void run_group(const Maps& m, const Args& a, float* r
 // two CTAs per SM where their shared memory fits and 64 registers suffice
 template <int N, int MODE>
 __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)) ? 2 : 1)
-    k_apply_tma(const __grid_constant__ Maps m, Args a) {
+    k_apply_tma(const __grid_constant__ Maps m, const __grid_constant__ Maps ms, Args a) {
     // programmatic dependent launch: the input (and the gate) come from the
     // previous kernel; the next kernel may start once every CTA has finished
     // its z-march (the trigger below)
@@ -313,7 +369,8 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
     constexpr Lay L = LayN<N>::value;
     extern __shared__ __align__(128) unsigned char dsm[];
     float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dsm) + 127) & ~uintptr_t(127));
-    float* sg = ring + L.floats;
+    float* ost = ring + L.floats;  // output staging tile (orders >= 6), 128-byte aligned
+    float* sg = ost + ost_floats(N, StoreTma<N>::value);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sg + 4 * GSL);
     const uint32_t bar_s = smem_u32(bars);
     // warp w runs group w % 4: each of the SM's four schedulers (warps are
@@ -330,10 +387,10 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
     __syncthreads();
     double racc = 0.0;
     switch (grp) {
-        case 0: run_group<N, 0, MODE>(m, a, ring, sg, bar_s, tx, ty, za, zb, racc); break;
-        case 1: run_group<N, 1, MODE>(m, a, ring, sg, bar_s, tx, ty, za, zb, racc); break;
-        case 2: run_group<N, 2, MODE>(m, a, ring, sg, bar_s, tx, ty, za, zb, racc); break;
-        default: run_group<N, 3, MODE>(m, a, ring, sg, bar_s, tx, ty, za, zb, racc); break;
+        case 0: run_group<N, 0, MODE>(m, ms, a, ring, ost, sg, bar_s, tx, ty, za, zb, racc); break;
+        case 1: run_group<N, 1, MODE>(m, ms, a, ring, ost, sg, bar_s, tx, ty, za, zb, racc); break;
+        case 2: run_group<N, 2, MODE>(m, ms, a, ring, ost, sg, bar_s, tx, ty, za, zb, racc); break;
+        default: run_group<N, 3, MODE>(m, ms, a, ring, ost, sg, bar_s, tx, ty, za, zb, racc); break;
     }
     pdl_trigger();
     if (MODE == OP_RESIDUAL && a.partials != nullptr) {
@@ -381,6 +438,7 @@ EncodeTiled encode_fn() {
 struct Cache {
     struct Entry {
         const void* x;
+        bool store;  // maps of an output vector (the whole padded box of each class)
         Maps m;
     };
     std::vector<Entry> e;
@@ -388,7 +446,11 @@ struct Cache {
 };
 constexpr size_t kCacheEntries = 48;
 
-bool encode_maps(const pn_handle* h, const void* x, Maps& m) {
+// Load maps (store = false): each class's active extents, so that the copy
+// engine writes 0 for inactive and out-of-domain slots.  Store maps: the whole
+// padded box of each class's planes (the kernel writes 0 into the inactive
+// slots of its tile; rows beyond the box are clipped).
+bool encode_maps(const pn_handle* h, const void* x, Maps& m, bool store) {
     const EncodeTiled enc = encode_fn();
     if (!enc) return false;
     std::memset(&m, 0, sizeof(m));
@@ -400,11 +462,12 @@ bool encode_maps(const pn_handle* h, const void* x, Maps& m) {
     for (int c = 0; c < 8; ++c) {
         if (n[c] == 0) continue;
         const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
-        const cuuint64_t dim[4] = {cuuint64_t(h->R + bx), cuuint64_t(h->R + by), cuuint64_t(h->R + bz),
+        const cuuint64_t dim[4] = {store ? cuuint64_t(h->pitch_x) : cuuint64_t(h->R + bx),
+                                   cuuint64_t(store ? h->R + 1 : h->R + by), cuuint64_t(store ? h->R + 1 : h->R + bz),
                                    cuuint64_t(n[c])};
         const cuuint64_t str[3] = {cuuint64_t(h->pitch_x) * 4, cuuint64_t(h->pitch_y) * 4,
                                    cuuint64_t(h->plane_stride) * 4};
-        const cuuint32_t box[4] = {cuuint32_t(BX), cuuint32_t(BY), 1u, cuuint32_t(n[c])};
+        const cuuint32_t box[4] = {cuuint32_t(store ? TX : BX), cuuint32_t(store ? TY : BY), 1u, cuuint32_t(n[c])};
         const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
         void* base = const_cast<char*>(static_cast<const char*>(x)) + size_t(p0[c]) * h->plane_stride * 4;
         if (enc(&m.tm[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -415,7 +478,7 @@ bool encode_maps(const pn_handle* h, const void* x, Maps& m) {
     return true;
 }
 
-const Maps* maps_for(const pn_handle* h, const void* x) {
+const Maps* maps_for(const pn_handle* h, const void* x, bool store) {
     pn_handle* hm = const_cast<pn_handle*>(h);
     Cache* c = static_cast<Cache*>(hm->tma_cache);
     if (!c) {
@@ -424,10 +487,11 @@ const Maps* maps_for(const pn_handle* h, const void* x) {
         hm->tma_cache = c;
     }
     for (const auto& e : c->e)
-        if (e.x == x) return &e.m;
+        if (e.x == x && e.store == store) return &e.m;
     Cache::Entry ne;
     ne.x = x;
-    if (!encode_maps(h, x, ne.m)) return nullptr;
+    ne.store = store;
+    if (!encode_maps(h, x, ne.m, store)) return nullptr;
     if (c->e.size() < kCacheEntries) {
         c->e.push_back(ne);
         return &c->e.back().m;
@@ -439,27 +503,28 @@ const Maps* maps_for(const pn_handle* h, const void* x) {
 }
 
 template <int N, int MODE>
-cudaError_t launch_n(const Maps& m, const Args& a, dim3 grid, cudaStream_t s, bool pdl) {
+cudaError_t launch_n(const Maps& m, const Maps& ms, const Args& a, dim3 grid, cudaStream_t s, bool pdl) {
     auto kern = k_apply_tma<N, MODE>;
     static std::atomic<unsigned long long> configured{0};
     const size_t bytes = smem_bytes(N);
     cudaError_t e = pn_smem_attr_once(configured, reinterpret_cast<const void*>(kern), int(bytes));
     if (e != cudaSuccess) return e;
-    return launch_pdl(pdl, kern, grid, dim3(TX, NG, TY), bytes, s, m, a);
+    return launch_pdl(pdl, kern, grid, dim3(TX, NG, TY), bytes, s, m, ms, a);
 }
 
 template <int MODE>
-cudaError_t launch_mode(const pn_handle* h, const Maps& m, const Args& a, dim3 grid, cudaStream_t s) {
+cudaError_t launch_mode(const pn_handle* h, const Maps& m, const Maps& ms, const Args& a, dim3 grid,
+                        cudaStream_t s) {
     const bool pdl = h->pdl != 0;
     switch (h->N) {
-        case 0: return launch_n<0, MODE>(m, a, grid, s, pdl);
-        case 1: return launch_n<1, MODE>(m, a, grid, s, pdl);
-        case 2: return launch_n<2, MODE>(m, a, grid, s, pdl);
-        case 3: return launch_n<3, MODE>(m, a, grid, s, pdl);
-        case 4: return launch_n<4, MODE>(m, a, grid, s, pdl);
-        case 5: return launch_n<5, MODE>(m, a, grid, s, pdl);
-        case 6: return launch_n<6, MODE>(m, a, grid, s, pdl);
-        default: return launch_n<7, MODE>(m, a, grid, s, pdl);
+        case 0: return launch_n<0, MODE>(m, ms, a, grid, s, pdl);
+        case 1: return launch_n<1, MODE>(m, ms, a, grid, s, pdl);
+        case 2: return launch_n<2, MODE>(m, ms, a, grid, s, pdl);
+        case 3: return launch_n<3, MODE>(m, ms, a, grid, s, pdl);
+        case 4: return launch_n<4, MODE>(m, ms, a, grid, s, pdl);
+        case 5: return launch_n<5, MODE>(m, ms, a, grid, s, pdl);
+        case 6: return launch_n<6, MODE>(m, ms, a, grid, s, pdl);
+        default: return launch_n<7, MODE>(m, ms, a, grid, s, pdl);
     }
 }
 
@@ -476,10 +541,18 @@ bool tma_serves(const pn_handle* h) {
 
 cudaError_t launch_tma_main(const pn_handle* h, int mode, const tiled::Args& a, dim3 grid, cudaStream_t s) {
     if (!tma_serves(h)) return cudaErrorNotSupported;
-    const tma::Maps* m = tma::maps_for(h, a.x);
+    const tma::Maps* m = tma::maps_for(h, a.x, false);
     if (!m) return cudaErrorInvalidValue;
-    if (mode == OP_RESIDUAL) return tma::launch_mode<OP_RESIDUAL>(h, *m, a, grid, s);
-    return tma::launch_mode<OP_APPLY>(h, *m, a, grid, s);
+    const tma::Maps* ms = m;  // unused below order 6
+    if (h->N >= 6) {
+        // the output's maps (the tile store needs a 16-byte aligned, padded y)
+        ms = tma::maps_for(h, a.y, true);
+        if (!ms) return cudaErrorInvalidValue;
+        m = tma::maps_for(h, a.x, false);  // (the cache may have moved the entry)
+        if (!m) return cudaErrorInvalidValue;
+    }
+    if (mode == OP_RESIDUAL) return tma::launch_mode<OP_RESIDUAL>(h, *m, *ms, a, grid, s);
+    return tma::launch_mode<OP_APPLY>(h, *m, *ms, a, grid, s);
 }
 
 void tma_cache_free(pn_handle* h) {
