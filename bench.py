@@ -820,6 +820,17 @@ def run_batched(args):
             times.append(ms)
     its = [st["iterations"] for st in stats]
     ok = sum(1 for st in stats if st["status"] == 0)
+    solo_min = 1 << 21  # the library's default: instances at least this large are solved one by one
+    n_solo = sum(1 for s in systems if s.layout.n_active >= solo_min)
+    # the same batch with every instance in the batched launches
+    batch.set_solo(0)
+    all_times = []
+    for it in range(1 + max(1, args.steps // 2)):
+        us = [s.zeros(torch.float64) for s in systems]
+        ms_all, _ = timed(lambda: batch.solve(us, tol=1e-6, max_iter=200000, raise_on_error=False))
+        if it >= 1:
+            all_times.append(ms_all)
+    batch.set_solo(solo_min)
 
     def one_by_one():
         out = []
@@ -841,7 +852,9 @@ def run_batched(args):
         "launches": stats[0]["launches"], "tiling": tiling,
         "one_by_one_ms": seq_ms, "one_by_one_converged": sum(1 for st in seq_stats if st["status"] == 0),
         "one_by_one_launches": int(sum(st["launches"] for st in seq_stats)),
-        "speedup_vs_one_by_one": seq_ms / best, "steps": args.steps, "warmup": args.warmup}), flush=True)
+        "speedup_vs_one_by_one": seq_ms / best, "solo_min_unknowns": solo_min, "solo_instances": n_solo,
+        "all_batched_ms": min(all_times), "all_batched_speedup_vs_one_by_one": seq_ms / min(all_times),
+        "steps": args.steps, "warmup": args.warmup}), flush=True)
     batch.close()
     for s in systems:
         s.close()

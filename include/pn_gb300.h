@@ -466,6 +466,12 @@ int pn_batch_get_tiling(const pn_batch* batch, int64_t* op_chunk, int64_t* vec_c
                         int* vec_ctas_per_sm);
 int pn_batch_tune(pn_batch* batch, void* stream);
 int pn_batch_set_mode(pn_batch* batch, int mode, long long spin_limit);
+/* Instances with at least min_unknowns unknowns fill the GPU alone and gain
+ * nothing from sharing launches: pn_batch_solve solves them first, one after
+ * another, with pn_solve (the same FP64 refinement around FP32 GMRES with one
+ * Gram-Schmidt pass and the batch's restart), and the rest together in the
+ * batched launches.  Default 2^21; min_unknowns <= 0 batches every instance. */
+int pn_batch_set_solo(pn_batch* batch, long long min_unknowns);
 int pn_batch_barrier_test(int blocks, int expected, long long spin_limit, int* timed_out, void* stream);
 /* Arnoldi-step operator of the graph mode: 1 = every 3D instance the tiled
  * FP32 kernel serves gets its own gated launch on one of eight side streams

@@ -697,6 +697,9 @@ struct pn_batch {
     cudaStream_t s = nullptr;
     cudaGraphExec_t cycle = nullptr;
     int mode = 0;                   // PN_BATCH_GRAPH or PN_BATCH_PERSISTENT
+    // instances with at least this many unknowns fill the GPU alone: pn_batch_solve
+    // solves them one after another with pn_solve (<= 0: none)
+    int64_t solo_min = int64_t(1) << 21;
     int use_tiled = 1;              // Arnoldi-step operator: per-instance tiled launches on graph branches
     int n_tiled = 0, n_generic = 0;
     static constexpr int NSIDE = 8;
@@ -1134,6 +1137,12 @@ int pn_batch_set_tiling(pn_batch* b, int64_t op_chunk, int64_t vec_chunk, int op
     return build_lists(b);
 }
 
+int pn_batch_set_solo(pn_batch* b, long long min_unknowns) {
+    if (!b) return PN_ERR_ARG;
+    b->solo_min = int64_t(min_unknowns);
+    return PN_OK;
+}
+
 int pn_batch_set_mode(pn_batch* b, int mode, long long spin_limit) {
     if (!b) return PN_ERR_ARG;
     if ((mode != PN_BATCH_GRAPH && mode != PN_BATCH_PERSISTENT) || spin_limit < 1)
@@ -1376,9 +1385,32 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     std::vector<int> inner(n, 0), outer(n, 0), status(n, PN_OK);
     std::vector<double> rel(n, 0.0);
     int64_t launches = 0;
+    // Instances large enough to fill the GPU alone (b->solo_min unknowns) gain
+    // nothing from sharing launches: they are solved first, one after another,
+    // by pn_solve with the same refinement and inner GMRES (FP32 basis, one
+    // Gram-Schmidt pass, the batch's restart), and left out of the batched
+    // launches (marked done).
+    std::vector<char> solo(n, 0);
+    std::vector<pn_solve_stats> solo_st(n);
+    for (int i = 0; i < n; ++i) {
+        if (b->solo_min <= 0 || b->hs[i]->n_active < b->solo_min) continue;
+        solo[i] = 1;
+        pn_solve_opts os = o;
+        os.solver = PN_SOLVER_IR_GMRES;
+        os.basis = PN_BASIS_F32;
+        os.ortho = PN_ORTHO_CGS1;
+        os.augment = 0;
+        os.profile = 0;
+        os.precond = nullptr;
+        std::memset(&solo_st[i], 0, sizeof(pn_solve_stats));
+        const int r = pn_solve(b->hs[i], u[i], &os, &solo_st[i], b->s);
+        solo_st[i].status = r;
+        launches += solo_st[i].launches;
+    }
     for (int i = 0; i < n; ++i) {
         BState& S = b->h_state[i];
         std::memset(&S, 0, sizeof(BState));
+        S.done = solo[i];
     }
     rc = write_state(b);
     if (rc != PN_OK) return rc;
@@ -1481,10 +1513,15 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     for (int i = 0; i < n; ++i) {
         pn_solve_stats& st = stats[i];
         std::memset(&st, 0, sizeof(st));
-        st.status = status[i];
-        st.iterations = inner[i];
-        st.outer_iterations = outer[i];
-        st.rel_residual = rel[i];
+        if (solo[i]) {
+            st = solo_st[i];
+            status[i] = st.status;
+        } else {
+            st.status = status[i];
+            st.iterations = inner[i];
+            st.outer_iterations = outer[i];
+            st.rel_residual = rel[i];
+        }
         st.seconds = secs;
         st.launches = launches;
         if (status[i] != PN_OK && worst == PN_OK) worst = status[i];

@@ -52,7 +52,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
            "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels",
            "pn_get_workspace", "pn_wait_timeout_test", "pn_set_pdl", "pn_cnn_set_conv_kernel",
-           "pn_cnn_take_error", "pn_fma_peak"]
+           "pn_cnn_take_error", "pn_fma_peak", "pn_batch_set_solo"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -153,6 +153,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_cnn_set_conv_kernel": (i, [vp, i]),
         "pn_cnn_take_error": (i, [vp]),
         "pn_fma_peak": (i, [i, ctypes.POINTER(d), vp]),
+        "pn_batch_set_solo": (i, [vp, ctypes.c_longlong]),
         "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
         "pn_batch_get_op_path": (i, [vp, ctypes.POINTER(i)]),
@@ -660,6 +661,11 @@ class Batch:
 
     def set_op_path(self, tiled: bool):
         self._check(self._lib.pn_batch_set_op_path(self._h, 1 if tiled else 0))
+
+    def set_solo(self, min_unknowns: int):
+        """Instances with at least min_unknowns unknowns are solved one by one
+        (pn_solve) inside solve(); <= 0: every instance batched."""
+        self._check(self._lib.pn_batch_set_solo(self._h, int(min_unknowns)))
 
     def set_mode(self, persistent: bool, spin_limit: int = 1 << 24):
         """persistent=True: one cooperative launch per restart cycle with

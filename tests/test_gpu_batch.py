@@ -233,3 +233,31 @@ def test_batched_exact_eigenvector_breakdown():
     batch.close()
     s0.close()
     s1.close()
+
+
+def test_solo_instances_solved_one_by_one_inside_the_batch():
+    """With a solo threshold between the instances' sizes, the larger ones are
+    solved one after another by pn_solve inside pn_batch_solve and the rest by
+    the batched launches: every instance meets the oracle residual 1e-6, and a
+    solo instance's solution is bitwise the single-system solve with the same
+    options (FP64 refinement around FP32 GMRES(m), one Gram-Schmidt pass)."""
+    from paper_1807_00410_gb300 import Batch
+    systems, descs = zip(*[_instance(*c) for c in MIXED])
+    sizes = [s.layout.n_active for s in systems]
+    thr = sorted(sizes)[len(sizes) // 2]
+    batch = Batch(systems, restart=8)
+    batch.set_solo(thr)
+    us = [s.zeros(torch.float64) for s in systems]
+    stats = batch.solve(us, tol=1e-6, max_iter=20000)
+    for s, d, u, st in zip(systems, descs, us, stats):
+        assert st["status"] == 0
+        lay, A, b = _oracle(d)
+        assert opn.relative_residual(A, b, lay.join(s.to_planes(u))) <= 1.0001e-6
+    for s, u, n in zip(systems, us, sizes):
+        if n >= thr:
+            ref = s.zeros(torch.float64)
+            s.solve(ref, solver="ir", tol=1e-6, restart=8, ortho="cgs1", max_iter=20000)
+            assert torch.equal(u, ref)
+    batch.close()
+    for s in systems:
+        s.close()
