@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--batch-seed", type=int, default=0)
     ap.add_argument("--batch-rmin", type=int, default=24)
     ap.add_argument("--batch-rmax", type=int, default=96)
+    ap.add_argument("--network-only", action="store_true",
+                    help="time the learned preconditioner's network (P3: 19 input, 16 output channels): forward at "
+                         "64^3 and a training step (batch 8 at 32^3) with the tcgen05 and the mma.sync convolutions")
     ap.add_argument("--large-solve", action="store_true",
                     help="the P7 256^3 cloud (1.08 G unknowns) solved by FP16-basis refinement, capped at "
                          "--large-iters inner iterations: time per iteration and the residual reached")
@@ -860,6 +863,45 @@ def run_batched(args):
         s.close()
 
 
+def run_network_only(args):
+    """The network alone: W warm-up and K timed forwards (batch 1 at 64^3, the
+    preconditioner's size) and training steps (batch 8 at 32^3: forward,
+    backward, Adam), CUDA events, for each convolution kernel."""
+    import torch
+
+    from paper_1807_00410_gb300 import Net
+    from paper_1807_00410_gb300 import learned as L
+    torch.cuda.set_device(0)
+    K = 16
+    net = Net(K + 3, K)
+    net.set_params(L.init_params(K + 3, K, seed=1))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    out = {}
+    for kern in ("tcgen05", "mma_sync"):
+        net.set_conv_kernel(kern)
+        row = {}
+        for what, (B, R) in (("forward", (1, 64)), ("train_step", (8, 32))):
+            x = torch.randn((B, R, R, R, K + 3), device="cuda", generator=g)
+            t = torch.randn((B, R, R, R, K), device="cuda", generator=g)
+            fn = (lambda: net.forward(x)) if what == "forward" else (lambda: net.train_step(x, t, 1e-4))
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                fn()
+            e1.record()
+            e1.synchronize()
+            row[what + "_ms"] = e0.elapsed_time(e1) / args.steps
+        out[kern] = row
+    net.take_error()
+    net.close()
+    print(json.dumps({"mode": "network-only", "network": "U-Net 4 levels, widths 16/32/48/64, c_in 19, c_out 16",
+                      "forward": "batch 1 at 64^3", "train_step": "batch 8 at 32^3 (forward, backward, Adam)",
+                      "kernels": out, "steps": args.steps, "warmup": args.warmup}), flush=True)
+
+
 def run_large_solve(args):
     """Full-size solve on the P7 256^3 thresholded-fBm cloud (albedo 0.99,
     g 0.6, sigma_t_min --large-sigma-min, seeded point source): IR with the
@@ -898,6 +940,9 @@ def run_large_solve(args):
 
 def main():
     args = parse()
+    if args.network_only:
+        run_network_only(args)
+        return
     if args.large_solve:
         run_large_solve(args)
         return
