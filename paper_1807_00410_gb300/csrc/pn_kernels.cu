@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_op_f64(OpArgs<double> a, const double* 
             const int64_t s = row + x;
             double out = 0.0;
             if (rowact && x < R + px) {
-                const double diag = fma(-fl, cms[s], cmt[s]);
+                const double diag = fma_rn(-fl, cms[s], cmt[s]);  // op_point's rounding, step for step
                 double tr = 0.0;
                 for (int ti = 0; ti < nt; ++ti) {
                     const Term tm = ts[ti];
@@ -189,13 +189,13 @@ __global__ void __launch_bounds__(256) k_op_f64(OpArgs<double> a, const double* 
                     const int64_t qb = int64_t(tm.q) * a.plane_stride + s;
                     const double vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : 0.0;
                     const double vm = (i - b >= 0) ? a.x[qb - b * stride] : 0.0;
-                    tr = fma(tm.cd, vp - vm, tr);
+                    tr = fma_rn(tm.cd, sub_rn(vp, vm), tr);
                 }
-                const double own = diag * a.x[pbase + s];
-                out = MODE == OP_APPLY_T ? own - tr : own + tr;
+                const double own = mul_rn(diag, a.x[pbase + s]);
+                out = MODE == OP_APPLY_T ? sub_rn(own, tr) : add_rn(own, tr);
                 if (MODE == OP_RESIDUAL) {
                     const double bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : 0.0);
-                    out = bq - out;
+                    out = sub_rn(bq, out);
                     racc = fma(out, out, racc);
                 }
             }

@@ -37,6 +37,18 @@ template <typename T> __device__ __forceinline__ T plane_fl(const Plane& p);
 template <> __device__ __forceinline__ float plane_fl<float>(const Plane& p) { return p.fl_f; }
 template <> __device__ __forceinline__ double plane_fl<double>(const Plane& p) { return p.fl_d; }
 
+// Rounding of each step pinned (no contraction left to the compiler), so that
+// every kernel that forms an output from the same inputs -- this per-point
+// form, the FP64 class-mean kernel -- gets the same bits.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 // Mean of a centre field over the in-domain voxel centres adjacent to slot
 // (x, y, z) of a grid with parity bits (px, py, pz).  Along an odd axis the
 // candidates are slots i-1 and i; clamping both into [0, R) repeats the single
@@ -71,11 +83,11 @@ template <typename T, int MODE>
 __device__ __forceinline__ T op_point(const OpArgs<T>& a, int p, const Plane& P, int x, int y, int z, int64_t s) {
     const int R = a.R;
     const int64_t pbase = int64_t(p) * a.plane_stride;
-    const T diag = a.periodic ? centre_mean_periodic(a.st, R, x, y, z, P.px, P.py, P.pz) -
-                                    plane_fl<T>(P) * centre_mean_periodic(a.ss, R, x, y, z, P.px, P.py, P.pz)
-                              : centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz) -
-                                    plane_fl<T>(P) * centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz);
-    T acc = diag * a.x[pbase + s];
+    const T diag = a.periodic ? fma_rn(-plane_fl<T>(P), centre_mean_periodic(a.ss, R, x, y, z, P.px, P.py, P.pz),
+                                       centre_mean_periodic(a.st, R, x, y, z, P.px, P.py, P.pz))
+                              : fma_rn(-plane_fl<T>(P), centre_mean(a.ss, R, x, y, z, P.px, P.py, P.pz),
+                                       centre_mean(a.st, R, x, y, z, P.px, P.py, P.pz));
+    T acc = mul_rn(diag, a.x[pbase + s]);
     T tr = T(0);
     for (int ti = P.t0; ti < P.t1; ++ti) {
         const Term tm = a.terms[ti];
@@ -96,12 +108,12 @@ __device__ __forceinline__ T op_point(const OpArgs<T>& a, int p, const Plane& P,
             vp = (i + 1 - b < R + 1 - b) ? a.x[qb + (1 - b) * stride] : T(0);
             vm = (i - b >= 0) ? a.x[qb - b * stride] : T(0);
         }
-        tr += term_coef<T>(tm) * (vp - vm);
+        tr = fma_rn(term_coef<T>(tm), sub_rn(vp, vm), tr);
     }
-    acc = (MODE == OP_APPLY_T) ? acc - tr : acc + tr;
+    acc = (MODE == OP_APPLY_T) ? sub_rn(acc, tr) : add_rn(acc, tr);
     if (MODE == OP_RESIDUAL) {
         const T bq = a.bvec ? a.bvec[pbase + s] : ((p < a.n_q) ? a.q[pbase + s] : T(0));
-        return bq - acc;
+        return sub_rn(bq, acc);
     }
     return acc;
 }
