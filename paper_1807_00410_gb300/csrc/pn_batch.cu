@@ -700,6 +700,7 @@ struct pn_batch {
     // instances with at least this many unknowns fill the GPU alone: pn_batch_solve
     // solves them one after another with pn_solve (<= 0: none)
     int64_t solo_min = int64_t(1) << 21;
+    int64_t graph_solo = -1;        // solo_min the captured cycle was built for (its tiled launches skip solo instances)
     int use_tiled = 1;              // Arnoldi-step operator: per-instance tiled launches on graph branches
     int n_tiled = 0, n_generic = 0;
     static constexpr int NSIDE = 8;
@@ -869,7 +870,11 @@ void launch_cycle(pn_batch* b, const std::vector<char>* running = nullptr) {
     kb_update<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv);
 }
 
-int ensure_graph(pn_batch* b) {
+// The captured restart cycle.  `members` (or null: every instance) selects the
+// instances that get a tiled operator launch in it; the others (the ones
+// pn_batch_solve hands to pn_solve) are left out instead of being launched
+// gated in every Arnoldi step.
+int ensure_graph(pn_batch* b, const std::vector<char>* members = nullptr) {
     if (b->cycle) return PN_OK;
     if (b->use_tiled && b->n_tiled > 0) {
         // one gated launch per tiled instance outside the capture (a device 0
@@ -884,7 +889,7 @@ int ensure_graph(pn_batch* b) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "pn_batch: begin capture");
-    launch_cycle(b);
+    launch_cycle(b, members);
     const cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(b->s, &graph);
     if (le != cudaSuccess) {
@@ -1379,9 +1384,21 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     if (e != cudaSuccess) return bcuda(b, e, "pn_batch_solve");
     e = cudaMemcpyAsync(b->d_ptrs + p_x(b), u, size_t(b->n) * sizeof(void*), cudaMemcpyHostToDevice, b->s);
     if (e != cudaSuccess) return bcuda(b, e, "pn_batch_solve");
-    int rc = b->mode == PN_BATCH_GRAPH ? ensure_graph(b) : PN_OK;
-    if (rc != PN_OK) return rc;
     const int n = b->n;
+    // the instances pn_solve takes (b->solo_min unknowns or more; see below)
+    std::vector<char> solo(n, 0), members(n, 1);
+    for (int i = 0; i < n; ++i)
+        if (b->solo_min > 0 && b->hs[i]->n_active >= b->solo_min) {
+            solo[i] = 1;
+            members[i] = 0;
+        }
+    if (b->cycle && b->graph_solo != b->solo_min) {
+        cudaGraphExecDestroy(b->cycle);
+        b->cycle = nullptr;
+    }
+    int rc = b->mode == PN_BATCH_GRAPH ? ensure_graph(b, &members) : PN_OK;
+    if (rc != PN_OK) return rc;
+    b->graph_solo = b->solo_min;
     std::vector<int> inner(n, 0), outer(n, 0), status(n, PN_OK);
     std::vector<double> rel(n, 0.0);
     int64_t launches = 0;
@@ -1390,11 +1407,9 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     // by pn_solve with the same refinement and inner GMRES (FP32 basis, one
     // Gram-Schmidt pass, the batch's restart), and left out of the batched
     // launches (marked done).
-    std::vector<char> solo(n, 0);
     std::vector<pn_solve_stats> solo_st(n);
     for (int i = 0; i < n; ++i) {
-        if (b->solo_min <= 0 || b->hs[i]->n_active < b->solo_min) continue;
-        solo[i] = 1;
+        if (!solo[i]) continue;
         pn_solve_opts os = o;
         os.solver = PN_SOLVER_IR_GMRES;
         os.basis = PN_BASIS_F32;
