@@ -470,7 +470,7 @@ int pn_batch_set_mode(pn_batch* batch, int mode, long long spin_limit);
  * nothing from sharing launches: pn_batch_solve solves them first, one after
  * another, with pn_solve (the same FP64 refinement around FP32 GMRES with one
  * Gram-Schmidt pass and the batch's restart), and the rest together in the
- * batched launches.  Default 2^21; min_unknowns <= 0 batches every instance. */
+ * batched launches.  Default 2^18; min_unknowns <= 0 batches every instance. */
 int pn_batch_set_solo(pn_batch* batch, long long min_unknowns);
 int pn_batch_barrier_test(int blocks, int expected, long long spin_limit, int* timed_out, void* stream);
 /* Arnoldi-step operator of the graph mode: 1 = every 3D instance the tiled

@@ -699,7 +699,7 @@ struct pn_batch {
     int mode = 0;                   // PN_BATCH_GRAPH or PN_BATCH_PERSISTENT
     // instances with at least this many unknowns fill the GPU alone: pn_batch_solve
     // solves them one after another with pn_solve (<= 0: none)
-    int64_t solo_min = int64_t(1) << 21;
+    int64_t solo_min = int64_t(1) << 18;
     int64_t graph_solo = -1;        // solo_min the captured cycle was built for (its tiled launches skip solo instances)
     int use_tiled = 1;              // Arnoldi-step operator: per-instance tiled launches on graph branches
     int n_tiled = 0, n_generic = 0;
