@@ -100,19 +100,16 @@ __device__ __forceinline__ void compute_class(const Args& a, const float* buf, i
 #pragma unroll
     for (int i = 0; i < MAXC; ++i) {
         if (i < CT.n) {
-            // one partial sum per axis (three short dependency chains instead
-            // of one long one), added in a fixed order
-            float trx = 0.0f, try_ = 0.0f, trz = 0.0f;
+            float tr = 0.0f;
 #pragma unroll
             for (int t = 0; t < MAXT; ++t)
-                if (t < CT.row[i].nt[0]) trx = fmaf(CT.row[i].c[0][t], dx[CT.row[i].j[0][t]], trx);
+                if (t < CT.row[i].nt[0]) tr = fmaf(CT.row[i].c[0][t], dx[CT.row[i].j[0][t]], tr);
 #pragma unroll
             for (int t = 0; t < MAXT; ++t)
-                if (t < CT.row[i].nt[1]) try_ = fmaf(CT.row[i].c[1][t], dy[CT.row[i].j[1][t]], try_);
+                if (t < CT.row[i].nt[1]) tr = fmaf(CT.row[i].c[1][t], dy[CT.row[i].j[1][t]], tr);
 #pragma unroll
             for (int t = 0; t < MAXT; ++t)
-                if (t < CT.row[i].nt[2]) trz = fmaf(CT.row[i].c[2][t], dz[CT.row[i].j[2][t]], trz);
-            const float tr = __fadd_rn(__fadd_rn(trx, try_), trz);
+                if (t < CT.row[i].nt[2]) tr = fmaf(CT.row[i].c[2][t], dz[CT.row[i].j[2][t]], tr);
             const float d = fmaf(-a.fl[CT.row[i].l], ss, st);
             float out = fmaf(d, own[i], tscale * tr);
             if (MODE == OP_RESIDUAL) {
