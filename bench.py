@@ -824,8 +824,10 @@ def run_batched(args):
     ok = sum(1 for st in stats if st["status"] == 0)
     solo_min = 1 << 18  # the library's default: instances at least this large are solved one by one
     n_solo = sum(1 for s in systems if s.layout.n_active >= solo_min)
-    # the same batch with every instance in the batched launches
+    # the same batch with every instance in the batched launches (tiling
+    # re-tuned for that set)
     batch.set_solo(0)
+    batch.tune()
     all_times = []
     for it in range(1 + max(1, args.steps // 2)):
         us = [s.zeros(torch.float64) for s in systems]

@@ -438,7 +438,9 @@ int pn_cnn_precondition(pn_handle* h, pn_cnn* net, const float* v, float* z, voi
  * chunk {4096, 16384, 65536} x {2, 4, 8} CTAs per SM, the per-instance tiled
  * operator path against the best of those, and the Arnoldi vector kernels
  * over vector chunk {16384, 65536, 262144} x {2, 4, 8}, on this batch, and
- * keeps the fastest of each (pn_batch_get_tiling, pn_batch_get_op_path).
+ * keeps the fastest of each (pn_batch_get_tiling, pn_batch_get_op_path).  It
+ * times the instances the batched launches take under the current solo
+ * threshold (pn_batch_set_solo), so call it after changing that threshold.
  * pn_batch_set_mode: PN_BATCH_GRAPH (default) replays the captured cycle;
  * PN_BATCH_PERSISTENT runs each cycle as ONE cooperative launch (a grid of
  * resident CTAs, two per SM) whose phases are separated by grid barriers.
@@ -470,7 +472,9 @@ int pn_batch_set_mode(pn_batch* batch, int mode, long long spin_limit);
  * nothing from sharing launches: pn_batch_solve solves them first, one after
  * another, with pn_solve (the same FP64 refinement around FP32 GMRES with one
  * Gram-Schmidt pass and the batch's restart), and the rest together in the
- * batched launches.  Default 2^18; min_unknowns <= 0 batches every instance. */
+ * batched launches, whose work lists then hold no chunk of a solo instance
+ * (pn_batch_apply restores the full lists).  Default 2^18; min_unknowns <= 0
+ * batches every instance. */
 int pn_batch_set_solo(pn_batch* batch, long long min_unknowns);
 int pn_batch_barrier_test(int blocks, int expected, long long spin_limit, int* timed_out, void* stream);
 /* Arnoldi-step operator of the graph mode: 1 = every 3D instance the tiled

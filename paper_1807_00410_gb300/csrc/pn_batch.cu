@@ -701,6 +701,8 @@ struct pn_batch {
     // solves them one after another with pn_solve (<= 0: none)
     int64_t solo_min = int64_t(1) << 18;
     int64_t graph_solo = -1;        // solo_min the captured cycle was built for (its tiled launches skip solo instances)
+    bool lists_all = true;          // the work lists hold every instance (else the members of lists_solo)
+    int64_t lists_solo = 0;
     int use_tiled = 1;              // Arnoldi-step operator: per-instance tiled launches on graph branches
     int n_tiled = 0, n_generic = 0;
     static constexpr int NSIDE = 8;
@@ -734,15 +736,24 @@ inline size_t p_ax(const pn_batch* b) { return p_x(b) + b->n; }   // apply: inpu
 inline size_t p_ay(const pn_batch* b) { return p_ax(b) + b->n; }   // apply: outputs
 inline size_t p_total(const pn_batch* b) { return p_ay(b) + b->n; }
 
-int build_lists(pn_batch* b) {
+// The operator and vector work lists (chunks of every instance, or of the
+// instances `members` selects: the others get empty ranges and no chunks).
+int build_lists(pn_batch* b, const std::vector<char>* members = nullptr) {
     b->opc.clear();
     b->vc.clear();
     b->oc_first.assign(b->n, 0);
     b->oc_count.assign(b->n, 0);
     b->vc_first.assign(b->n, 0);
     b->vc_count.assign(b->n, 0);
+    b->lists_all = members == nullptr;
+    b->lists_solo = members ? b->solo_min : 0;
     for (int i = 0; i < b->n; ++i) {
         const BInst& in = b->inst[i];
+        if (members && !(*members)[i]) {
+            b->oc_first[i] = int(b->opc.size());
+            b->vc_first[i] = int(b->vc.size());
+            continue;
+        }
         b->oc_first[i] = int(b->opc.size());
         for (int p = 0; p < in.K; ++p)
             for (int64_t s0 = 0; s0 < in.plane_stride; s0 += b->cho) b->opc.push_back(OpChunk{i, p, s0});
@@ -785,8 +796,10 @@ int build_lists(pn_batch* b) {
     counts.insert(counts.end(), b->oc_count.begin(), b->oc_count.end());
     counts.insert(counts.end(), b->vc_first.begin(), b->vc_first.end());
     counts.insert(counts.end(), b->vc_count.begin(), b->vc_count.end());
-    e = cudaMemcpy(b->d_opc, b->opc.data(), b->opc.size() * sizeof(OpChunk), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_vc, b->vc.data(), b->vc.size() * sizeof(VecChunk), cudaMemcpyHostToDevice);
+    if (!b->opc.empty())
+        e = cudaMemcpy(b->d_opc, b->opc.data(), b->opc.size() * sizeof(OpChunk), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !b->vc.empty())
+        e = cudaMemcpy(b->d_vc, b->vc.data(), b->vc.size() * sizeof(VecChunk), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_counts, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bcuda(b, e, "pn_batch: uploading work lists");
@@ -1216,10 +1229,21 @@ int pn_batch_tune(pn_batch* b, void* stream) {
     if (!b) return PN_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return bcuda(b, e, "pn_batch_tune");
-    // every instance live for the timing; the basis holds whatever it holds
+    // the instances of the batched launches under the current solo threshold
+    // (pn_batch_solve hands the others to pn_solve): the tiling is chosen for
+    // the work lists those launches sweep
+    std::vector<char> members(b->n, 1);
+    int n_members = b->n;
+    for (int i = 0; i < b->n; ++i)
+        if (b->solo_min > 0 && b->hs[i]->n_active >= b->solo_min) {
+            members[i] = 0;
+            --n_members;
+        }
+    const std::vector<char>* mem = (n_members > 0 && n_members < b->n) ? &members : nullptr;
+    // every member live for the timing; the basis holds whatever it holds
     for (int i = 0; i < b->n; ++i) {
         std::memset(&b->h_state[i], 0, sizeof(BState));
-        b->h_state[i].run = b->h_state[i].live = 1;
+        b->h_state[i].run = b->h_state[i].live = (mem == nullptr || members[i]) ? 1 : 0;
     }
     int rc = write_state(b);
     if (rc != PN_OK) return rc;
@@ -1244,7 +1268,7 @@ int pn_batch_tune(pn_batch* b, void* stream) {
             } else if (what == 2) {
                 const int keep = b->use_tiled;
                 b->use_tiled = 1;
-                launch_step_apply(b, 0, live.data());
+                launch_step_apply(b, 0, live.data(), mem);
                 b->use_tiled = keep;
             } else {
                 kb_mdot<<<gv, 256, 0, b->s>>>(b->d_inst, b->d_state, b->d_vc, nch, b->chv, jmid, b->d_part_vec);
@@ -1280,7 +1304,7 @@ int pn_batch_tune(pn_batch* b, void* stream) {
         for (int mu : mults) {
             b->cho = oc;
             b->op_mult = mu;
-            if ((rc = build_lists(b)) != PN_OK) break;
+            if ((rc = build_lists(b, mem)) != PN_OK) break;
             const float t = time_it(1);
             if (t < 0.0f) {
                 rc = bcuda(b, cudaGetLastError(), "pn_batch_tune");
@@ -1294,7 +1318,7 @@ int pn_batch_tune(pn_batch* b, void* stream) {
         }
     b->cho = bo;
     b->op_mult = bmo;
-    if (rc == PN_OK && (rc = build_lists(b)) == PN_OK && b->n_tiled > 0) {
+    if (rc == PN_OK && (rc = build_lists(b, mem)) == PN_OK && b->n_tiled > 0) {
         // the Arnoldi-step operator: per-instance tiled launches vs the generic launch
         const float tt = time_it(2);
         if (tt < 0.0f) rc = bcuda(b, cudaGetLastError(), "pn_batch_tune");
@@ -1305,7 +1329,7 @@ int pn_batch_tune(pn_batch* b, void* stream) {
         for (int mu : mults) {
             b->chv = vcn;
             b->vec_mult = mu;
-            if ((rc = build_lists(b)) != PN_OK) break;
+            if ((rc = build_lists(b, mem)) != PN_OK) break;
             const float t = time_it(0);
             if (t < 0.0f) {
                 rc = bcuda(b, cudaGetLastError(), "pn_batch_tune");
@@ -1322,7 +1346,7 @@ int pn_batch_tune(pn_batch* b, void* stream) {
     cudaEventDestroy(e1);
     b->chv = bv;
     b->vec_mult = bmv;
-    const int rc2 = build_lists(b);
+    const int rc2 = build_lists(b, mem);
     std::memset(b->h_state, 0, size_t(b->n) * sizeof(BState));
     const int rc3 = write_state(b);
     e = cudaStreamSynchronize(b->s);
@@ -1341,6 +1365,13 @@ int pn_batch_apply(pn_batch* b, const void* const* x, void* const* y, int dtype,
             return bfail(b, PN_ERR_ARG, "pn_batch_apply: vectors must be 16-byte aligned");
     }
     cudaStream_t us = (cudaStream_t)stream;
+    if (!b->lists_all) {
+        // the last solve left the solo instances out of the work lists
+        const cudaError_t es = cudaStreamSynchronize(b->s);
+        if (es != cudaSuccess) return bcuda(b, es, "pn_batch_apply");
+        const int rl = build_lists(b);
+        if (rl != PN_OK) return rl;
+    }
     // the pointer arrays are batch-owned: order after earlier work on b->s
     std::vector<const void*> p(2 * size_t(b->n));
     for (int i = 0; i < b->n; ++i) {
@@ -1387,16 +1418,26 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     const int n = b->n;
     // the instances pn_solve takes (b->solo_min unknowns or more; see below)
     std::vector<char> solo(n, 0), members(n, 1);
+    int n_members = n;  // instances of the batched launches
     for (int i = 0; i < n; ++i)
         if (b->solo_min > 0 && b->hs[i]->n_active >= b->solo_min) {
             solo[i] = 1;
             members[i] = 0;
+            --n_members;
         }
     if (b->cycle && b->graph_solo != b->solo_min) {
         cudaGraphExecDestroy(b->cycle);
         b->cycle = nullptr;
     }
-    int rc = b->mode == PN_BATCH_GRAPH ? ensure_graph(b, &members) : PN_OK;
+    // work lists of the batched instances only: the kernels that sweep them
+    // (every Arnoldi step) then never visit a solo instance's chunks
+    int rc = PN_OK;
+    if (n_members < n && (b->lists_all || b->lists_solo != b->solo_min))
+        rc = build_lists(b, &members);
+    else if (n_members == n && !b->lists_all)
+        rc = build_lists(b);
+    if (rc != PN_OK) return rc;
+    rc = b->mode == PN_BATCH_GRAPH ? ensure_graph(b, &members) : PN_OK;
     if (rc != PN_OK) return rc;
     b->graph_solo = b->solo_min;
     std::vector<int> inner(n, 0), outer(n, 0), status(n, PN_OK);
@@ -1474,10 +1515,12 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
         for (;;) {
             int n_run = 0;
             for (int i = 0; i < n; ++i) n_run += b->h_state[i].run ? 1 : 0;
-            if (b->mode == PN_BATCH_GRAPH && 4 * n_run <= n && b->use_tiled && b->n_tiled > 0) {
-                // few instances left: launch this cycle directly, with tiled
-                // operator launches for the running instances only (the
-                // captured graph would launch every instance's, gated)
+            if (b->mode == PN_BATCH_GRAPH && 4 * n_run <= n_members && b->use_tiled && b->n_tiled > 0) {
+                // few of the batched instances left: launch this cycle
+                // directly, with tiled operator launches for the running
+                // instances only (the captured graph would launch every
+                // member's, gated).  The solo instances do not count: the
+                // graph has no launches of theirs.
                 std::vector<char> running(n);
                 for (int i = 0; i < n; ++i) running[i] = b->h_state[i].run ? 1 : 0;
                 launch_cycle(b, &running);

@@ -664,7 +664,9 @@ class Batch:
 
     def set_solo(self, min_unknowns: int):
         """Instances with at least min_unknowns unknowns are solved one by one
-        (pn_solve) inside solve(); <= 0: every instance batched."""
+        (pn_solve) inside solve(); <= 0: every instance batched.  tune()
+        chooses the tiling for the batched instances under this threshold:
+        call it again after changing the threshold."""
         self._check(self._lib.pn_batch_set_solo(self._h, int(min_unknowns)))
 
     def set_mode(self, persistent: bool, spin_limit: int = 1 << 24):

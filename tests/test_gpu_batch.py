@@ -258,6 +258,19 @@ def test_solo_instances_solved_one_by_one_inside_the_batch():
             ref = s.zeros(torch.float64)
             s.solve(ref, solver="ir", tol=1e-6, restart=8, ortho="cgs1", max_iter=20000)
             assert torch.equal(u, ref)
+    # the solve's work lists left the solo instances out: a batched apply
+    # afterwards still covers every instance
+    ys = [s.zeros(torch.float64) for s in systems]
+    batch.apply(us, ys)
+    for s, u, y in zip(systems, us, ys):
+        ref = s.zeros(torch.float64)
+        s.apply(u, ref)
+        assert torch.equal(y, ref)
+    # and a solve with every instance batched again meets the target
+    batch.set_solo(0)
+    us2 = [s.zeros(torch.float64) for s in systems]
+    for st in batch.solve(us2, tol=1e-6, max_iter=20000):
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-6
     batch.close()
     for s in systems:
         s.close()
