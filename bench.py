@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the FP32 operator on the P_N cloud medium given by --apply-n / --apply-r")
+    ap.add_argument("--access-probe", action="store_true",
+                    help="bandwidth of a plain copy with the tiled operator's access pattern (P7 and P5 plane "
+                         "counts at --apply-r^3) against tile shape and loads in flight, next to the operator")
     ap.add_argument("--threshold-sweep", action="store_true",
                     help="iterations / time to 1e-6 vs the sigma_t threshold on the 64^3 cloud medium")
     ap.add_argument("--checkerboard", action="store_true",
@@ -713,6 +716,30 @@ def run_apply_only(args):
     sysm.close()
 
 
+def run_access_probe(args):
+    """What DRAM delivers to the tiled operator's access pattern without its
+    arithmetic (pn_access_probe): copies of 64 and 36 planes (P7, P5) of an
+    --apply-r^3 grid by 512-thread CTAs marching column tiles through z, for
+    tile shapes 32 x 4, 64 x 2, 128 x 1 and 1, 2, 4 z-slices of loads in flight
+    per thread (32, 64, 128 KB per CTA at 64 planes), as fractions of the
+    measured copy peak."""
+    import torch
+
+    from paper_1807_00410_gb300 import pn as ppn
+    torch.cuda.set_device(0)
+    hbm_peak, peak_src = peaks()
+    rows = []
+    for planes in (64, 36):
+        for tile_x in (32, 64, 128):
+            for slices in (1, 2, 4):
+                gbs = ppn.access_probe(args.apply_r, planes, tile_x, slices)
+                rows.append({"planes": planes, "tile": f"{tile_x}x{128 // tile_x}", "slices_in_flight": slices,
+                             "kb_in_flight_per_cta": planes * slices // 2, "gb_s": round(gbs, 1),
+                             "frac": round(gbs / hbm_peak, 4)})
+    print(json.dumps({"mode": "access-probe", "R": args.apply_r, "peak": hbm_peak, "peak_source": peak_src,
+                      "rows": rows}), flush=True)
+
+
 def run_threshold_sweep(args):
     """Convergence against the extinction threshold (the paper clamps sigma_t
     from below because vacuum makes A singular, section "Nebulae"): IR solves
@@ -958,6 +985,9 @@ def main():
         return
     if args.apply_only:
         run_apply_only(args)
+        return
+    if args.access_probe:
+        run_access_probe(args)
         return
     if args.impl == "reference":
         run_reference(args)

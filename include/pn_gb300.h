@@ -587,6 +587,21 @@ int pn_set_pdl(pn_handle* h, int on);
  */
 int pn_fma_peak(int dtype, double* gflops_out, void* stream);
 
+/*
+ * Bandwidth of the tiled operator's memory access pattern without its
+ * arithmetic (a measurement aid; the paper has no counterpart): a copy of
+ * `planes` (4..64, a multiple of 4) coefficient planes of an R^3 grid (R in
+ * [128, 512], a multiple of tile_x) in the library's plane-major padded
+ * layout, by CTAs of 512 threads that march tiles of tile_x x (128 / tile_x)
+ * columns (tile_x in {32, 64, 128}) through z, each thread holding `slices`
+ * (1, 2 or 4) z-slices x planes / 4 loads in flight: with 64 planes, 32, 64
+ * or 128 KB in flight per CTA.  *gbs_out (host) = 2 x 4 x planes x R (R+1)^2
+ * bytes / the best of five timed copies, in GB/s.  Allocates two buffers of
+ * about planes x 4 (R+1)^3 bytes (PN_ERR_ALLOC if they do not fit) and two
+ * events; synchronises `stream`.  PN_ERR_ARG for arguments out of range.
+ */
+int pn_access_probe(int R, int planes, int tile_x, int slices, double* gbs_out, void* stream);
+
 /* Kernel classes reported by pn_profile_get. */
 #define PN_PROF_APPLY    0   /* pn_apply / pn_apply_t operator launches */
 #define PN_PROF_RESIDUAL 1   /* residual operator launches */

@@ -147,3 +147,122 @@ extern "C" int pn_fma_peak(int dtype, double* gflops_out, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return dtype == PN_F64 ? fma_peak<double>(gflops_out, s) : fma_peak<float>(gflops_out, s);
 }
+
+// ---- bandwidth of the operator's access pattern -------------------------------
+//
+// pn_access_probe: a copy of `planes` coefficient planes of a padded R^3 grid
+// in the library's plane-major layout, marching column tiles through z the way
+// the tiled operator does, with none of its arithmetic.  Each CTA of 512
+// threads (four groups of 128, like the operator's) owns a tile of tile_x x
+// (128 / tile_x) columns and a z chunk; thread (column, group g) copies planes
+// g, g + 4, ... at its column, SL z-slices at a time, so that every thread
+// has SL x planes / 4 loads in flight.  It measures what DRAM delivers to
+// this pattern -- rows of tile_x floats scattered over `planes` planes whose
+// starts lie (R + 1)^2 pitch_x floats apart -- as a function of the run
+// length and of the bytes in flight per SM.
+
+namespace {
+
+constexpr int kProbeThreads = 512;
+
+template <int SL, int WX>
+__global__ void __launch_bounds__(kProbeThreads, 1)
+    k_access_probe(const float* __restrict__ in, float* __restrict__ out, int R, int planes, int64_t pitch_x,
+                   int64_t pitch_y, int64_t plane_stride, int zc) {
+    constexpr int WY = 128 / WX;
+    const int g = threadIdx.y, lin = threadIdx.x + 32 * threadIdx.z;  // group, position within the tile
+    const int x = blockIdx.x * WX + lin % WX, y = blockIdx.y * WY + lin / WX;
+    const int za = blockIdx.z * zc, zb = min(za + zc, R + 1);
+    if (y > R) return;
+    const int np = (planes - g + 3) / 4;  // planes g, g + 4, ... below `planes`
+    for (int z = za; z < zb; z += SL) {
+        float v[SL][16];
+#pragma unroll
+        for (int d = 0; d < SL; ++d)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                v[d][j] = (j < np && z + d < zb)
+                              ? __ldg(in + (g + 4 * j) * plane_stride + (z + d) * pitch_y + y * pitch_x + x)
+                              : 0.0f;
+#pragma unroll
+        for (int d = 0; d < SL; ++d)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < np && z + d < zb) out[(g + 4 * j) * plane_stride + (z + d) * pitch_y + y * pitch_x + x] = v[d][j];
+    }
+}
+
+template <int SL, int WX>
+cudaError_t launch_probe(const float* in, float* out, int R, int planes, int64_t px, int64_t py, int64_t ps, int zc,
+                         cudaStream_t s) {
+    constexpr int WY = 128 / WX;
+    const dim3 grid(unsigned(R / WX), unsigned((R + 1 + WY - 1) / WY), unsigned((R + 1 + zc - 1) / zc));
+    k_access_probe<SL, WX><<<grid, dim3(32, 4, 4), 0, s>>>(in, out, R, planes, px, py, ps, zc);
+    return cudaGetLastError();
+}
+
+cudaError_t probe_once(int tile_x, int slices, const float* in, float* out, int R, int planes, int64_t px, int64_t py,
+                       int64_t ps, int zc, cudaStream_t s) {
+    switch (tile_x * 8 + slices) {
+        case 32 * 8 + 1: return launch_probe<1, 32>(in, out, R, planes, px, py, ps, zc, s);
+        case 32 * 8 + 2: return launch_probe<2, 32>(in, out, R, planes, px, py, ps, zc, s);
+        case 32 * 8 + 4: return launch_probe<4, 32>(in, out, R, planes, px, py, ps, zc, s);
+        case 64 * 8 + 1: return launch_probe<1, 64>(in, out, R, planes, px, py, ps, zc, s);
+        case 64 * 8 + 2: return launch_probe<2, 64>(in, out, R, planes, px, py, ps, zc, s);
+        case 64 * 8 + 4: return launch_probe<4, 64>(in, out, R, planes, px, py, ps, zc, s);
+        case 128 * 8 + 1: return launch_probe<1, 128>(in, out, R, planes, px, py, ps, zc, s);
+        case 128 * 8 + 2: return launch_probe<2, 128>(in, out, R, planes, px, py, ps, zc, s);
+        default: return launch_probe<4, 128>(in, out, R, planes, px, py, ps, zc, s);
+    }
+}
+
+}  // namespace
+
+extern "C" int pn_access_probe(int R, int planes, int tile_x, int slices, double* gbs_out, void* stream) {
+    if (!gbs_out || R < 128 || R > 512 || planes < 4 || planes > 64 || planes % 4 != 0 ||
+        (tile_x != 32 && tile_x != 64 && tile_x != 128) || (slices != 1 && slices != 2 && slices != 4) ||
+        R % tile_x != 0)
+        return PN_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the plane-major layout of a handle of this size: rows padded to 16
+    // bytes, planes padded to 256 bytes
+    const int64_t px = (int64_t(R) + 1 + 3) / 4 * 4;
+    const int64_t py = px * (R + 1);
+    const int64_t ps = (py * (R + 1) + 63) / 64 * 64;
+    const size_t n = size_t(planes) * size_t(ps);
+    float* in = nullptr;
+    float* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&in, n * sizeof(float)) != cudaSuccess || cudaMalloc(&out, n * sizeof(float)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (in) cudaFree(in);
+        if (out) cudaFree(out);
+        if (e0) cudaEventDestroy(e0);
+        return PN_ERR_ALLOC;
+    }
+    const int zc = (R + 1 + 3) / 4;  // four z chunks
+    cudaError_t e = cudaMemsetAsync(in, 0, n * sizeof(float), s);
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = probe_once(tile_x, slices, in, out, R, planes, px, py, ps, zc, s);
+    float best = 1e30f;
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = probe_once(tile_x, slices, in, out, R, planes, px, py, ps, zc, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) best = ms;
+    }
+    cudaFree(in);
+    cudaFree(out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PN_ERR_CUDA;
+    }
+    const double bytes = 2.0 * 4.0 * double(planes) * double(R) * double(R + 1) * double(R + 1);
+    *gbs_out = bytes / (double(best) * 1e-3) / 1e9;
+    return PN_OK;
+}

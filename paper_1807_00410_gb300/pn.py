@@ -52,7 +52,7 @@ EXPORTS = ["pn_create", "pn_create_2d", "pn_destroy", "pn_get_layout", "pn_last_
            "pn_set_apply_tiling", "pn_batch_set_op_path", "pn_batch_get_op_path", "pn_set_apply_kernel",
            "pn_get_apply_kernel", "pn_set_l2_residency", "pn_get_apply_plan", "pn_set_stream_kernels",
            "pn_get_workspace", "pn_wait_timeout_test", "pn_set_pdl", "pn_cnn_set_conv_kernel",
-           "pn_cnn_take_error", "pn_fma_peak", "pn_batch_set_solo"]
+           "pn_cnn_take_error", "pn_fma_peak", "pn_batch_set_solo", "pn_access_probe"]
 PROFILE_KINDS = ["apply", "residual", "mdot", "maxpy", "dot", "vector", "scalar", "precond"]
 
 
@@ -153,6 +153,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pn_cnn_set_conv_kernel": (i, [vp, i]),
         "pn_cnn_take_error": (i, [vp]),
         "pn_fma_peak": (i, [i, ctypes.POINTER(d), vp]),
+        "pn_access_probe": (i, [i, i, i, i, ctypes.POINTER(d), vp]),
         "pn_batch_set_solo": (i, [vp, ctypes.c_longlong]),
         "pn_get_apply_plan": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "pn_batch_set_op_path": (i, [vp, i]),
@@ -730,6 +731,18 @@ def fma_peak(dtype="f64", stream=None) -> float:
     rc = lib.pn_fma_peak(PN_F64 if dtype == "f64" else PN_F32, ctypes.byref(out), _stream_ptr(stream))
     if rc != PN_OK:
         raise PnError(rc, "pn_fma_peak failed")
+    return out.value
+
+
+def access_probe(R: int, planes: int, tile_x: int, slices: int, stream=None) -> float:
+    """pn_access_probe: GB/s of a copy with the tiled operator's access pattern
+    (tile_x x 128/tile_x column tiles marching in z over `planes` planes,
+    `slices` z-slices of loads in flight per thread)."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.pn_access_probe(int(R), int(planes), int(tile_x), int(slices), ctypes.byref(out), _stream_ptr(stream))
+    if rc != PN_OK:
+        raise PnError(rc, "pn_access_probe failed")
     return out.value
 
 

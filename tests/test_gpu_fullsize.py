@@ -135,3 +135,18 @@ def test_programmatic_dependent_launch_changes_no_bit():
     rel, _ = _oracle_residual(p, gpu, sols[0][0])
     assert rel <= 1.0001e-6
     gpu.close()
+
+
+def test_measurement_aids_report_plausible_rates():
+    """The FMA-peak and access-pattern microbenchmarks (roofline denominators
+    and the bandwidth ceiling of the operator's access pattern) return rates
+    within physical bounds: FP32 FMA above FP64 FMA, and every copy rate
+    positive and below twice the nominal HBM rate; more loads in flight do
+    not make the copy slower by more than timing noise."""
+    from paper_1807_00410_gb300.pn import access_probe, fma_peak
+    f64, f32 = fma_peak("f64"), fma_peak("f32")
+    assert 0 < f64 < f32
+    rates = [access_probe(128, 64, 32, s) for s in (1, 4)]
+    assert all(0 < r < 2 * 7900 for r in rates)
+    assert rates[1] > 0.8 * rates[0]
+    assert 0 < access_probe(128, 36, 128, 2) < 2 * 7900

@@ -60,6 +60,11 @@ def test_argument_errors_without_gpu(lib):
     o = pn._SolveOpts()
     lib.pn_default_solve_opts(ctypes.byref(o))
     assert o.tol == 1e-6 and o.restart == 60
+    g = ctypes.c_double()
+    for args in ((100, 64, 32, 1), (256, 62, 32, 1), (256, 64, 48, 1), (256, 64, 32, 3), (160, 64, 64, 1)):
+        assert lib.pn_access_probe(*args, ctypes.byref(g), None) == pn.PN_ERR_ARG, args
+    assert lib.pn_access_probe(256, 64, 32, 1, None, None) == pn.PN_ERR_ARG
+    assert lib.pn_fma_peak(7, ctypes.byref(g), None) == pn.PN_ERR_ARG
 
 
 def test_struct_sizes_match_header():
