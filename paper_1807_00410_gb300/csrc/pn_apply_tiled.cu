@@ -502,6 +502,16 @@ __device__ __forceinline__ void face_body(const Args& a, int x_lo, const FaceRan
     }
 }
 
+// Ahead of the TMA main kernel under programmatic dependent launch: waits for
+// the input's producer, then lets the main kernel start at once (the two
+// write disjoint outputs); the main kernel waits for this one at its end.
+template <int N, int MODE>
+__global__ void __launch_bounds__(256) k_face_x_first(Args a, int x_lo, FaceRanges fr) {
+    pdl_wait();
+    pdl_trigger();
+    face_body<N, MODE>(a, x_lo, fr);
+}
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(256) k_face_x(Args a, int x_lo, FaceRanges fr) {
     // Launched right after the main kernel (programmatic dependent launch:
@@ -596,7 +606,20 @@ cudaError_t launch_n(const pn_handle* h, const tiled::Args& a, const TiledPlan& 
         if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, h->ev_fork, 0);
         if (e != cudaSuccess) return e;
     }
-    if (h->tile_kernel == PN_APPLY_KERNEL_TMA && tma_serves(h)) {
+    const bool tma_main = h->tile_kernel == PN_APPLY_KERNEL_TMA && tma_serves(h);
+    if (pdl && tma_main && a.live == nullptr) {
+        // face-column kernel first, then the main kernel overlapping it (both
+        // on s; k_face_x_first and late_wait above)
+        tiled::Args af = a;
+        if (af.partials) af.partials += p.grid.x * p.grid.y * p.grid.z;
+        const tiled::FaceRanges fr = face_ranges(h);
+        e = launch_pdl(true, tiled::k_face_x_first<N, MODE>, dim3(fr.b[5]), dim3(256), 0, s, af, p.x_end, fr);
+        if (e != cudaSuccess) return e;
+        tiled::Args am = a;
+        am.late_wait = 1;
+        return launch_tma_main(h, MODE, am, p.grid, s);
+    }
+    if (tma_main) {
         e = launch_tma_main(h, MODE, a, p.grid, s);
     } else {
         e = launch_pdl(pdl, kern, p.grid, p.block, p.smem, s, a);

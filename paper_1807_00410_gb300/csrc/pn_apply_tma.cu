@@ -363,9 +363,12 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
     k_apply_tma(const __grid_constant__ Maps m, const __grid_constant__ Maps ms, Args a) {
     // programmatic dependent launch: the input (and the gate) come from the
     // previous kernel; the next kernel may start once every CTA has finished
-    // its z-march (the trigger below)
-    pdl_wait();
-    if (a.live && !*a.live) return;  // uniform over the grid
+    // its z-march (the trigger below).  With a.late_wait the previous kernel
+    // is the face-column kernel, which triggered right after its own wait:
+    // the input is complete already, and the wait at the end makes this
+    // kernel complete only after the face outputs (for the kernel after it).
+    if (!a.late_wait) pdl_wait();
+    if (a.live && !*a.live) return;  // uniform over the grid (never with late_wait)
     constexpr Lay L = LayN<N>::value;
     extern __shared__ __align__(128) unsigned char dsm[];
     float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dsm) + 127) & ~uintptr_t(127));
@@ -392,6 +395,7 @@ __global__ void __launch_bounds__(NT, (N <= 4 || (N == 5 && MODE != OP_RESIDUAL)
         case 2: run_group<N, 2, MODE>(m, ms, a, ring, ost, sg, bar_s, tx, ty, za, zb, racc); break;
         default: run_group<N, 3, MODE>(m, ms, a, ring, ost, sg, bar_s, tx, ty, za, zb, racc); break;
     }
+    if (a.late_wait) pdl_wait();
     pdl_trigger();
     if (MODE == OP_RESIDUAL && a.partials != nullptr) {
         __shared__ double red[NT / 32];

@@ -96,6 +96,8 @@ struct Args {
     double* partials;    // residual: per-CTA FP64 sums of r^2
     const int* live;     // null, or a device flag: the launch does nothing while it is 0
     unsigned int* err;   // TMA kernel: set to 1 where a bounded wait ran out (else untouched)
+    int late_wait;       // TMA kernel under programmatic dependent launch after the face-column
+                         // kernel: wait for it at the end instead of the start (see launch_n)
 };
 
 // Right-hand side of one class at slot s of this thread's column (residual
