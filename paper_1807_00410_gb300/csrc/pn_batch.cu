@@ -22,10 +22,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pn_internal.h"
@@ -1448,21 +1450,50 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     // by pn_solve with the same refinement and inner GMRES (FP32 basis, one
     // Gram-Schmidt pass, the batch's restart), and left out of the batched
     // launches (marked done).
+    // Two host threads take them, largest first, each on its own stream (two
+    // of the side streams, idle until the batched cycles): every pn_solve
+    // synchronises with the host between its restart cycles, and the other
+    // solve's kernels fill those gaps.  Each solve runs on its own handle and
+    // stream, so its result does not depend on the other.
     std::vector<pn_solve_stats> solo_st(n);
-    for (int i = 0; i < n; ++i) {
-        if (!solo[i]) continue;
-        pn_solve_opts os = o;
-        os.solver = PN_SOLVER_IR_GMRES;
-        os.basis = PN_BASIS_F32;
-        os.ortho = PN_ORTHO_CGS1;
-        os.augment = 0;
-        os.profile = 0;
-        os.precond = nullptr;
-        std::memset(&solo_st[i], 0, sizeof(pn_solve_stats));
-        const int r = pn_solve(b->hs[i], u[i], &os, &solo_st[i], b->s);
-        solo_st[i].status = r;
-        launches += solo_st[i].launches;
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i)
+        if (solo[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->hs[a]->n_active > b->hs[c]->n_active; });
+    std::atomic<int> next{0};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bcuda(b, e, "pn_batch_solve");
+    auto worker = [&](cudaStream_t ws) {
+        cudaSetDevice(dev);  // the current device is per host thread
+        for (int q = next.fetch_add(1); q < int(order.size()); q = next.fetch_add(1)) {
+            const int i = order[q];
+            pn_solve_opts os = o;
+            os.solver = PN_SOLVER_IR_GMRES;
+            os.basis = PN_BASIS_F32;
+            os.ortho = PN_ORTHO_CGS1;
+            os.augment = 0;
+            os.profile = 0;
+            os.precond = nullptr;
+            std::memset(&solo_st[i], 0, sizeof(pn_solve_stats));
+            const int r = pn_solve(b->hs[i], u[i], &os, &solo_st[i], ws);
+            solo_st[i].status = r;
+        }
+    };
+    std::thread t1;
+    bool second = false;
+    if (order.size() >= 2) {
+        try {
+            t1 = std::thread(worker, b->side[1]);
+            second = true;
+        } catch (...) {
+            // no second thread: this one takes every instance
+        }
     }
+    worker(b->side[0]);
+    if (second) t1.join();
+    for (int i = 0; i < n; ++i)
+        if (solo[i]) launches += solo_st[i].launches;
     for (int i = 0; i < n; ++i) {
         BState& S = b->h_state[i];
         std::memset(&S, 0, sizeof(BState));
