@@ -849,7 +849,7 @@ def run_batched(args):
             times.append(ms)
     its = [st["iterations"] for st in stats]
     ok = sum(1 for st in stats if st["status"] == 0)
-    solo_min = 1 << 18  # the library's default: instances at least this large are solved one by one
+    solo_min = 1 << 18  # the library's default: instances at least this large are solved by pn_solve
     n_solo = sum(1 for s in systems if s.layout.n_active >= solo_min)
     # the same batch with every instance in the batched launches (tiling
     # re-tuned for that set)

@@ -664,8 +664,8 @@ class Batch:
         self._check(self._lib.pn_batch_set_op_path(self._h, 1 if tiled else 0))
 
     def set_solo(self, min_unknowns: int):
-        """Instances with at least min_unknowns unknowns are solved one by one
-        (pn_solve) inside solve(); <= 0: every instance batched.  tune()
+        """Instances with at least min_unknowns unknowns are solved by pn_solve,
+        two at a time on two streams, inside solve(); <= 0: every instance batched.  tune()
         chooses the tiling for the batched instances under this threshold:
         call it again after changing the threshold."""
         self._check(self._lib.pn_batch_set_solo(self._h, int(min_unknowns)))
