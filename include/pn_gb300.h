@@ -471,9 +471,9 @@ int pn_batch_set_mode(pn_batch* batch, int mode, long long spin_limit);
 /* Instances with at least min_unknowns unknowns fill the GPU alone and gain
  * nothing from sharing launches: pn_batch_solve solves them first with
  * pn_solve (the same FP64 refinement around FP32 GMRES with one Gram-Schmidt
- * pass and the batch's restart), two at a time from two host threads on two
- * of the batch's streams, largest first (each solve's result is that of a
- * solve on its own), and the rest together in the batched launches, whose work lists then hold no chunk of a solo instance
+ * pass and the batch's restart), three at a time from three host threads on
+ * three of the batch's streams, largest first (each solve's result is that
+ * of a solve on its own), and the rest together in the batched launches, whose work lists then hold no chunk of a solo instance
  * (pn_batch_apply restores the full lists).  Default 2^18; min_unknowns <= 0
  * batches every instance. */
 int pn_batch_set_solo(pn_batch* batch, long long min_unknowns);

@@ -1450,8 +1450,8 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     // by pn_solve with the same refinement and inner GMRES (FP32 basis, one
     // Gram-Schmidt pass, the batch's restart), and left out of the batched
     // launches (marked done).
-    // Two host threads take them, largest first, each on its own stream (two
-    // of the side streams, idle until the batched cycles): every pn_solve
+    // kSoloWorkers host threads take them, largest first, each on its own
+    // stream (side streams, idle until the batched cycles): every pn_solve
     // synchronises with the host between its restart cycles, and the other
     // solve's kernels fill those gaps.  Each solve runs on its own handle and
     // stream, so its result does not depend on the other.
@@ -1480,18 +1480,18 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
             solo_st[i].status = r;
         }
     };
-    std::thread t1;
-    bool second = false;
-    if (order.size() >= 2) {
+    constexpr int kSoloWorkers = 3;
+    static_assert(kSoloWorkers <= pn_batch::NSIDE, "one side stream per worker");
+    std::vector<std::thread> helpers;
+    for (int t = 1; t < kSoloWorkers && t < int(order.size()); ++t) {
         try {
-            t1 = std::thread(worker, b->side[1]);
-            second = true;
+            helpers.emplace_back(worker, b->side[t]);
         } catch (...) {
-            // no second thread: this one takes every instance
+            break;  // fewer threads: the running ones take what is left
         }
     }
     worker(b->side[0]);
-    if (second) t1.join();
+    for (auto& t : helpers) t.join();
     for (int i = 0; i < n; ++i)
         if (solo[i]) launches += solo_st[i].launches;
     for (int i = 0; i < n; ++i) {

@@ -665,7 +665,7 @@ class Batch:
 
     def set_solo(self, min_unknowns: int):
         """Instances with at least min_unknowns unknowns are solved by pn_solve,
-        two at a time on two streams, inside solve(); <= 0: every instance batched.  tune()
+        three at a time on three streams, inside solve(); <= 0: every instance batched.  tune()
         chooses the tiling for the batched instances under this threshold:
         call it again after changing the threshold."""
         self._check(self._lib.pn_batch_set_solo(self._h, int(min_unknowns)))
