@@ -487,7 +487,7 @@ def run_ours(args):
     u = sysm.zeros(torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     opts = dict(solver="ir", tol=1e-6, restart=args.restart, inner_tol=args.inner_tol, max_iter=30000,
-                check_every=5, ortho=args.ortho, basis=args.basis,
+                check_every=8, ortho=args.ortho, basis=args.basis,
                 augment=args.augment if args.basis == "f16" else 0)
     for _ in range(args.warmup):
         u.zero_()

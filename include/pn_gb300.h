@@ -495,8 +495,11 @@ int pn_batch_get_op_path(const pn_batch* batch, int* tiled);
  * kernel (below) and both schedules of the face-column kernel (the outputs
  * right of the tiles: concurrently on a side stream, or after the main kernel)
  * on this handle (allocates two scratch vectors; synchronises `stream`), keeps
- * the fastest and reports its ctas_per_sm and time (either output may be
- * NULL); pn_get_apply_plan reports the whole plan (any output may be NULL);
+ * the fastest and reports its ctas_per_sm and time per apply (either output
+ * may be NULL).  While programmatic dependent launch is enabled (pn_set_pdl,
+ * the default) each timing is a chain of four applies launched as the
+ * solvers launch them (face-column kernel first, the main kernel overlapping
+ * it), so the plan is chosen for the solvers' Arnoldi steps; pn_get_apply_plan reports the whole plan (any output may be NULL);
  * pn_set_apply_tiling sets ctas_per_sm directly (1..16).  Results do not
  * depend on the plan except for the order of the residual's partial sums.
  */

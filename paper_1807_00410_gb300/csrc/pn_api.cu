@@ -648,6 +648,13 @@ int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms)
     int best = h->tile_ctas_per_sm, best_k = h->tile_kernel, best_f = h->face_serial;
     float best_t = 1e30f, best_raw = 0.0f;
     const int nk = pn::tma_serves(h) ? 2 : 1;
+    // With programmatic dependent launch enabled (the solvers' Arnoldi steps)
+    // each timing is a chain of kChain applies launched the way the solver
+    // launches them (face-column kernel first, the main kernel overlapping
+    // it): a plan that wins in isolation can lose there (P5 64^3: 1 CTA per
+    // SM 36.8 against 38.0 us alone, 83.9 against 78.2 ms per solve).
+    const bool chain = h->pdl_enabled != 0;
+    constexpr int kChain = 4;
     for (int ci = 0; ci < 8 * nk; ++ci) {
         const int c = cands[ci % 4];
         if (e != cudaSuccess) break;
@@ -660,12 +667,15 @@ int pn_tune_apply(pn_handle* h, void* stream, int* ctas_per_sm, double* best_ms)
         float t[10];
         for (int rep = 0; rep < 12 && e == cudaSuccess; ++rep) {
             e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) e = pn::launch_op(h, pn::OP_APPLY, x, y, PN_F32, nullptr, s);
+            h->pdl = chain ? 1 : 0;
+            for (int q = 0; q < (chain ? kChain : 1) && e == cudaSuccess; ++q)
+                e = pn::launch_op(h, pn::OP_APPLY, x, y, PN_F32, nullptr, s);
+            h->pdl = 0;
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.0f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (rep >= 2) t[rep - 2] = ms;
+            if (rep >= 2) t[rep - 2] = ms / float(chain ? kChain : 1);
         }
         if (e != cudaSuccess) break;
         std::sort(t, t + 10);
