@@ -653,7 +653,7 @@ def run_ours(args):
                        "stream_tma": args.stream_tma,
                        "basis": args.basis, "apply_ctas_per_sm": tiling["ctas_per_sm"], "apply_kernel": tiling["kernel"],
                        "apply_face_serial": tiling["face_serial"],
-                       "inner_tol": args.inner_tol, "l2": "flushed between timed solves (512 MiB write)",
+                       "inner_tol": args.inner_tol, "check_every": opts["check_every"], "l2": "flushed between timed solves (512 MiB write)",
                        "replicas": f"one independent problem per GPU (medium seed = {args.seed} + rank)"},
             "solve": {"iterations": stats[-1]["iterations"], "outer_iterations": stats[-1]["outer_iterations"],
                       "rel_residual": stats[-1]["rel_residual"], "wall_s": wall},
