@@ -24,7 +24,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # the bench's solve options (bench.py: run_ours)
-BENCH_OPTS = dict(solver="ir", tol=1e-6, restart=12, inner_tol=1e-2, max_iter=30000, check_every=5, ortho="cgs1",
+BENCH_OPTS = dict(solver="ir", tol=1e-6, restart=12, inner_tol=1e-2, max_iter=30000, check_every=8, ortho="cgs1",
                   basis="f16", augment=4)
 
 
