@@ -700,7 +700,7 @@ struct pn_batch {
     cudaGraphExec_t cycle = nullptr;
     int mode = 0;                   // PN_BATCH_GRAPH or PN_BATCH_PERSISTENT
     // instances with at least this many unknowns fill the GPU alone: pn_batch_solve
-    // solves them one after another with pn_solve (<= 0: none)
+    // solves them with pn_solve, a few at a time on their own streams (<= 0: none)
     int64_t solo_min = int64_t(1) << 18;
     int64_t graph_solo = -1;        // solo_min the captured cycle was built for (its tiled launches skip solo instances)
     bool lists_all = true;          // the work lists hold every instance (else the members of lists_solo)
@@ -1446,8 +1446,8 @@ int pn_batch_solve(pn_batch* b, double* const* u, const pn_solve_opts* opts, pn_
     std::vector<double> rel(n, 0.0);
     int64_t launches = 0;
     // Instances large enough to fill the GPU alone (b->solo_min unknowns) gain
-    // nothing from sharing launches: they are solved first, one after another,
-    // by pn_solve with the same refinement and inner GMRES (FP32 basis, one
+    // nothing from sharing launches: they are solved first by pn_solve with
+    // the same refinement and inner GMRES (FP32 basis, one
     // Gram-Schmidt pass, the batch's restart), and left out of the batched
     // launches (marked done).
     // kSoloWorkers host threads take them, largest first, each on its own
