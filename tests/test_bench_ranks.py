@@ -40,3 +40,30 @@ def test_replica_seeds_differ_by_rank():
     import pn_inputs
     a, b = pn_inputs.p5_64_fbm(0), pn_inputs.p5_64_fbm(1)
     assert a.source_voxel != b.source_voxel or (a.sigma_t != b.sigma_t).any()
+
+
+def test_threaded_csr_products_equal_scipy_and_drive_the_oracle_cgls():
+    """The CPU baseline's threaded sparse products (row blocks of A and of
+    A^T on separate threads) equal SciPy's own A @ v and A.T @ v, for thread
+    counts that do and do not divide the row count, and the oracle's CGLS
+    takes the same iterates through them as through the plain matrix."""
+    np = pytest.importorskip("numpy")
+    sp = pytest.importorskip("scipy.sparse")
+    import bench
+    from oracle import pn as opn
+    rng = np.random.Generator(np.random.PCG64(5))
+    A = sp.random(101, 101, density=0.05, random_state=7, format="csr") + sp.identity(101, format="csr") * 3.0
+    v = rng.standard_normal(101)
+    for threads in (1, 3, 8):
+        op = bench.ThreadedCSR(A.tocsr(), threads)
+        assert np.array_equal(op @ v, A @ v)
+        assert np.array_equal(op.T @ v, A.T @ v)
+        op.close()
+    b = rng.standard_normal(101)
+    op = bench.ThreadedCSR(A.tocsr(), 4)
+    x1 = opn.cgls(op, b, tol=1e-300, max_iter=12)
+    x2 = opn.cgls(A.tocsr(), b, tol=1e-300, max_iter=12)
+    op.close()
+    r1 = x1[0] if isinstance(x1, tuple) else x1
+    r2 = x2[0] if isinstance(x2, tuple) else x2
+    assert np.array_equal(r1, r2)
