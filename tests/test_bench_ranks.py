@@ -67,3 +67,27 @@ def test_threaded_csr_products_equal_scipy_and_drive_the_oracle_cgls():
     r1 = x1[0] if isinstance(x1, tuple) else x1
     r2 = x2[0] if isinstance(x2, tuple) else x2
     assert np.array_equal(r1, r2)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference (the FP64 oracle's CGLS on the host cores,
+    the reference arm of this paper-only build) prints one JSON line with the
+    contract's keys: the metric and unit of the GPU arm, impl "reference", a
+    cpu_baseline naming the method, cores and sample, and an e2e object whose
+    value is the line's own with no host-device copies."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+                         cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "solve/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["steps"] == 1 and d["warmup"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "CGLS" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
