@@ -210,10 +210,18 @@ def cgls(A, b: np.ndarray, tol: float = 1e-10, max_iter: int = 100000, x0=None, 
     form is never computed explicitly; section "Runtime": solving the normal
     form because A is non-symmetric).  Textbook CGLS steps; convergence is
     tested on the residual of the original system, ||Q - A u|| / ||Q||.
+    A: a matrix (anything with A @ v and A.T @ v) or a pair of functions
+    (v -> A v, v -> A^T v).
     Returns (u, iterations, relative residual).
     """
-    matvec = A.__matmul__ if not callable(A) else A[0]
-    rmatvec = (lambda v: A.T @ v) if not callable(A) else A[1]
+    if isinstance(A, tuple):
+        matvec, rmatvec = A
+    else:
+        def matvec(v):
+            return A @ v
+
+        def rmatvec(v):
+            return A.T @ v
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     r = b - matvec(x)
     s = rmatvec(r)

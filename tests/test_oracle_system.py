@@ -331,6 +331,9 @@ def test_iterative_solvers_reach_the_direct_solution(N):
     xc, it, rel = pn.cgls(S.A, S.b, tol=1e-12)
     assert rel <= 1e-12
     np.testing.assert_allclose(xc, x, atol=1e-9 * np.abs(x).max())
+    # the operator as a pair of functions takes the same iterates
+    xp, itp, relp = pn.cgls((lambda v: S.A @ v, lambda v: S.A.T @ v), S.b, tol=1e-12)
+    assert itp == it and relp == rel and np.array_equal(xp, xc)
     xg, it, rel = gmres.gmres(S.A, S.b, tol=1e-12, m=30)
     assert rel <= 1e-12
     np.testing.assert_allclose(xg, x, atol=1e-9 * np.abs(x).max())
